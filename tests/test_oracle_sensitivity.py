@@ -1,0 +1,88 @@
+"""Plant plausible mistakes in copies of the C oracle and check the pins catch them.
+
+Each mutant is compiled from a text-edited copy of ``oracle/oci_oracle.c`` in a
+temporary directory (the oracle itself carries no mutation switches) and run
+against the checks of test_oracle_pins: the whole-problem solve assembled from
+the balance equations, numpy's Gauss-Legendre rule, and the infinite-medium
+recurrence.  A mutant that still passes them would mean the pins are blind to
+that kind of error.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import brute
+from oracle import build as obuild
+
+SRC = os.path.join(os.path.dirname(obuild.__file__), "oci_oracle.c")
+
+MUTANTS = {
+    # c^- sign of the incident term (time-average, right corner)
+    "c_minus_sign": ("cm[1] = dx / 4.0 * Q[1] + e * pR - mu[m] * ink;",
+                     "cm[1] = dx / 4.0 * Q[1] + e * pR + mu[m] * ink;"),
+    # dropped time-edge term in c^+
+    "c_plus_drop_time": ("cm[0] = dx / 4.0 * Q[0] + e * pL + mu[m] * ink;",
+                         "cm[0] = dx / 4.0 * Q[0] + mu[m] * ink;"),
+    # wrong sign of the lower streaming coupling in A^+/A^-
+    "A_offdiag_sign": ("        -h,  d,    0.0,   e,", "        h,  d,    0.0,   e,"),
+    # transposed scattering weight index (w_m instead of w_n)
+    "S_weight_index": ("M[(size_t)(4 * m + i) * n4 + 4 * n + i] -= s * w[n];",
+                       "M[(size_t)(4 * m + i) * n4 + 4 * n + i] -= s * w[m];"),
+    # dt instead of dt/2 in the end-of-step equation (E = dx/(v dt) halved)
+    "E_factor": ("const double E = dx / (v * dt);       /* dx / (v dt)   */",
+                 "const double E = dx / (2.0 * v * dt); /* dx / (v dt)   */"),
+    # SI: reflecting left face picks the same ordinate instead of its mirror
+    "si_reflect_index": ("ink = psi_out[ix_psi(0, N - 1 - m, 0, N)];", "ink = psi_out[ix_psi(0, m - 1, 0, N)];"),
+    # SI: scattering source lagged on the wrong moment
+    "si_phi_moment": ("b[2] = dx / 4.0 * (ss * ph[2] + Q[2]) + mu * inh;",
+                      "b[2] = dx / 4.0 * (ss * ph[0] + Q[2]) + mu * inh;"),
+    # quadrature weights normalised to 1 instead of 2
+    "gl_weight_norm": ("double wi = 2.0 / ((1.0 - x * x) * dp * dp);", "double wi = 1.0 / ((1.0 - x * x) * dp * dp);"),
+    # upwind closure taken from the wrong corner of the upstream cell
+    "upwind_corner": ("if (j > 0) return psi[ix_psi(j - 1, m, cR, N)];", "if (j > 0) return psi[ix_psi(j - 1, m, cL, N)];"),
+}
+
+
+def _build_mutant(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    lib = obuild.build(force=True, src=str(path), out=str(tmp_path / f"lib{name}.so"))
+    return oracle.load_library(lib)
+
+
+def _pins_fail(lib):
+    """True if any pin detects the mutant."""
+    mu, w = oracle.gauss_legendre(8, lib=lib)
+    m2, w2 = np.polynomial.legendre.leggauss(8)
+    if np.abs(mu - m2).max() > 1e-12 or np.abs(w - w2).max() > 1e-12:
+        return True
+    for bcl, bcr in (("reflect", "incident"), ("incident", "reflect")):
+        p = workloads.random_small(seed=77, J=5, N=4, bc_left=bcl, bc_right=bcr)
+        pe_b, ph_b = brute.run(p, 2)
+        for method in ("oci", "si"):
+            r = oracle.run(p, method, 2, tol=1e-13, max_iter=5000, lib=lib)
+            if r["status"] != 0:
+                return True
+            if np.abs(r["phi_steps"] - ph_b).max() > 1e-9 * np.abs(ph_b).max():
+                return True
+    return False
+
+
+def test_unmutated_copy_passes(tmp_path):
+    src = open(SRC).read()
+    path = tmp_path / "same.c"
+    path.write_text(src)
+    lib = oracle.load_library(obuild.build(force=True, src=str(path), out=str(tmp_path / "libsame.so")))
+    assert not _pins_fail(lib)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    lib = _build_mutant(tmp_path, name)
+    assert _pins_fail(lib), f"planted mistake {name} passed every pin"
