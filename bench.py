@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark: converged one-cell-inversion time steps on one GB300 (or N replicas).
+
+A benchmark step is one time step of the transient problem iterated to the
+tolerance (relative change of phi < 1e-8): the whole hot path -- halo gather,
+per-ordinate block solves, scattering-moment reduction, capacitance solve,
+back-substitution, residual -- every iteration, plus the end-of-step commit.
+
+Default workload: the production homogeneous slab (65536 cells, S_64, Sigma = 1,
+c = 0.9, dx = 0.1 mfp, dt = 0.05, v = 1, Q = 1, reflecting left / vacuum right),
+FP32 angular flux with compensated moments and FP64 capacitance / residual.
+``value`` = cell-ordinate updates per second (cells x ordinates x iterations /
+device time), summed over replicas.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload slab|hetero] [--precision fp32|fp64]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "cell-ordinate updates/s, OCI to 1e-8 per time step"
+UNIT = "cell-ord/s"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_2305_13555_gb300", "csrc", "oci_device.cuh")
+
+
+def make_problem(args):
+    if args.workload == "slab":
+        p = workloads.config2(N=args.n_ord, c=args.c, dx=args.dx, J=args.cells, n_steps=args.steps + args.warmup)
+        desc = (f"homogeneous slab {p['n_cells']} cells, S_{p['n_ord']}, sigma_t=1, c={args.c}, dx={args.dx} mfp, "
+                f"dt=0.05, v=1, Q=1, reflect/vacuum, tol 1e-8")
+    else:
+        p = workloads.config4(seed=args.seed, J=args.cells if args.cells != 65536 else 131072,
+                              n_steps=args.steps + args.warmup)
+        desc = (f"seeded layered slab {p['n_cells']} cells, S_64, sigma_t 10^U(-2,2), c U(0,0.999), "
+                f"tau U(0.05,5), dt=0.02, vacuum/vacuum, tol 1e-8 (seed {args.seed})")
+    return p, desc
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in (KERNEL_SRC, os.path.join(ROOT, "paper_2305_13555_gb300", "csrc", "oci_kernels_f32.cu")):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(key):
+    """Per-launch DRAM bytes of the iteration kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    for line in open(TRAFFIC_FILE):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == key and parts[1] == kernel_hash():
+            return float(parts[2])
+    return None
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(J, N, rs):
+    """Bytes one OCI iteration must move: per cell-ordinate 2 incident values,
+    2 time-edge values, 2 outgoing values (6 words); per cell phi^l in and
+    phi^{l+1} out (8 doubles), the source moments (4 words) and a material id."""
+    return 6 * J * N * rs + J * (64 + 4 * rs + 4)
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2305_13555_gb300 as pkg
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    pkg.load_library()
+    prob, desc = make_problem(args)
+    J, N = prob["n_cells"], prob["n_ord"]
+    rs = 4 if args.precision == "fp32" else 8
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    s = pkg.Solver(prob, precision=args.precision, tol=prob["tol"], stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        rc, st = s.step()
+        assert rc == pkg.OCI_OK, (rc, st)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    iters, secs, launches = [], [], 0
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()  # evict the ~100 MB working set from L2 between timed steps
+        rc, st = s.step()
+        assert rc == pkg.OCI_OK, (rc, st)
+        iters.append(st["iters"])
+        secs.append(st["seconds"])
+        launches += st["iters"] + 2  # step prologue + iterations + commit
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    dev_time = float(sum(secs))
+    units = float(J) * N * float(sum(iters))
+    if world > 1:
+        t = torch.tensor([dev_time, units], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        dev_time, units = float(tmax[0]), float(t[1])
+    value = units / dev_time
+
+    # roofline: the iteration kernel alone, CUDA events on the same stream
+    t_launch = pkg.oci_profile_iterations(s.h, 50)
+    abytes = algorithmic_bytes(J, N, rs)
+    peaks, peak_kind = load_peaks()
+    peak = float(peaks["hbm_gbs"])
+    achieved = abytes / t_launch / 1e9
+    traffic = read_traffic(f"{args.workload}_{args.precision}_S{N}_J{J}")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "k_cells<OCI> (one OCI iteration)", "launch_us": round(t_launch * 1e6, 3),
+                "algorithmic_bytes_per_launch": abytes}
+
+    # end to end through the C ABI with host buffers: source in, fluxes out
+    q_host = np.ascontiguousarray(np.asarray(prob["q"], dtype=np.float64))
+    phi_host = np.zeros((J, 4))
+    e2e_iters = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pkg.oci_set_source(s.h, q_host)
+        rc, st = s.step()
+        pkg.oci_fluxes(s.h, phi_host)
+        e2e_iters += st["iters"]
+    e2e_t = time.perf_counter() - t0
+    e2e = {"value": float(J) * N * e2e_iters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(q_host.nbytes),
+           "d2h_bytes_per_step": int(phi_host.nbytes)}
+    s.close()
+
+    compare = {}
+    if not args.no_compare and rank == 0:
+        compare = run_compare(args, pkg, torch, stream)
+    return {
+        "value": value, "units": units, "dev_time": dev_time, "wall": wall, "iters": iters, "launches": launches,
+        "roofline": roofline, "e2e": e2e, "clocks": clk, "desc": desc, "J": J, "N": N, "compare": compare,
+    }
+
+
+def run_compare(args, pkg, torch, stream):
+    """SI and FP64 OCI on the same problem (fewer steps), for context."""
+    out = {}
+    prob, _ = make_problem(args)
+    J, N = prob["n_cells"], prob["n_ord"]
+    for name, method, prec in (("si_" + args.precision, "si", args.precision), ("oci_fp64", "oci", "fp64"),
+                               ("si_fp64", "si", "fp64")):
+        if prec == args.precision and method == "oci":
+            continue
+        s = pkg.Solver(prob, precision=prec, tol=prob["tol"], stream=stream.cuda_stream)
+        n_w, n_t = 2, min(args.steps, 5)
+        its, secs = [], []
+        ok = True
+        for k in range(n_w + n_t):
+            rc, st = s.step(method)
+            if rc != pkg.OCI_OK:
+                ok = False
+                break
+            if k >= n_w:
+                its.append(st["iters"])
+                secs.append(st["seconds"])
+        s.close()
+        if ok:
+            out[name] = {"updates_per_s": J * N * sum(its) / sum(secs), "s_per_step": sum(secs) / len(secs),
+                         "iters_per_step": sum(its) / len(its)}
+    return out
+
+
+def cpu_baseline(args, seconds_target=15.0):
+    """The FP64 oracle (dense LU per cell) on the host cores: OCI iterations of
+    the same problem, as many as fit about seconds_target."""
+    import oracle
+    prob, _ = make_problem(args)
+    J, N = prob["n_cells"], prob["n_ord"]
+    P = oracle.Problem(prob)
+    t0 = time.perf_counter()
+    oracle.run(P, "oci", 1, tol=0.0, max_iter=1, commit_unconverged=True)
+    t1 = time.perf_counter() - t0
+    m = int(max(1, min(50, seconds_target / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.run(P, "oci", 1, tol=0.0, max_iter=m, commit_unconverged=True)
+    t = time.perf_counter() - t0
+    return {"value": J * N * m / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{m} OCI iterations (FP64 dense LU per cell) of one time step of the same {J}-cell S_{N} "
+                      f"problem, {t:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step a bounded sample (a few OCI
+    iterations of the workload) timed on the host cores."""
+    import oracle
+    prob, desc = make_problem(args)
+    J, N = prob["n_cells"], prob["n_ord"]
+    P = oracle.Problem(prob)
+    for _ in range(args.warmup):
+        oracle.run(P, "oci", 1, tol=0.0, max_iter=1, commit_unconverged=True)
+    its, secs = 0, 0.0
+    per_step = 2
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(P, "oci", 1, tol=0.0, max_iter=per_step, commit_unconverged=True)
+        secs += time.perf_counter() - t0
+        its += per_step
+    value = J * N * its / secs
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "parallelism": "host threads (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"{per_step} OCI iterations per step of the {J}-cell S_{N} problem"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="slab", choices=["slab", "hetero"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--n-ord", type=int, default=64)
+    ap.add_argument("--cells", type=int, default=65536)
+    ap.add_argument("--c", type=float, default=0.9)
+    ap.add_argument("--dx", type=float, default=0.1)
+    ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    r = run_ours(args, rank, world)
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(args)
+        out = {
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["dev_time"] / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": r["desc"], "cells": r["J"], "ordinates": r["N"],
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "flushed (256 MiB write) between timed steps; iterations within a step reuse L2"},
+            "iters_per_step": sum(r["iters"]) / len(r["iters"]),
+            "s_per_step": r["dev_time"] / args.steps,
+            "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
+            "clocks": r["clocks"], "compare": r["compare"],
+        }
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * oci.h -- C ABI of the GB300 (sm_103a) one-cell-inversion library for
+ * transient slab-geometry S_N transport, discretised with simple corner balance
+ * (SCB) in space and multiple balance (MB) in time (arXiv 2305.13555).
+ *
+ * Problem statement (Sec. "Derivation of MB-SCB", Eq. 1): mono-energetic,
+ * isotropic scattering and source, slab [0, X] of n_cells cells of widths dx_j
+ * with total / scattering cross sections Sigma_j, Sigma_{s,j}; particle speed
+ * v; time step dt; initial angular flux psi_{m,0}; prescribed incident angular
+ * flux at x = 0 (mu_m > 0) and x = X (mu_m < 0), or vacuum, or reflection.
+ * Angles: n_ord-point Gauss-Legendre quadrature (weights sum to 2), ordinates
+ * ascending in mu.  Per cell and ordinate the unknowns are the corner fluxes
+ * (k,L) (k,R) (k+1/2,L) (k+1/2,R): time-average (k) and end-of-step (k+1/2)
+ * values on the left (L) and right (R) half cells (the vector psi_n of the
+ * OCI section).
+ *
+ * Conventions for every entry point
+ *   - Host pointers are read (or written) during the call only; the library
+ *     copies what it keeps.  Device pointers are noted as such.
+ *   - Array layouts are C row-major, doubles unless stated:
+ *       per-cell quantities [n_cells]; sources q[n_cells][4] in component order
+ *       (Q_{k,L}, Q_{k,R}, Q_{k+1/2,L}, Q_{k+1/2,R});
+ *       scalar-flux moments phi[n_cells][4] in the same order;
+ *       time-edge angular flux psi[n_cells][n_ord][2] (L, R);
+ *       boundary data bc[n_ord/2][2] = (time moment k, k+1/2) for pair p:
+ *       left face -> ordinate n_ord/2 + p (mu > 0), right face -> ordinate
+ *       n_ord/2 - 1 - p (mu < 0).
+ *   - Every call returns an OCI_* status; none aborts or prints.  On an error
+ *     the handle stays usable and its committed state is unchanged, except
+ *     after OCI_ECUDA, after which only oci_destroy is meaningful.
+ *   - A handle is bound to the CUDA device current at oci_create and to the
+ *     stream given there (oci_set_stream changes it).  Calls on one handle
+ *     must not overlap; different handles are independent.
+ */
+#ifndef OCI_GB300_OCI_H
+#define OCI_GB300_OCI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+    OCI_OK = 0,
+    OCI_EINVAL = 1,    /* invalid argument (sizes, signs, NULL where required) */
+    OCI_ENOMEM = 2,    /* device or host allocation failed */
+    OCI_ECUDA = 3,     /* a CUDA call failed; see oci_last_cuda_error */
+    OCI_ENOTCONV = 4,  /* max_iter reached before the tolerance */
+    OCI_ENAN = 5,      /* non-finite scalar flux detected in the residual */
+    OCI_ETIMEOUT = 6,  /* device-side iteration guard tripped (launch cap) */
+    OCI_ESTATE = 7     /* call not valid in the handle's current state */
+};
+
+enum { OCI_BC_VACUUM = 0, OCI_BC_REFLECT = 1, OCI_BC_INCIDENT = 2 };
+
+/* Arithmetic / storage precision of the angular flux and per-ordinate blocks.
+ * OCI_FP64: everything in double.  OCI_FP32: angular flux, per-ordinate 4x4
+ * blocks and the scattering-moment sums in float (the sums compensated,
+ * TwoSum), the 4x4 capacitance solve and the residual norm in double. */
+enum { OCI_FP64 = 0, OCI_FP32 = 1 };
+
+/* ------------------------------------------------------------- problem */
+typedef struct oci_problem {
+    int32_t n_cells;           /* J >= 1 */
+    int32_t n_ord;             /* N: even, 2 <= N <= 256 */
+    const double *dx;          /* host [J], > 0 */
+    const double *sigma_t;     /* host [J], >= 0 */
+    const double *sigma_s;     /* host [J], 0 <= sigma_s <= sigma_t */
+    const double *q;           /* host [J][4] isotropic source moments, or NULL = 0 */
+    double v;                  /* speed > 0 (may be +inf: steady state) */
+    double dt;                 /* time step > 0 */
+    int32_t bc_left, bc_right; /* OCI_BC_* */
+    const double *psi_bc_left;  /* host [N/2][2] for OCI_BC_INCIDENT, else ignored */
+    const double *psi_bc_right; /* host [N/2][2] for OCI_BC_INCIDENT, else ignored */
+    const double *psi0;        /* host [J][N][2] initial angular flux, or NULL = 0 */
+    int32_t precision;         /* OCI_FP64 or OCI_FP32 */
+    int32_t max_iter;          /* iterations allowed per time step, >= 1 */
+    double tol;                /* convergence: ||phi^{l+1}-phi^l||_2/||phi^{l+1}||_2 < tol */
+    void *cuda_stream;         /* cudaStream_t to launch on, or NULL (legacy default stream) */
+} oci_problem;
+
+/* Per-step statistics. */
+typedef struct oci_stats {
+    int32_t iters;       /* iterations taken (the one meeting tol included) */
+    int32_t status;      /* OCI_OK, OCI_ENOTCONV, OCI_ENAN, OCI_ETIMEOUT */
+    double residual;     /* last relative change of phi */
+    double seconds;      /* device time of the step (CUDA events on the handle's stream) */
+    int32_t committed;   /* 1 if the step advanced the state */
+    int32_t nn_accepts;  /* learned guess / corrections kept (0 without a network) */
+    int32_t nn_rejects;  /* learned corrections reverted by the safeguard */
+    int32_t reserved;
+} oci_stats;
+
+typedef struct oci_handle oci_handle;
+
+/* Create a solver for problem *p (Sec. "Derivation of MB-SCB": the inputs of
+ * Eq. 1 plus dx_j, dt and N).  Copies every input, computes the Gauss-Legendre
+ * set, the per-material per-ordinate block inverses (the A^+/A^- matrices of
+ * the SI section) and the capacitance matrices of the OCI cell system, and
+ * allocates all device memory (owned by the handle).  Errors: OCI_EINVAL for
+ * out-of-range sizes or values (N odd or > 256, dx <= 0, sigma_s > sigma_t,
+ * v or dt <= 0, NULL arrays), OCI_ENOMEM, OCI_ECUDA.  *out is set only on OK. */
+int oci_create(const oci_problem *p, oci_handle **out);
+
+/* Release the handle and all its device memory.  NULL is accepted. */
+void oci_destroy(oci_handle *h);
+
+/* Replace the source moments used from the next step on (Q_k and Q_{k+1/2}
+ * of Eqs. scb-mb-a..d): host [J][4].  OCI_EINVAL on NULL. */
+int oci_set_source(oci_handle *h, const double *q);
+
+/* Iteration controls: tolerance (>= 0; 0 iterates to max_iter), iteration cap
+ * (>= 1), and whether a step that hits the cap still commits its last iterate
+ * (1) or leaves the state at the previous step (0, default). */
+int oci_set_iteration(oci_handle *h, double tol, int32_t max_iter, int32_t commit_unconverged);
+
+/* Change the stream subsequent calls launch on (cudaStream_t, NULL = legacy). */
+int oci_set_stream(oci_handle *h, void *cuda_stream);
+
+/* Advance one time step with one-cell inversion (Sec. "One-Cell Inversion"):
+ * each iteration every cell solves (A - S) Psi = c for its 4N unknowns with
+ * the neighbours' incident fluxes from iterate l, via the block-diagonal plus
+ * rank-4 (Woodbury) form; iterate until the relative change of phi < tol.
+ * The initial iterate has both time moments equal to psi_{k-1/2}.  Returns
+ * OCI_OK, OCI_ENOTCONV (state kept unless commit_unconverged), OCI_ENAN,
+ * OCI_ETIMEOUT or OCI_ECUDA.  Synchronises the handle's stream once. */
+int oci_step(oci_handle *h, oci_stats *st);
+
+/* Same contract with source iteration (Sec. "Source Iteration (SI)"): the
+ * scattering source lags one iteration and every ordinate is swept cell by cell
+ * in its direction of travel, mu < 0 first (so a reflecting left face uses the
+ * current sweep; a reflecting right face uses the previous iterate). */
+int si_step(oci_handle *h, oci_stats *st);
+
+/* Scalar-flux moments phi = sum_n w_n psi_n of the last committed step
+ * (Eq. following the SI sweeps): host [J][4]. */
+int oci_fluxes(const oci_handle *h, double *phi);
+
+/* Same into device memory: dptr is a device pointer to J*4 doubles.  The copy
+ * is enqueued on the handle's stream (no synchronisation). */
+int oci_fluxes_device(const oci_handle *h, void *dptr);
+
+/* Checkpoint: the committed time-edge angular flux psi_{k+1/2} -> host
+ * [J][N][2]; in OCI_FP32 mode the stored floats are widened. */
+int oci_get_state(const oci_handle *h, double *psi_edge);
+
+/* Resume: replace the time-edge angular flux (host [J][N][2]); the next step
+ * starts from it. */
+int oci_set_state(oci_handle *h, const double *psi_edge);
+
+/* Time the one-cell-inversion iteration kernel alone: run n_iter iterations
+ * from the current step's initial iterate as plain stream launches (no graph,
+ * no convergence exit), bracketed by CUDA events on the handle's stream, and
+ * return the mean device time per launch in *seconds_per_launch.  The
+ * committed state (psi_{k-1/2}, published phi) is untouched and the next step
+ * restarts from it.  Used by the benchmark's roofline figure. */
+int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_launch);
+
+/* Problem sizes and quadrature of the handle: mu[N], w[N] host (may be NULL). */
+int oci_query(const oci_handle *h, int32_t *n_cells, int32_t *n_ord, double *mu, double *w);
+
+/* Message for a status code (static storage). */
+const char *oci_strerror(int code);
+
+/* Text of the last CUDA error seen by this handle ("" if none). */
+const char *oci_last_cuda_error(const oci_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCI_GB300_OCI_H */

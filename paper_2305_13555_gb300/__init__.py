@@ -1,0 +1,269 @@
+"""GB300 (sm_103a) one-cell inversion for transient slab S_N transport.
+
+Thin Python binding of the C ABI declared in ``include/oci.h`` (arguments are
+marshalled here; every step of the method runs in the library's CUDA kernels).
+The functions carry the C names: ``oci_create``, ``oci_step``, ``si_step``,
+``oci_fluxes`` ... and ``Solver`` wraps a handle for convenience.
+
+Importing this package loads ``_build/liboci_gb300.so``; it raises if the
+library has not been built (``python -m paper_2305_13555_gb300.build``) --
+there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OCI_OK, OCI_EINVAL, OCI_ENOMEM, OCI_ECUDA, OCI_ENOTCONV, OCI_ENAN, OCI_ETIMEOUT, OCI_ESTATE = range(8)
+OCI_BC_VACUUM, OCI_BC_REFLECT, OCI_BC_INCIDENT = 0, 1, 2
+OCI_FP64, OCI_FP32 = 0, 1
+_BC = {"vacuum": OCI_BC_VACUUM, "reflect": OCI_BC_REFLECT, "reflecting": OCI_BC_REFLECT,
+       "incident": OCI_BC_INCIDENT}
+_PREC = {"fp64": OCI_FP64, "f64": OCI_FP64, "double": OCI_FP64, "fp32": OCI_FP32, "f32": OCI_FP32,
+         "float": OCI_FP32}
+
+
+class OciProblem(ctypes.Structure):
+    _fields_ = [
+        ("n_cells", ctypes.c_int32), ("n_ord", ctypes.c_int32),
+        ("dx", ctypes.c_void_p), ("sigma_t", ctypes.c_void_p), ("sigma_s", ctypes.c_void_p),
+        ("q", ctypes.c_void_p), ("v", ctypes.c_double), ("dt", ctypes.c_double),
+        ("bc_left", ctypes.c_int32), ("bc_right", ctypes.c_int32),
+        ("psi_bc_left", ctypes.c_void_p), ("psi_bc_right", ctypes.c_void_p), ("psi0", ctypes.c_void_p),
+        ("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class OciStats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("residual", ctypes.c_double),
+        ("seconds", ctypes.c_double), ("committed", ctypes.c_int32), ("nn_accepts", ctypes.c_int32),
+        ("nn_rejects", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+# Every entry point declared in include/oci.h, with its ctypes signature.
+_VP, _I32, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+SIGNATURES = {
+    "oci_create": (ctypes.c_int, [ctypes.POINTER(OciProblem), ctypes.POINTER(ctypes.c_void_p)]),
+    "oci_destroy": (None, [_VP]),
+    "oci_set_source": (ctypes.c_int, [_VP, _VP]),
+    "oci_set_iteration": (ctypes.c_int, [_VP, _D, _I32, _I32]),
+    "oci_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "oci_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
+    "si_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
+    "oci_fluxes": (ctypes.c_int, [_VP, _VP]),
+    "oci_fluxes_device": (ctypes.c_int, [_VP, _VP]),
+    "oci_get_state": (ctypes.c_int, [_VP, _VP]),
+    "oci_set_state": (ctypes.c_int, [_VP, _VP]),
+    "oci_query": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "oci_profile_iterations": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(ctypes.c_double)]),
+    "oci_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "oci_last_cuda_error": (ctypes.c_char_p, [_VP]),
+}
+
+LIB_PATH = _build.LIB
+_lib = None
+
+
+def load_library(path: str = None):
+    """Load the C-ABI library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is missing: build it with paper_2305_13555_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class OciError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"{msg}: status {code} ({oci_strerror(code)})")
+
+
+def oci_strerror(code: int) -> str:
+    return load_library().oci_strerror(int(code)).decode()
+
+
+def _f64(a, shape):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def oci_create(prob: dict, precision="fp64", tol=None, max_iter=100000, stream=None):
+    """Create a handle from a problem dict (see ``workloads``); returns an int handle."""
+    J, N = int(prob["n_cells"]), int(prob["n_ord"])
+    keep = {
+        "dx": _f64(prob["dx"], (J,)), "sigma_t": _f64(prob["sigma_t"], (J,)),
+        "sigma_s": _f64(prob["sigma_s"], (J,)),
+        "q": None if prob.get("q") is None else _f64(prob["q"], (J, 4)),
+        "bl": None if prob.get("psi_bc_left") is None else _f64(prob["psi_bc_left"], (N // 2, 2)),
+        "br": None if prob.get("psi_bc_right") is None else _f64(prob["psi_bc_right"], (N // 2, 2)),
+        "psi0": None if prob.get("psi0") is None else _f64(prob["psi0"], (J, N, 2)),
+    }
+    bcl, bcr = prob.get("bc_left", 0), prob.get("bc_right", 0)
+    s = OciProblem(J, N, _ptr(keep["dx"]), _ptr(keep["sigma_t"]), _ptr(keep["sigma_s"]), _ptr(keep["q"]),
+                   float(prob["v"]), float(prob["dt"]),
+                   _BC[bcl] if isinstance(bcl, str) else int(bcl), _BC[bcr] if isinstance(bcr, str) else int(bcr),
+                   _ptr(keep["bl"]), _ptr(keep["br"]), _ptr(keep["psi0"]),
+                   _PREC[precision] if isinstance(precision, str) else int(precision), int(max_iter),
+                   float(prob.get("tol", 1e-8) if tol is None else tol),
+                   stream if stream is not None else _current_stream())
+    h = ctypes.c_void_p()
+    rc = load_library().oci_create(ctypes.byref(s), ctypes.byref(h))
+    if rc != OCI_OK:
+        raise OciError(rc, "oci_create")
+    return h.value
+
+
+def oci_destroy(h):
+    load_library().oci_destroy(h)
+
+
+def _check(rc, what, h=None):
+    if rc != OCI_OK:
+        extra = ""
+        if rc == OCI_ECUDA and h is not None:
+            extra = " " + load_library().oci_last_cuda_error(h).decode()
+        raise OciError(rc, what + extra)
+
+
+def oci_set_source(h, q):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    _check(load_library().oci_set_source(h, _ptr(q)), "oci_set_source", h)
+
+
+def oci_set_iteration(h, tol, max_iter, commit_unconverged=False):
+    _check(load_library().oci_set_iteration(h, float(tol), int(max_iter), int(bool(commit_unconverged))),
+           "oci_set_iteration", h)
+
+
+def oci_set_stream(h, stream):
+    _check(load_library().oci_set_stream(h, stream), "oci_set_stream", h)
+
+
+def oci_step(h):
+    """One OCI time step; returns (status, stats dict).  Raises only on
+    OCI_EINVAL / OCI_ECUDA; convergence failures come back as the status."""
+    st = OciStats()
+    rc = load_library().oci_step(h, ctypes.byref(st))
+    if rc in (OCI_EINVAL, OCI_ECUDA, OCI_ENOMEM):
+        _check(rc, "oci_step", h)
+    return rc, st.as_dict()
+
+
+def si_step(h):
+    st = OciStats()
+    rc = load_library().si_step(h, ctypes.byref(st))
+    if rc in (OCI_EINVAL, OCI_ECUDA, OCI_ENOMEM):
+        _check(rc, "si_step", h)
+    return rc, st.as_dict()
+
+
+def oci_query(h):
+    J, N = ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().oci_query(h, ctypes.byref(J), ctypes.byref(N), None, None), "oci_query", h)
+    mu, w = np.zeros(N.value), np.zeros(N.value)
+    _check(load_library().oci_query(h, None, None, _ptr(mu), _ptr(w)), "oci_query", h)
+    return J.value, N.value, mu, w
+
+
+def oci_fluxes(h, out=None):
+    J = oci_query(h)[0]
+    out = np.zeros((J, 4)) if out is None else out
+    _check(load_library().oci_fluxes(h, _ptr(out)), "oci_fluxes", h)
+    return out
+
+
+def oci_fluxes_device(h, dptr):
+    _check(load_library().oci_fluxes_device(h, dptr), "oci_fluxes_device", h)
+
+
+def oci_profile_iterations(h, n_iter):
+    """Mean device seconds per launch of the OCI iteration kernel (see oci.h)."""
+    sec = ctypes.c_double()
+    _check(load_library().oci_profile_iterations(h, int(n_iter), ctypes.byref(sec)), "oci_profile_iterations", h)
+    return sec.value
+
+
+def oci_get_state(h):
+    J, N, _, _ = oci_query(h)
+    out = np.zeros((J, N, 2))
+    _check(load_library().oci_get_state(h, _ptr(out)), "oci_get_state", h)
+    return out
+
+
+def oci_set_state(h, psi):
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    _check(load_library().oci_set_state(h, _ptr(psi)), "oci_set_state", h)
+
+
+class Solver:
+    """Owns one handle.  ``step()`` / ``si_step()`` advance one time step."""
+
+    def __init__(self, prob, precision="fp64", tol=None, max_iter=100000, stream=None):
+        self.prob = prob
+        self.h = oci_create(prob, precision, tol, max_iter, stream)
+
+    def step(self, method="oci"):
+        return (oci_step if method == "oci" else si_step)(self.h)
+
+    def fluxes(self):
+        return oci_fluxes(self.h)
+
+    def get_state(self):
+        return oci_get_state(self.h)
+
+    def set_state(self, psi):
+        oci_set_state(self.h, psi)
+
+    def set_source(self, q):
+        oci_set_source(self.h, q)
+
+    def set_iteration(self, tol, max_iter, commit_unconverged=False):
+        oci_set_iteration(self.h, tol, max_iter, commit_unconverged)
+
+    def close(self):
+        if self.h:
+            oci_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,700 @@
+// C ABI of the one-cell-inversion library (declarations and contracts in
+// include/oci.h).  Host-side setup in double precision: Gauss-Legendre set,
+// per-material block inverses and Woodbury capacitance; device memory owned by
+// the handle; each time step is one CUDA graph launch whose iteration loop is a
+// device-side conditional WHILE node, so the host synchronises once per step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/oci.h"
+#include "oci_kernels.h"
+
+using ocik::IterConfig;
+using ocik::IterState;
+using ocik::KernelSet;
+using ocik::KParams;
+using ocik::kmat;
+using ocik::r2;
+using ocik::r4;
+
+namespace {
+
+constexpr int kBlock = 256;
+
+// Gauss-Legendre nodes (ascending) and weights by Newton's method on P_N,
+// P_N' from N (x P_N - P_{N-1}) / (x^2 - 1), started from the Tricomi
+// asymptotic estimate of the k-th root.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double pi = 3.141592653589793238462643;
+    for (int k = 1; k <= n / 2 + (n & 1); ++k) {
+        const double th = pi * (4.0 * k - 1.0) / (4.0 * n + 2.0);
+        double r = (1.0 - (n - 1.0) / (8.0 * n * n * n)) * std::cos(th);
+        double d = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double pm = 1.0, pc = r;  // P_0, P_1
+            for (int l = 2; l <= n; ++l) {
+                const double pn = ((2.0 * l - 1.0) * r * pc - (l - 1.0) * pm) / l;
+                pm = pc;
+                pc = pn;
+            }
+            if (n == 1) { pm = 1.0; pc = r; }
+            d = n * (r * pc - pm) / (r * r - 1.0);
+            const double step = pc / d;
+            r -= step;
+            if (std::fabs(step) <= 4e-17) break;
+        }
+        double pm = 1.0, pc = r;
+        for (int l = 2; l <= n; ++l) {
+            const double pn = ((2.0 * l - 1.0) * r * pc - (l - 1.0) * pm) / l;
+            pm = pc;
+            pc = pn;
+        }
+        if (n == 1) { pm = 1.0; pc = r; }
+        d = n * (r * pc - pm) / (r * r - 1.0);
+        const double wk = 2.0 / ((1.0 - r * r) * d * d);
+        x[n - k] = r;   // k-th largest
+        x[k - 1] = -r;
+        w[n - k] = wk;
+        w[k - 1] = wk;
+    }
+    if (n & 1) x[n / 2] = 0.0;
+}
+
+struct Material {
+    double dx, st, ss;
+};
+
+}  // namespace
+
+struct oci_handle {
+    int J = 0, N = 0, P = 0, prec = 0, bcl = 0, bcr = 0;
+    double v = 1.0, dt = 1.0;
+    int lpc = 32, ppl = 1;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<double> mu, w;      // full N ordinates
+    std::vector<double> dx;         // per cell
+    std::vector<int> mat;           // per cell
+    std::vector<Material> mats;
+    KernelSet ks{};
+    // device memory (one allocation)
+    void *d_base = nullptr;
+    size_t d_bytes = 0;
+    void *faceP[2] = {nullptr, nullptr}, *faceM[2] = {nullptr, nullptr};
+    void *psi_edge = nullptr, *g = nullptr, *cellq = nullptr, *tab = nullptr, *matpar = nullptr, *muw = nullptr,
+         *refl = nullptr;
+    int *d_mat = nullptr;
+    kmat *d_matK = nullptr;
+    double *phi[2] = {nullptr, nullptr}, *phi0 = nullptr, *phi_out = nullptr, *partials = nullptr;
+    IterState *d_st = nullptr;
+    IterConfig *d_cfg = nullptr;
+    IterState *h_st = nullptr;      // pinned
+    IterConfig cfg{};
+    int grid_cells = 1, grid_pc = 1;
+    // graphs
+    cudaGraph_t graph_oci = nullptr, graph_si = nullptr;
+    cudaGraphExec_t exec_oci = nullptr, exec_si = nullptr;
+    bool guess_valid = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+};
+
+namespace {
+
+int cuda_fail(oci_handle *h, cudaError_t e, const char *what)
+{
+    if (h) {
+        char buf[256];
+        std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+        h->err = buf;
+    }
+    return OCI_ECUDA;
+}
+
+#define CK(h, call)                                          \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+size_t rsize(const oci_handle *h) { return h->prec == OCI_FP64 ? 8 : 4; }
+
+template <typename R>
+KParams<R> make_params(const oci_handle *h, int use_cond, cudaGraphConditionalHandle cond)
+{
+    KParams<R> p{};
+    p.J = h->J;
+    p.P = h->P;
+    p.bc_left = h->bcl;
+    p.bc_right = h->bcr;
+    p.use_cond = use_cond;
+    p.cond = cond;
+    p.mat = h->d_mat;
+    p.cellq = (const r4<R> *)h->cellq;
+    p.tab = (const r4<R> *)h->tab;
+    p.matpar = (const r2<R> *)h->matpar;
+    p.matK = h->d_matK;
+    p.muw = (const r2<R> *)h->muw;
+    for (int b = 0; b < 2; ++b) {
+        p.faceP[b] = (r2<R> *)h->faceP[b];
+        p.faceM[b] = (r2<R> *)h->faceM[b];
+        p.phi[b] = h->phi[b];
+    }
+    p.psi_edge = (r4<R> *)h->psi_edge;
+    p.g = (r4<R> *)h->g;
+    p.refl = (r2<R> *)h->refl;
+    p.phi0 = h->phi0;
+    p.phi_out = h->phi_out;
+    p.partials = h->partials;
+    p.st = h->d_st;
+    p.cfg = h->d_cfg;
+    return p;
+}
+
+// Upload a host array converted to the storage precision.
+int upload_real(oci_handle *h, void *dst, const std::vector<double> &src)
+{
+    if (h->prec == OCI_FP64) {
+        CK(h, cudaMemcpyAsync(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    } else {
+        std::vector<float> f(src.begin(), src.end());
+        CK(h, cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));  // f is a temporary
+        return OCI_OK;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return OCI_OK;
+}
+
+// psi [J][N][2] (host, ordinates ascending) -> psi_edge [J][P] (+L, +R, -L, -R)
+// and phi0 = (sum w psi_L, sum w psi_R) in both time moments.
+int load_state(oci_handle *h, const double *psi)
+{
+    const int J = h->J, N = h->N, P = h->P;
+    std::vector<double> pe((size_t)J * P * 4, 0.0), ph0((size_t)J * 4, 0.0);
+    if (psi) {
+        for (int j = 0; j < J; ++j) {
+            double sL = 0.0, sR = 0.0;
+            for (int m = 0; m < N; ++m) {
+                sL += h->w[m] * psi[((size_t)j * N + m) * 2];
+                sR += h->w[m] * psi[((size_t)j * N + m) * 2 + 1];
+            }
+            for (int p = 0; p < P; ++p) {
+                const int mp = P + p, mm = P - 1 - p;
+                double *o = &pe[((size_t)j * P + p) * 4];
+                o[0] = psi[((size_t)j * N + mp) * 2];
+                o[1] = psi[((size_t)j * N + mp) * 2 + 1];
+                o[2] = psi[((size_t)j * N + mm) * 2];
+                o[3] = psi[((size_t)j * N + mm) * 2 + 1];
+            }
+            ph0[j * 4 + 0] = sL; ph0[j * 4 + 1] = sR; ph0[j * 4 + 2] = sL; ph0[j * 4 + 3] = sR;
+        }
+    }
+    int rc = upload_real(h, h->psi_edge, pe);
+    if (rc) return rc;
+    CK(h, cudaMemcpyAsync(h->phi0, ph0.data(), ph0.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->phi_out, ph0.data(), ph0.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->guess_valid = false;
+    return OCI_OK;
+}
+
+int upload_source(oci_handle *h, const double *q)
+{
+    std::vector<double> cq((size_t)h->J * 4, 0.0);
+    if (q)
+        for (int j = 0; j < h->J; ++j)
+            for (int c = 0; c < 4; ++c) cq[(size_t)j * 4 + c] = h->dx[j] / 4.0 * q[(size_t)j * 4 + c];
+    return upload_real(h, h->cellq, cq);
+}
+
+// Per-material tables: complex entries of A_{+mu_p}^{-1}, (e, s), and the
+// capacitance inverse K = (I - s M_r)^{-1}, M_r = sum_p 2 w_p Re(A_p^{-1}).
+int build_tables(oci_handle *h)
+{
+    const int P = h->P, nm = (int)h->mats.size();
+    std::vector<double> tab((size_t)nm * P * 8), par((size_t)nm * 2), muw((size_t)P * 2);
+    std::vector<kmat> K(nm);
+    const bool steady = std::isinf(h->v);
+    for (int p = 0; p < P; ++p) {
+        muw[2 * p] = h->mu[P + p];
+        muw[2 * p + 1] = h->w[P + p];
+    }
+    for (int m = 0; m < nm; ++m) {
+        const Material &mt = h->mats[m];
+        const double e = steady ? 0.0 : mt.dx / (2.0 * h->v * h->dt);
+        const double s = mt.dx * mt.ss / 4.0;
+        double M00 = 0, M01 = 0, M10 = 0, M11 = 0;
+        for (int p = 0; p < P; ++p) {
+            const double mu = h->mu[P + p];
+            const std::complex<double> t((mu + mt.dx * mt.st) / 2.0, -mu / 2.0);
+            const std::complex<double> D = t * (t + 2.0 * e) + 2.0 * e * e;
+            const std::complex<double> Pc = (t + 2.0 * e) / D, Rc = -e / D, Uc = 2.0 * e / D, Vc = t / D;
+            double *o = &tab[((size_t)m * P + p) * 8];
+            o[0] = Pc.real(); o[1] = Pc.imag(); o[2] = Rc.real(); o[3] = Rc.imag();
+            o[4] = Uc.real(); o[5] = Uc.imag(); o[6] = Vc.real(); o[7] = Vc.imag();
+            const double wp = 2.0 * h->w[P + p];
+            M00 += wp * Pc.real(); M01 += wp * Rc.real(); M10 += wp * Uc.real(); M11 += wp * Vc.real();
+        }
+        const double a00 = 1.0 - s * M00, a01 = -s * M01, a10 = -s * M10, a11 = 1.0 - s * M11;
+        const double det = a00 * a11 - a01 * a10;
+        if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return OCI_EINVAL;
+        K[m] = kmat{a11 / det, -a01 / det, -a10 / det, a00 / det};
+        par[2 * m] = e;
+        par[2 * m + 1] = s;
+    }
+    int rc = upload_real(h, h->tab, tab);
+    if (!rc) rc = upload_real(h, h->matpar, par);
+    if (!rc) rc = upload_real(h, h->muw, muw);
+    if (rc) return rc;
+    CK(h, cudaMemcpy(h->d_matK, K.data(), sizeof(kmat) * nm, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->d_mat, h->mat.data(), sizeof(int) * h->J, cudaMemcpyHostToDevice));
+    return OCI_OK;
+}
+
+int upload_boundaries(oci_handle *h, const double *bl, const double *br)
+{
+    const int J = h->J, P = h->P;
+    const size_t rs = rsize(h);
+    std::vector<double> l((size_t)P * 2, 0.0), r((size_t)P * 2, 0.0);
+    if (h->bcl == OCI_BC_INCIDENT && bl) std::memcpy(l.data(), bl, sizeof(double) * P * 2);
+    if (h->bcr == OCI_BC_INCIDENT && br) std::memcpy(r.data(), br, sizeof(double) * P * 2);
+    for (int b = 0; b < 2; ++b) {
+        int rc = upload_real(h, h->faceP[b], l);  // face 0 = first P pairs
+        if (rc) return rc;
+        rc = upload_real(h, (char *)h->faceM[b] + (size_t)J * P * 2 * rs, r);  // face J
+        if (rc) return rc;
+    }
+    return OCI_OK;
+}
+
+// Kernel node helper.
+int add_kernel(oci_handle *h, cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *dep, int ndep,
+               const void *fn, dim3 grid, dim3 block, void **args)
+{
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeKernel;
+    np.kernel.func = const_cast<void *>(fn);
+    np.kernel.gridDim = grid;
+    np.kernel.blockDim = block;
+    np.kernel.sharedMemBytes = 0;
+    np.kernel.kernelParams = args;
+    CK(h, cudaGraphAddNode(node, g, dep, nullptr, ndep, &np));
+    return OCI_OK;
+}
+
+// Step graph: begin -> [si_prep] -> WHILE { [march ->] cells } -> commit.
+template <typename R>
+int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout)
+{
+    cudaGraph_t g;
+    CK(h, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    CK(h, cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
+    KParams<R> plain = make_params<R>(h, 0, 0);
+    KParams<R> loop = make_params<R>(h, 1, cond);
+    void *a_plain[] = {&plain};
+    void *a_loop[] = {&loop};
+    IterState *st = h->d_st;
+    void *a_st[] = {&st};
+    cudaGraphNode_t n_begin, n_prev, n_while, n_commit;
+    int rc = add_kernel(h, g, &n_begin, nullptr, 0, (const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st);
+    if (rc) return rc;
+    n_prev = n_begin;
+    if (si) {
+        cudaGraphNode_t n_prep;
+        rc = add_kernel(h, g, &n_prep, &n_prev, 1, h->ks.si_prep, dim3(h->grid_pc), dim3(kBlock), a_plain);
+        if (rc) return rc;
+        n_prev = n_prep;
+    }
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CK(h, cudaGraphAddNode(&n_while, g, &n_prev, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaGraphNode_t b_cells;
+    if (si) {
+        cudaGraphNode_t b_march;
+        const int nm = h->bcl == OCI_BC_REFLECT ? h->P : 2 * h->P;
+        rc = add_kernel(h, body, &b_march, nullptr, 0, h->ks.march, dim3(nm), dim3(32), a_plain);
+        if (rc) return rc;
+        rc = add_kernel(h, body, &b_cells, &b_march, 1, h->ks.cells_si, dim3(h->grid_cells), dim3(kBlock), a_loop);
+    } else {
+        rc = add_kernel(h, body, &b_cells, nullptr, 0, h->ks.cells_oci, dim3(h->grid_cells), dim3(kBlock), a_loop);
+    }
+    if (rc) return rc;
+    rc = add_kernel(h, g, &n_commit, &n_while, 1, si ? h->ks.commit_si : h->ks.commit_oci, dim3(h->grid_pc),
+                    dim3(kBlock), a_plain);
+    if (rc) return rc;
+    CK(h, cudaGraphInstantiate(eout, g, 0));
+    *gout = g;
+    return OCI_OK;
+}
+
+int ensure_graphs(oci_handle *h)
+{
+    if (h->exec_oci) return OCI_OK;
+    int rc;
+    if (h->prec == OCI_FP64) {
+        rc = build_graph<double>(h, false, &h->graph_oci, &h->exec_oci);
+        if (!rc) rc = build_graph<double>(h, true, &h->graph_si, &h->exec_si);
+    } else {
+        rc = build_graph<float>(h, false, &h->graph_oci, &h->exec_oci);
+        if (!rc) rc = build_graph<float>(h, true, &h->graph_si, &h->exec_si);
+    }
+    return rc;
+}
+
+int launch_guess(oci_handle *h)
+{
+    if (h->prec == OCI_FP64) {
+        KParams<double> p = make_params<double>(h, 0, 0);
+        void *a[] = {&p};
+        CK(h, cudaLaunchKernel(h->ks.guess, dim3(h->grid_pc), dim3(kBlock), a, 0, h->stream));
+    } else {
+        KParams<float> p = make_params<float>(h, 0, 0);
+        void *a[] = {&p};
+        CK(h, cudaLaunchKernel(h->ks.guess, dim3(h->grid_pc), dim3(kBlock), a, 0, h->stream));
+    }
+    return OCI_OK;
+}
+
+int run_step(oci_handle *h, bool si, oci_stats *st)
+{
+    if (!h) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    int rc = ensure_graphs(h);
+    if (rc) return rc;
+    if (!h->guess_valid) {
+        rc = launch_guess(h);
+        if (rc) return rc;
+    }
+    CK(h, cudaEventRecord(h->ev0, h->stream));
+    CK(h, cudaGraphLaunch(si ? h->exec_si : h->exec_oci, h->stream));
+    CK(h, cudaEventRecord(h->ev1, h->stream));
+    CK(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    const IterState s = *h->h_st;
+    h->guess_valid = s.committed != 0;
+    int status;
+    switch (s.status) {
+    case ocik::ST_CONVERGED: status = OCI_OK; break;
+    case ocik::ST_MAXITER: status = OCI_ENOTCONV; break;
+    case ocik::ST_NAN: status = OCI_ENAN; break;
+    case ocik::ST_GUARD: status = OCI_ETIMEOUT; break;
+    default: status = OCI_ETIMEOUT; break;
+    }
+    if (st) {
+        st->iters = s.iter;
+        st->status = status;
+        st->residual = s.resid;
+        st->seconds = ms * 1e-3;
+        st->committed = s.committed;
+        st->nn_accepts = 0;
+        st->nn_rejects = 0;
+        st->reserved = 0;
+    }
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int oci_create(const oci_problem *p, oci_handle **out)
+{
+    if (!p || !out) return OCI_EINVAL;
+    const int J = p->n_cells, N = p->n_ord;
+    if (J < 1 || N < 2 || N > 256 || (N & 1)) return OCI_EINVAL;
+    if (!p->dx || !p->sigma_t || !p->sigma_s) return OCI_EINVAL;
+    if (!(p->v > 0.0) || !(p->dt > 0.0) || !std::isfinite(p->dt)) return OCI_EINVAL;
+    if (p->precision != OCI_FP64 && p->precision != OCI_FP32) return OCI_EINVAL;
+    if (p->max_iter < 1 || !(p->tol >= 0.0)) return OCI_EINVAL;
+    for (int bc : {p->bc_left, p->bc_right})
+        if (bc < OCI_BC_VACUUM || bc > OCI_BC_INCIDENT) return OCI_EINVAL;
+    if ((p->bc_left == OCI_BC_INCIDENT && !p->psi_bc_left) || (p->bc_right == OCI_BC_INCIDENT && !p->psi_bc_right))
+        return OCI_EINVAL;
+    for (int j = 0; j < J; ++j) {
+        const double dx = p->dx[j], st = p->sigma_t[j], ss = p->sigma_s[j];
+        if (!(dx > 0.0) || !std::isfinite(dx) || !(st >= 0.0) || !std::isfinite(st) || !(ss >= 0.0) || ss > st)
+            return OCI_EINVAL;
+    }
+    oci_handle *h = new (std::nothrow) oci_handle();
+    if (!h) return OCI_ENOMEM;
+    h->J = J;
+    h->N = N;
+    h->P = N / 2;
+    h->prec = p->precision;
+    h->bcl = p->bc_left;
+    h->bcr = p->bc_right;
+    h->v = p->v;
+    h->dt = p->dt;
+    h->stream = (cudaStream_t)p->cuda_stream;
+    h->cfg.max_iter = p->max_iter;
+    h->cfg.tol = p->tol;
+    h->cfg.commit_unconverged = 0;
+    gauss_legendre(N, h->mu, h->w);
+    h->dx.assign(p->dx, p->dx + J);
+    // materials: distinct (dx, sigma_t, sigma_s)
+    std::map<std::tuple<double, double, double>, int> idx;
+    h->mat.resize(J);
+    for (int j = 0; j < J; ++j) {
+        const auto key = std::make_tuple(p->dx[j], p->sigma_t[j], p->sigma_s[j]);
+        auto it = idx.find(key);
+        if (it == idx.end()) {
+            it = idx.emplace(key, (int)h->mats.size()).first;
+            h->mats.push_back(Material{p->dx[j], p->sigma_t[j], p->sigma_s[j]});
+        }
+        h->mat[j] = it->second;
+    }
+    // kernel layout
+    const int P = h->P;
+    if (P <= 32) {
+        int l = 1;
+        while (l < P) l <<= 1;
+        h->lpc = l;
+        h->ppl = 1;
+    } else {
+        h->lpc = 32;
+        h->ppl = P <= 64 ? 2 : 4;
+    }
+    const bool okk = h->prec == OCI_FP64 ? ocik::kernel_set_f64(h->lpc, h->ppl, &h->ks)
+                                         : ocik::kernel_set_f32(h->lpc, h->ppl, &h->ks);
+    if (!okk) { delete h; return OCI_EINVAL; }
+    const int warps_per_block = kBlock / 32;
+    const int nchunks = (J + h->ks.cells_per_warp - 1) / h->ks.cells_per_warp;
+    h->grid_cells = (nchunks + warps_per_block - 1) / warps_per_block;
+    const int npc = (J + h->ks.cells_per_warp_pc - 1) / h->ks.cells_per_warp_pc;
+    h->grid_pc = (npc + warps_per_block - 1) / warps_per_block;
+    if (h->grid_pc > 152 * 16) h->grid_pc = 152 * 16;
+
+    int rc = OCI_OK;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return OCI_ECUDA; }
+    // device layout
+    const size_t rs = rsize(h), nm = h->mats.size();
+    const size_t face = (size_t)(J + 1) * P * 2 * rs;
+    size_t sizes[] = {face, face, face, face,                 // faceP[0], faceP[1], faceM[0], faceM[1]
+                      (size_t)J * P * 4 * rs,                 // psi_edge
+                      (size_t)J * P * 4 * rs,                 // g
+                      (size_t)J * 4 * rs,                     // cellq
+                      nm * P * 8 * rs,                        // tab
+                      nm * 2 * rs,                            // matpar
+                      (size_t)P * 2 * rs,                     // muw
+                      (size_t)P * 2 * rs,                     // refl
+                      (size_t)J * sizeof(int),                // mat
+                      nm * sizeof(kmat),                      // matK
+                      (size_t)J * 32, (size_t)J * 32, (size_t)J * 32, (size_t)J * 32,  // phi[2], phi0, phi_out
+                      (size_t)h->grid_cells * 16,             // partials
+                      sizeof(IterState), sizeof(IterConfig)};
+    const int ns = sizeof(sizes) / sizeof(sizes[0]);
+    size_t off[32], total = 0;
+    for (int i = 0; i < ns; ++i) {
+        off[i] = total;
+        total += (sizes[i] + 255) & ~(size_t)255;
+    }
+    if (cudaMalloc(&h->d_base, total) != cudaSuccess) { delete h; return OCI_ENOMEM; }
+    h->d_bytes = total;
+    char *b = (char *)h->d_base;
+    h->faceP[0] = b + off[0]; h->faceP[1] = b + off[1]; h->faceM[0] = b + off[2]; h->faceM[1] = b + off[3];
+    h->psi_edge = b + off[4]; h->g = b + off[5]; h->cellq = b + off[6]; h->tab = b + off[7];
+    h->matpar = b + off[8]; h->muw = b + off[9]; h->refl = b + off[10]; h->d_mat = (int *)(b + off[11]);
+    h->d_matK = (kmat *)(b + off[12]);
+    h->phi[0] = (double *)(b + off[13]); h->phi[1] = (double *)(b + off[14]);
+    h->phi0 = (double *)(b + off[15]); h->phi_out = (double *)(b + off[16]);
+    h->partials = (double *)(b + off[17]);
+    h->d_st = (IterState *)(b + off[18]);
+    h->d_cfg = (IterConfig *)(b + off[19]);
+    if (cudaMallocHost(&h->h_st, sizeof(IterState)) != cudaSuccess) { oci_destroy(h); return OCI_ENOMEM; }
+    if (cudaMemsetAsync(h->d_base, 0, total, h->stream) != cudaSuccess ||
+        cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+        oci_destroy(h);
+        return OCI_ECUDA;
+    }
+    rc = build_tables(h);
+    if (!rc) rc = upload_source(h, p->q);
+    if (!rc) rc = upload_boundaries(h, p->psi_bc_left, p->psi_bc_right);
+    if (!rc) rc = load_state(h, p->psi0);
+    if (!rc && cudaMemcpy(h->d_cfg, &h->cfg, sizeof(IterConfig), cudaMemcpyHostToDevice) != cudaSuccess) rc = OCI_ECUDA;
+    if (rc) { oci_destroy(h); return rc; }
+    *out = h;
+    return OCI_OK;
+}
+
+void oci_destroy(oci_handle *h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    if (h->exec_oci) cudaGraphExecDestroy(h->exec_oci);
+    if (h->exec_si) cudaGraphExecDestroy(h->exec_si);
+    if (h->graph_oci) cudaGraphDestroy(h->graph_oci);
+    if (h->graph_si) cudaGraphDestroy(h->graph_si);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->h_st) cudaFreeHost(h->h_st);
+    if (h->d_base) cudaFree(h->d_base);
+    delete h;
+}
+
+int oci_set_source(oci_handle *h, const double *q)
+{
+    if (!h || !q) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    return upload_source(h, q);
+}
+
+int oci_set_iteration(oci_handle *h, double tol, int32_t max_iter, int32_t commit_unconverged)
+{
+    if (!h || !(tol >= 0.0) || max_iter < 1) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    h->cfg.tol = tol;
+    h->cfg.max_iter = max_iter;
+    h->cfg.commit_unconverged = commit_unconverged ? 1 : 0;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(h->d_cfg, &h->cfg, sizeof(IterConfig), cudaMemcpyHostToDevice));
+    return OCI_OK;
+}
+
+int oci_set_stream(oci_handle *h, void *cuda_stream)
+{
+    if (!h) return OCI_EINVAL;
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->stream = (cudaStream_t)cuda_stream;
+    return OCI_OK;
+}
+
+int oci_step(oci_handle *h, oci_stats *st) { return run_step(h, false, st); }
+
+int si_step(oci_handle *h, oci_stats *st) { return run_step(h, true, st); }
+
+int oci_fluxes(const oci_handle *hc, double *phi)
+{
+    oci_handle *h = const_cast<oci_handle *>(hc);
+    if (!h || !phi) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaMemcpyAsync(phi, h->phi_out, (size_t)h->J * 32, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return OCI_OK;
+}
+
+int oci_fluxes_device(const oci_handle *hc, void *dptr)
+{
+    oci_handle *h = const_cast<oci_handle *>(hc);
+    if (!h || !dptr) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaMemcpyAsync(dptr, h->phi_out, (size_t)h->J * 32, cudaMemcpyDeviceToDevice, h->stream));
+    return OCI_OK;
+}
+
+int oci_get_state(const oci_handle *hc, double *psi)
+{
+    oci_handle *h = const_cast<oci_handle *>(hc);
+    if (!h || !psi) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    const int J = h->J, N = h->N, P = h->P;
+    const size_t n = (size_t)J * P * 4;
+    std::vector<double> pe(n);
+    if (h->prec == OCI_FP64) {
+        CK(h, cudaMemcpyAsync(pe.data(), h->psi_edge, n * 8, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    } else {
+        std::vector<float> f(n);
+        CK(h, cudaMemcpyAsync(f.data(), h->psi_edge, n * 4, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (size_t i = 0; i < n; ++i) pe[i] = f[i];
+    }
+    for (int j = 0; j < J; ++j)
+        for (int p = 0; p < P; ++p) {
+            const double *o = &pe[((size_t)j * P + p) * 4];
+            const int mp = P + p, mm = P - 1 - p;
+            psi[((size_t)j * N + mp) * 2] = o[0];
+            psi[((size_t)j * N + mp) * 2 + 1] = o[1];
+            psi[((size_t)j * N + mm) * 2] = o[2];
+            psi[((size_t)j * N + mm) * 2 + 1] = o[3];
+        }
+    return OCI_OK;
+}
+
+int oci_set_state(oci_handle *h, const double *psi)
+{
+    if (!h || !psi) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    return load_state(h, psi);
+}
+
+int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_launch)
+{
+    if (!h || n_iter < 1 || !seconds_per_launch) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    int rc = launch_guess(h);
+    if (rc) return rc;
+    // no exit on tolerance or iteration count while timing
+    IterConfig timing{};
+    timing.max_iter = 0x3fffffff;
+    timing.tol = 0.0;
+    timing.commit_unconverged = 0;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(h->d_cfg, &timing, sizeof(IterConfig), cudaMemcpyHostToDevice));
+    IterState *st = h->d_st;
+    void *a_st[] = {&st};
+    CK(h, cudaLaunchKernel((const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st, 0, h->stream));
+    KParams<double> pd = make_params<double>(h, 0, 0);
+    KParams<float> pf = make_params<float>(h, 0, 0);
+    void *args[] = {h->prec == OCI_FP64 ? (void *)&pd : (void *)&pf};
+    CK(h, cudaEventRecord(h->ev0, h->stream));
+    for (int i = 0; i < n_iter; ++i)
+        CK(h, cudaLaunchKernel(h->ks.cells_oci, dim3(h->grid_cells), dim3(kBlock), args, 0, h->stream));
+    CK(h, cudaEventRecord(h->ev1, h->stream));
+    CK(h, cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    *seconds_per_launch = ms * 1e-3 / n_iter;
+    CK(h, cudaMemcpy(h->d_cfg, &h->cfg, sizeof(IterConfig), cudaMemcpyHostToDevice));
+    h->guess_valid = false;  // the face buffers now hold timing iterates
+    return OCI_OK;
+}
+
+int oci_query(const oci_handle *h, int32_t *n_cells, int32_t *n_ord, double *mu, double *w)
+{
+    if (!h) return OCI_EINVAL;
+    if (n_cells) *n_cells = h->J;
+    if (n_ord) *n_ord = h->N;
+    if (mu) std::memcpy(mu, h->mu.data(), sizeof(double) * h->N);
+    if (w) std::memcpy(w, h->w.data(), sizeof(double) * h->N);
+    return OCI_OK;
+}
+
+const char *oci_strerror(int code)
+{
+    switch (code) {
+    case OCI_OK: return "ok";
+    case OCI_EINVAL: return "invalid argument";
+    case OCI_ENOMEM: return "out of memory";
+    case OCI_ECUDA: return "CUDA error";
+    case OCI_ENOTCONV: return "not converged within max_iter";
+    case OCI_ENAN: return "non-finite scalar flux";
+    case OCI_ETIMEOUT: return "device iteration guard tripped";
+    case OCI_ESTATE: return "call not valid in this state";
+    default: return "unknown status";
+    }
+}
+
+const char *oci_last_cuda_error(const oci_handle *h) { return h ? h->err.c_str() : ""; }
+
+}  // extern "C"

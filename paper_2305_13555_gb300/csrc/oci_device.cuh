@@ -1,0 +1,738 @@
+// Device code for the one-cell-inversion (OCI) and source-iteration (SI)
+// schemes of MB-SCB transient slab S_N transport (arXiv 2305.13555).
+//
+// Data layout in HBM (R = float in FP32 mode, double in FP64 mode; P = N/2
+// ordinate pairs, pair p = (mu_p > 0, -mu_p), ascending mu_p):
+//   faceP[b][f][p]   r2  outgoing flux of +mu_p through face f (f = 0..J), the
+//                        (k, k+1/2) values of the upstream corner R of cell f-1;
+//   faceM[b][f][p]   r2  outgoing flux of -mu_p through face f, corner L of cell f;
+//                        b = ping-pong buffer; faceP[b][0] / faceM[b][J] hold
+//                        the prescribed boundary data and are never written by
+//                        a cell.
+//   psi_edge[j][p]   r4  time-edge flux psi_{k-1/2}: (+L, +R, -L, -R)
+//   cellq[j]         r4  (dx/4) (Q_kL, Q_kR, Q_hL, Q_hR)
+//   mat[j]           int material id; tab[m][p] = complex entries of A_{+mu}^{-1};
+//                        matpar[m] = (e = dx/(2 v dt), s = dx Sigma_s / 4);
+//                        matK[m] = (I - s M)^{-1} in double (Woodbury capacitance)
+//   phi[2][j][4]     double scalar-flux moments, ping-pong over iterations
+//   g[p][j]          r4  SI affine offsets (pair-major for the march)
+//   refl[p]          r2  SI: +mu flux leaving x = X in the previous iterate
+//
+// Per ordinate the 4x4 block of the SI section, A_m, acts on the corner pair
+// (L, R) as multiplication by a complex number: with v = v_L + i v_R the
+// streaming/collision block [[a, mu/2], [-mu/2, a]] is t = a - i mu/2, so
+//   A_{+mu} = [[t, e], [-2e, t + 2e]]  (a 2x2 matrix over C),
+//   A_{+mu}^{-1} = [[t + 2e, -e], [2e, t]] / (t (t + 2e) + 2 e^2),
+//   A_{-mu} = conj(A_{+mu}).
+// The cell system (A - S) Psi = c of the OCI section has S = s (1 w^T) (x) I_4,
+// so with y_m = A_m^{-1} c_m, r = sum_m w_m y_m, M = sum_m w_m A_m^{-1}:
+//   phi = (I - s M)^{-1} r,   psi_m = y_m + s A_m^{-1} phi   (Woodbury).
+// For a symmetric quadrature M is real in the C sense (M = M_r (x) I_2), so the
+// capacitance solve is two 2x2 real systems sharing one inverse K.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ocik {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename R> struct __align__(2 * sizeof(R)) r2 { R x, y; };
+template <typename R> struct __align__(16) r4 { R x, y, z, w; };
+struct __align__(16) kmat { double k00, k01, k10, k11; };
+
+enum : int { BC_VACUUM = 0, BC_REFLECT = 1, BC_INCIDENT = 2 };
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NAN = 3, ST_GUARD = 4 };
+// k_cells modes
+enum : int { M_OCI = 0, M_SI = 1 };
+// k_percell modes
+enum : int { C_COMMIT_OCI = 0, C_COMMIT_SI = 1, C_SI_PREP = 2, C_GUESS = 3 };
+
+// Iteration state of the current time step (device memory, one per handle).
+struct IterState {
+    int iter;          // iterations completed in this step
+    int status;        // ST_*
+    int base;          // face buffer read by iteration 1 of this step
+    int base_next;     // face buffer holding the next step's initial iterate
+    unsigned int arrive;  // blocks of the current launch that finished
+    int launches;      // launches of the iteration kernel in this step (guard)
+    int committed;     // last step advanced the state
+    int pad0;
+    double resid;      // last relative change of phi
+    double d2, p2;     // sum (dphi)^2, sum phi^2 of the last iteration
+};
+
+struct IterConfig {
+    int max_iter;
+    int commit_unconverged;
+    double tol;
+};
+
+template <typename R>
+struct KParams {
+    int J, P;
+    int bc_left, bc_right;
+    int use_cond;
+    int pad0;
+    cudaGraphConditionalHandle cond;
+    const int *mat;
+    const r4<R> *cellq;
+    const r4<R> *tab;      // [n_mat][P][2]: (Pr, Pi, Rr, Ri), (Ur, Ui, Vr, Vi)
+    const r2<R> *matpar;   // [n_mat]: (e, s)
+    const kmat *matK;      // [n_mat]
+    const r2<R> *muw;      // [P]: (mu, w)
+    r2<R> *faceP[2];
+    r2<R> *faceM[2];
+    r4<R> *psi_edge;
+    r4<R> *g;
+    r2<R> *refl;           // [P] SI: lagged mirror flux at a reflecting right face
+    double *phi[2];
+    double *phi0;
+    double *phi_out;
+    double *partials;      // [gridDim.x][2]
+    IterState *st;
+    const IterConfig *cfg;
+};
+
+// ------------------------------------------------------------ load helpers
+__device__ __forceinline__ r4<float> ldg4(const r4<float> *p)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ r4<double> ldg4(const r4<double> *p)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ r2<float> ldg2(const r2<float> *p)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ r2<double> ldg2(const r2<double> *p)
+{
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    return {v.x, v.y};
+}
+// Streaming (read-write across launches) data: plain coherent loads.
+__device__ __forceinline__ r4<float> ld4(const r4<float> *p)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ r4<double> ld4(const r4<double> *p)
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    const double2 b = reinterpret_cast<const double2 *>(p)[1];
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ r2<float> ld2(const r2<float> *p)
+{
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    return {v.x, v.y};
+}
+__device__ __forceinline__ r2<double> ld2(const r2<double> *p)
+{
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    return {v.x, v.y};
+}
+template <typename R> __device__ __forceinline__ void st2(r2<R> *p, R x, R y) { *p = r2<R>{x, y}; }
+template <typename R> __device__ __forceinline__ void st4(r4<R> *p, R x, R y, R z, R w) { *p = r4<R>{x, y, z, w}; }
+
+// Complex entries of A_{+mu}^{-1} for one (material, pair).
+template <typename R> struct Coef { R pr, pi, rr, ri, ur, ui, vr, vi; };
+
+template <typename R>
+__device__ __forceinline__ Coef<R> load_coef(const r4<R> *tab, int m, int P, int p)
+{
+    const r4<R> *t = tab + ((size_t)m * P + p) * 2;
+    const r4<R> a = ldg4(t), b = ldg4(t + 1);
+    return {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+}
+
+// y = A^{-1} u for the complex 2-vector u = (uk, uh).
+template <typename R>
+__device__ __forceinline__ void ainv(const Coef<R> &a, R ukr, R uki, R uhr, R uhi, R &ykr, R &yki, R &yhr, R &yhi)
+{
+    ykr = a.pr * ukr - a.pi * uki + a.rr * uhr - a.ri * uhi;
+    yki = a.pr * uki + a.pi * ukr + a.rr * uhi + a.ri * uhr;
+    yhr = a.ur * ukr - a.ui * uki + a.vr * uhr - a.vi * uhi;
+    yhi = a.ur * uki + a.ui * ukr + a.vr * uhi + a.vi * uhr;
+}
+
+// Error-free sum (Knuth's TwoSum) in round-to-nearest.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
+{
+    s = a + b;
+    e = 0.0;
+}
+
+// Reduce V values per lane (s with compensation e) over the LPC lanes of a
+// segment.  Afterwards lane holds NV = max(V/LPC, 1) sums in s[0..NV-1] for
+// value indices [base, base + NV) with base = NV * (lane % LPC) when V >= LPC,
+// else lane % V (lanes above V in the segment hold copies).
+template <int LPC, int V, bool COMP, typename R>
+__device__ __forceinline__ void reduce_scatter(R (&s)[V], R (&e)[V], int lane)
+{
+    constexpr int LS = LPC < V ? LPC : V;
+    // all-reduce over the segment bits above LS (only when V < LPC)
+#pragma unroll
+    for (int o = LPC / 2; o >= LS && o >= 1; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const R rs = __shfl_xor_sync(FULL, s[i], o);
+            if constexpr (COMP) {
+                const R re = __shfl_xor_sync(FULL, e[i], o);
+                R t;
+                two_sum(s[i], rs, s[i], t);
+                e[i] = e[i] + re + t;
+            } else {
+                s[i] = s[i] + rs;
+            }
+        }
+    }
+    // reduce-scatter over the low log2(LS) bits
+#pragma unroll
+    for (int lev = 0; (LS >> (lev + 1)) >= 1; ++lev) {
+        const int o = LS >> (lev + 1);
+        const int half = V >> (lev + 1);
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const R snd = up ? s[i] : s[i + half];
+            const R kp = up ? s[i + half] : s[i];
+            const R rs = __shfl_xor_sync(FULL, snd, o);
+            if constexpr (COMP) {
+                const R esnd = up ? e[i] : e[i + half];
+                const R ekp = up ? e[i + half] : e[i];
+                const R re = __shfl_xor_sync(FULL, esnd, o);
+                R t;
+                two_sum(kp, rs, s[i], t);
+                e[i] = ekp + re + t;
+            } else {
+                s[i] = kp + rs;
+            }
+        }
+    }
+}
+
+// Inverse of reduce_scatter's distribution: every lane of the segment ends
+// with all V values (own NV values start in a[0..NV-1]).
+template <int LPC, int V, typename R>
+__device__ __forceinline__ void all_gather(R (&a)[V], int lane)
+{
+    constexpr int LS = LPC < V ? LPC : V;
+    constexpr int NV0 = V / LS;
+#pragma unroll
+    for (int o = 1; o < LS; o <<= 1) {
+        const int n = NV0 * o;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const R rv = __shfl_xor_sync(FULL, a[i], o);
+            const R lo = up ? rv : a[i];
+            const R hi = up ? a[i] : rv;
+            a[i] = lo;
+            a[n + i] = hi;
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Sum (a, b) over the block in a fixed order; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double &a, double &b)
+{
+    __shared__ double sh[2][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) { sh[0][warp] = a; sh[1][warp] = b; }
+    __syncthreads();
+    if (warp == 0) {
+        a = lane < nw ? sh[0][lane] : 0.0;
+        b = lane < nw ? sh[1][lane] : 0.0;
+        a = warp_sum(a);
+        b = warp_sum(b);
+    }
+    __syncthreads();
+}
+
+// Last-block finalisation of one iteration: sum the per-block partials in a
+// fixed order, form the relative change of phi, update the state and the
+// graph's loop condition.
+__device__ __forceinline__ void finalize_iteration(double d2, double p2, double *partials, IterState *st,
+                                                   const IterConfig *cfg, int iter, int use_cond,
+                                                   cudaGraphConditionalHandle cond)
+{
+    __shared__ int is_last;
+    block_sum2(d2, p2);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = d2;
+        partials[2 * blockIdx.x + 1] = p2;
+        __threadfence();
+        const unsigned prev = atomicAdd(&st->arrive, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        a += __ldcg(partials + 2 * i);
+        b += __ldcg(partials + 2 * i + 1);
+    }
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+        const int it = iter + 1;
+        double resid;
+        if (b > 0.0) resid = sqrt(a / b);
+        else resid = (a == 0.0) ? 0.0 : __longlong_as_double(0x7ff0000000000000LL);
+        st->iter = it;
+        st->resid = resid;
+        st->d2 = a;
+        st->p2 = b;
+        st->arrive = 0u;
+        if (st->status == ST_RUNNING) {
+            int ns = ST_RUNNING;
+            if (!(resid == resid) || !(a == a) || !(b == b) || isinf(b)) ns = ST_NAN;
+            else if (resid < cfg->tol) ns = ST_CONVERGED;
+            else if (it >= cfg->max_iter) ns = ST_MAXITER;
+            st->status = ns;
+            if (use_cond) cudaGraphSetConditional(cond, ns == ST_RUNNING ? 1u : 0u);
+        }
+    }
+}
+
+// Iteration prologue shared by the iteration kernels: read the state, trip
+// the launch guard, stop the loop when the step is already decided.
+// Returns false when the kernel has nothing to do.
+template <typename R>
+__device__ __forceinline__ bool iteration_prologue(const KParams<R> &p, int &iter, int &base)
+{
+    IterState *st = p.st;
+    const int status = *(volatile int *)&st->status;
+    iter = *(volatile int *)&st->iter;
+    base = *(volatile int *)&st->base;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int launches = atomicAdd(&st->launches, 1);
+        if (status == ST_RUNNING && launches >= p.cfg->max_iter + 2) {
+            // The loop should have ended: stop it and report.
+            st->status = ST_GUARD;
+            if (p.use_cond) cudaGraphSetConditional(p.cond, 0u);
+        } else if (status != ST_RUNNING && p.use_cond) {
+            cudaGraphSetConditional(p.cond, 0u);
+        }
+    }
+    return status == ST_RUNNING;
+}
+
+// ---------------------------------------------------------------------------
+// One iteration over all cells.
+//   M_OCI: phi^{l+1} = K r with r = sum w A^{-1} c(halo^l); outgoing corners
+//          y_out + s (A^{-1} phi)_out into the other face buffer.
+//   M_SI : the scalar-flux update after a sweep: phi^{l+1} = sum w A^{-1}
+//          (c(faces^{l+1}) + s phi^l), and the next sweep's affine offsets
+//          g = (A^{-1}(c_fixed + s phi^{l+1}))_out.
+// LPC lanes per cell (power of two <= 32), PPL pairs per lane, CHUNK cell rows
+// per warp pass.
+// ---------------------------------------------------------------------------
+template <typename R, int LPC, int PPL, int CHUNK, int MODE>
+__global__ void __launch_bounds__(256) k_cells(const KParams<R> p)
+{
+    constexpr int SPW = 32 / LPC;
+    constexpr int CPC = CHUNK * SPW;
+    constexpr int V = 4 * CHUNK;
+    constexpr bool COMP = sizeof(R) == 4;
+    constexpr int NV = (V >= LPC) ? V / LPC : 1;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int seg = lane / LPC, ls = lane % LPC;
+    const int J = p.J, P = p.P;
+
+    int iter, base;
+    if (!iteration_prologue(p, iter, base)) return;
+    const int frd = MODE == M_OCI ? ((base + iter) & 1) : base;
+    const int fwr = frd ^ 1;
+    const double *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
+    double *phw = p.phi[(iter + 1) & 1];
+    const r2<R> *fPr = p.faceP[frd], *fMr = p.faceM[frd];
+    r2<R> *fPw = p.faceP[fwr], *fMw = p.faceM[fwr];
+    const bool refl_l = MODE == M_OCI && p.bc_left == BC_REFLECT;
+    const bool refl_r = MODE == M_OCI && p.bc_right == BC_REFLECT;
+
+    double acc_d2 = 0.0, acc_p2 = 0.0;
+    const int nchunks = (J + CPC - 1) / CPC;
+    for (int chunk = blockIdx.x * wpb + warp; chunk < nchunks; chunk += gridDim.x * wpb) {
+        R s_acc[V], e_acc[V];
+        R yo[CHUNK][PPL][4];
+        // ---------------- phase A: per-ordinate block solves y = A^{-1} c
+#pragma unroll
+        for (int r = 0; r < CHUNK; ++r) {
+            const int cell = chunk * CPC + r * SPW + seg;
+            const bool valid = cell < J;
+            const int m = valid ? __ldg(p.mat + cell) : 0;
+            const r4<R> qd = valid ? ldg4(p.cellq + cell) : r4<R>{0, 0, 0, 0};
+            const r2<R> es = ldg2(p.matpar + m);
+            R fkl = 0, fkr = 0, fhl = 0, fhr = 0;
+            if (MODE == M_SI && valid) {
+                const double2 a = __ldcg(reinterpret_cast<const double2 *>(phr + 4 * (size_t)cell));
+                const double2 b = __ldcg(reinterpret_cast<const double2 *>(phr + 4 * (size_t)cell) + 1);
+                fkl = (R)a.x * es.y; fkr = (R)a.y * es.y; fhl = (R)b.x * es.y; fhr = (R)b.y * es.y;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { s_acc[4 * r + k] = 0; e_acc[4 * r + k] = 0; }
+#pragma unroll
+            for (int i = 0; i < PPL; ++i) {
+                const int pp = ls + LPC * i;
+                yo[r][i][0] = yo[r][i][1] = yo[r][i][2] = yo[r][i][3] = 0;
+                if (valid && pp < P) {
+                    const Coef<R> a = load_coef(p.tab, m, P, pp);
+                    const r2<R> mw = ldg2(p.muw + pp);
+                    const r2<R> inP = (refl_l && cell == 0) ? ld2(fMr + pp) : ld2(fPr + (size_t)cell * P + pp);
+                    const r2<R> inM = (refl_r && cell == J - 1) ? ld2(fPr + (size_t)J * P + pp)
+                                                                : ld2(fMr + (size_t)(cell + 1) * P + pp);
+                    const r4<R> pe = ld4(p.psi_edge + (size_t)cell * P + pp);
+                    // fixed part of c (source + time edge), u+ = c+, u- = conj(c-)
+                    R ukr = qd.x + es.x * pe.x, uki = qd.y + es.x * pe.y, uhr = qd.z, uhi = qd.w;
+                    R vkr = qd.x + es.x * pe.z, vki = -(qd.y + es.x * pe.w), vhr = qd.z, vhi = -qd.w;
+                    if (MODE == M_SI) {
+                        // outgoing part of A^{-1} c_fixed (source and time edge only); the
+                        // next sweep's offset adds s (A^{-1} phi^{l+1})_out after the update
+                        yo[r][i][0] = a.pr * uki + a.pi * ukr + a.rr * uhi + a.ri * uhr;
+                        yo[r][i][1] = a.ur * uki + a.ui * ukr + a.vr * uhi + a.vi * uhr;
+                        yo[r][i][2] = a.pr * vkr - a.pi * vki + a.rr * vhr - a.ri * vhi;
+                        yo[r][i][3] = a.ur * vkr - a.ui * vki + a.vr * vhr - a.vi * vhi;
+                        // lagged scattering source s phi^l (b^+/b^- of the SI section)
+                        ukr += fkl; uki += fkr; uhr += fhl; uhi += fhr;
+                        vkr += fkl; vki -= fkr; vhr += fhl; vhi -= fhr;
+                        if (cell == J - 1 && p.bc_right == BC_REFLECT)  // lag for the next sweep
+                            st2(p.refl + pp, ld2(fPr + (size_t)J * P + pp).x, ld2(fPr + (size_t)J * P + pp).y);
+                    }
+                    // incident terms: +mu enters rows 1, 3 (corner L); -mu rows 2, 4 (corner R)
+                    ukr += mw.x * inP.x; uhr += mw.x * inP.y;
+                    vki -= mw.x * inM.x; vhi -= mw.x * inM.y;
+                    R ykr, yki, yhr, yhi, zkr, zki, zhr, zhi;
+                    ainv(a, ukr, uki, uhr, uhi, ykr, yki, yhr, yhi);
+                    ainv(a, vkr, vki, vhr, vhi, zkr, zki, zhr, zhi);
+                    if (MODE == M_OCI) {
+                        yo[r][i][0] = yki; yo[r][i][1] = yhi; yo[r][i][2] = zkr; yo[r][i][3] = zhr;
+                    }
+                    // w (y+ + conj(z)): moments (kL, kR, hL, hR)
+                    const R c0 = mw.y * (ykr + zkr), c1 = mw.y * (yki - zki);
+                    const R c2 = mw.y * (yhr + zhr), c3 = mw.y * (yhi - zhi);
+                    if (PPL == 1) {
+                        s_acc[4 * r + 0] = c0; s_acc[4 * r + 1] = c1; s_acc[4 * r + 2] = c2; s_acc[4 * r + 3] = c3;
+                    } else {
+                        R t;
+                        two_sum(s_acc[4 * r + 0], c0, s_acc[4 * r + 0], t); e_acc[4 * r + 0] += t;
+                        two_sum(s_acc[4 * r + 1], c1, s_acc[4 * r + 1], t); e_acc[4 * r + 1] += t;
+                        two_sum(s_acc[4 * r + 2], c2, s_acc[4 * r + 2], t); e_acc[4 * r + 2] += t;
+                        two_sum(s_acc[4 * r + 3], c3, s_acc[4 * r + 3], t); e_acc[4 * r + 3] += t;
+                    }
+                }
+            }
+        }
+        // ---------------- phase B: moments over the segment's lanes
+        reduce_scatter<LPC, V, COMP>(s_acc, e_acc, lane);
+        // ---------------- phase C: capacitance solve + residual, in double
+        const int base_idx = (V >= LPC) ? NV * ls : (ls % V);
+        const bool owner_lane = (V >= LPC) || (ls < V);
+        R phiR[V];
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            const int gi = base_idx + t;
+            const int row = gi >> 2, comp = gi & 3;
+            const int cell = chunk * CPC + row * SPW + seg;
+            const double r_own = (double)s_acc[t] + (double)e_acc[t];
+            double phi;
+            if (MODE == M_OCI) {
+                double r_par;
+                if constexpr (NV >= 4) r_par = (double)s_acc[t ^ 2] + (double)e_acc[t ^ 2];
+                else if constexpr (NV == 2) r_par = __shfl_xor_sync(FULL, r_own, 1);
+                else r_par = __shfl_xor_sync(FULL, r_own, 2);
+                const int m = cell < J ? __ldg(p.mat + cell) : 0;
+                const kmat K = p.matK[m];
+                phi = comp < 2 ? K.k00 * r_own + K.k01 * r_par : K.k10 * r_par + K.k11 * r_own;
+            } else {
+                phi = r_own;
+            }
+            if (owner_lane && cell < J) {
+                const double old = __ldcg(phr + 4 * (size_t)cell + comp);
+                const double d = phi - old;
+                acc_d2 += d * d;
+                acc_p2 += phi * phi;
+                phw[4 * (size_t)cell + comp] = phi;
+            }
+            phiR[t] = (R)phi;
+        }
+        // ---------------- phase D: every lane of the segment gets phi of its cells
+        all_gather<LPC, V>(phiR, lane);
+        // ---------------- phase E: back-substitution of the outgoing corners
+#pragma unroll
+        for (int r = 0; r < CHUNK; ++r) {
+            const int cell = chunk * CPC + r * SPW + seg;
+            if (cell >= J) continue;
+            const int m = __ldg(p.mat + cell);
+            const R s = ldg2(p.matpar + m).y;
+            const R Fkl = phiR[4 * r] * s, Fkr = phiR[4 * r + 1] * s, Fhl = phiR[4 * r + 2] * s, Fhr = phiR[4 * r + 3] * s;
+#pragma unroll
+            for (int i = 0; i < PPL; ++i) {
+                const int pp = ls + LPC * i;
+                if (pp >= P) continue;
+                const Coef<R> a = load_coef(p.tab, m, P, pp);
+                // +mu: Im(A^{-1} Phi); -mu: Re(A^{-1} conj(Phi))
+                const R ok = yo[r][i][0] + (a.pr * Fkr + a.pi * Fkl + a.rr * Fhr + a.ri * Fhl);
+                const R oh = yo[r][i][1] + (a.ur * Fkr + a.ui * Fkl + a.vr * Fhr + a.vi * Fhl);
+                const R mk = yo[r][i][2] + (a.pr * Fkl + a.pi * Fkr + a.rr * Fhl + a.ri * Fhr);
+                const R mh = yo[r][i][3] + (a.ur * Fkl + a.ui * Fkr + a.vr * Fhl + a.vi * Fhr);
+                if (MODE == M_OCI) {
+                    st2(fPw + (size_t)(cell + 1) * P + pp, ok, oh);
+                    st2(fMw + (size_t)cell * P + pp, mk, mh);
+                } else {
+                    st4(p.g + (size_t)pp * J + cell, ok, oh, mk, mh);
+                }
+            }
+        }
+    }
+    finalize_iteration(acc_d2, acc_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond);
+}
+
+// ---------------------------------------------------------------------------
+// Per-cell passes without reductions (LPC lanes per cell, PPL pairs per lane):
+//   C_COMMIT_OCI / C_COMMIT_SI: if the step is accepted, the end-of-step flux
+//     psi_{k+1/2} of every ordinate and corner, psi = A^{-1}(c + s phi), goes to
+//     psi_edge (multiple balance: it is the next step's psi_{k-1/2}); the next
+//     step's initial iterate (both time moments = psi_{k+1/2} at the faces)
+//     goes to the free face buffer; phi is published.
+//   C_SI_PREP: affine offsets g of the first sweep of a step from phi^(0).
+//   C_GUESS : initial iterate from psi_edge (after set_state or a rejected step).
+// ---------------------------------------------------------------------------
+template <typename R, int LPC, int PPL, int MODE>
+__global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
+{
+    constexpr int SPW = 32 / LPC;
+    const int lane = threadIdx.x & 31;
+    const int seg = lane / LPC, ls = lane % LPC;
+    const int J = p.J, P = p.P;
+    IterState *st = p.st;
+    const int status = st->status, iter = st->iter, base = st->base;
+    bool go = true;
+    int frd = 0, fgs = 0;
+    const double *phi_psi = nullptr, *phi_pub = nullptr;
+    if (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI) {
+        go = iter >= 1 && (status == ST_CONVERGED || (status == ST_MAXITER && p.cfg->commit_unconverged));
+        if (MODE == C_COMMIT_OCI) {
+            frd = (base + iter - 1) & 1;
+            fgs = frd ^ 1;
+            phi_psi = p.phi[iter & 1];
+        } else {
+            frd = base;
+            fgs = base ^ 1;
+            phi_psi = (iter - 1 == 0) ? p.phi0 : p.phi[(iter - 1) & 1];
+        }
+        phi_pub = p.phi[iter & 1];
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->committed = go ? 1 : 0;
+            st->base_next = go ? fgs : base;
+        }
+    } else if (MODE == C_SI_PREP) {
+        frd = base;
+        phi_psi = p.phi0;
+    } else {  // C_GUESS
+        fgs = st->base_next;
+    }
+    if (!go) return;
+    const bool refl_l = MODE == C_COMMIT_OCI && p.bc_left == BC_REFLECT;
+    const bool refl_r = MODE == C_COMMIT_OCI && p.bc_right == BC_REFLECT;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int cell = gw * SPW + seg; cell - seg < J; cell += nwarps * SPW) {
+        if (cell >= J) continue;
+        const int m = __ldg(p.mat + cell);
+        const r4<R> qd = ldg4(p.cellq + cell);
+        const r2<R> es = ldg2(p.matpar + m);
+        R Fkl = 0, Fkr = 0, Fhl = 0, Fhr = 0;
+        if (MODE != C_GUESS) {
+            const double2 a = __ldcg(reinterpret_cast<const double2 *>(phi_psi + 4 * (size_t)cell));
+            const double2 b = __ldcg(reinterpret_cast<const double2 *>(phi_psi + 4 * (size_t)cell) + 1);
+            Fkl = (R)a.x * es.y; Fkr = (R)a.y * es.y; Fhl = (R)b.x * es.y; Fhr = (R)b.y * es.y;
+        }
+#pragma unroll
+        for (int i = 0; i < PPL; ++i) {
+            const int pp = ls + LPC * i;
+            if (pp >= P) continue;
+            const r4<R> pe = ld4(p.psi_edge + (size_t)cell * P + pp);
+            if (MODE == C_GUESS) {
+                st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, pe.y, pe.y);
+                st2(p.faceM[fgs] + (size_t)cell * P + pp, pe.z, pe.z);
+                continue;
+            }
+            const Coef<R> a = load_coef(p.tab, m, P, pp);
+            const R mu = ldg2(p.muw + pp).x;
+            R ukr = qd.x + es.x * pe.x + Fkl, uki = qd.y + es.x * pe.y + Fkr, uhr = qd.z + Fhl, uhi = qd.w + Fhr;
+            R vkr = qd.x + es.x * pe.z + Fkl, vki = -(qd.y + es.x * pe.w) - Fkr, vhr = qd.z + Fhl, vhi = -qd.w - Fhr;
+            if (MODE == C_SI_PREP) {
+                const R ok = a.pr * uki + a.pi * ukr + a.rr * uhi + a.ri * uhr;
+                const R oh = a.ur * uki + a.ui * ukr + a.vr * uhi + a.vi * uhr;
+                const R mk = a.pr * vkr - a.pi * vki + a.rr * vhr - a.ri * vhi;
+                const R mh = a.ur * vkr - a.ui * vki + a.vr * vhr - a.vi * vhi;
+                st4(p.g + (size_t)pp * J + cell, ok, oh, mk, mh);
+                if (cell == J - 1 && p.bc_right == BC_REFLECT) {
+                    // SI lags a reflecting right face: the first sweep sees the
+                    // initial iterate's outgoing +mu flux there.
+                    const r2<R> v = ld2(p.faceP[frd] + (size_t)J * P + pp);
+                    st2(p.refl + pp, v.x, v.y);
+                }
+                continue;
+            }
+            const r2<R> inP = (refl_l && cell == 0) ? ld2(p.faceM[frd] + pp) : ld2(p.faceP[frd] + (size_t)cell * P + pp);
+            const r2<R> inM = (refl_r && cell == J - 1) ? ld2(p.faceP[frd] + (size_t)J * P + pp)
+                                                        : ld2(p.faceM[frd] + (size_t)(cell + 1) * P + pp);
+            ukr += mu * inP.x; uhr += mu * inP.y;
+            vki -= mu * inM.x; vhi -= mu * inM.y;
+            // end-of-step components only (k+1/2): second rows of A^{-1}
+            const R phr_ = a.ur * ukr - a.ui * uki + a.vr * uhr - a.vi * uhi;
+            const R phi_ = a.ur * uki + a.ui * ukr + a.vr * uhi + a.vi * uhr;
+            const R mhr = a.ur * vkr - a.ui * vki + a.vr * vhr - a.vi * vhi;
+            const R mhi = a.ur * vki + a.ui * vkr + a.vr * vhi + a.vi * vhr;
+            // psi+ = (L, R) = (Re, Im); psi- = conj(z): (Re z, -Im z)
+            st4(p.psi_edge + (size_t)cell * P + pp, phr_, phi_, mhr, -mhi);
+            st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, phi_, phi_);
+            st2(p.faceM[fgs] + (size_t)cell * P + pp, mhr, mhr);
+        }
+        if (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI) {
+            for (int c = ls; c < 4; c += LPC) {
+                p.phi_out[4 * (size_t)cell + c] = __ldcg(phi_pub + 4 * (size_t)cell + c);
+                p.phi0[4 * (size_t)cell + c] = __ldcg(phi_pub + 4 * (size_t)cell + 2 + (c & 1));
+            }
+        }
+    }
+}
+
+// Step prologue: reset the iteration state for a new time step.
+static __global__ void k_step_begin(IterState *st)
+{
+    st->iter = 0;
+    st->status = ST_RUNNING;
+    st->arrive = 0u;
+    st->launches = 0;
+    st->base = st->base_next;
+    st->resid = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// SI transport sweep (Sec. "Source Iteration"): for one ordinate, march the
+// cells in the direction of travel.  With the lagged scattering source folded
+// into g, the outgoing corner pair of cell j is an affine map of the incident
+// pair: out = G in + g, G = mu [[Im P, Im Rr], [Im U, Im V]] (the same for
+// +mu and -mu).  One warp per (pair, direction); all lanes carry the chain,
+// lane k stages cell k of each 32-cell batch in shared memory.  A reflecting
+// left face needs the -mu sweep first, so then one warp runs both directions.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void si_stage(const KParams<R> &p, int pp, int dir, int j, bool ok, r4<R> &G, r2<R> &g)
+{
+    if (ok) {
+        const int m = __ldg(p.mat + j);
+        const Coef<R> a = load_coef(p.tab, m, p.P, pp);
+        const R mu = ldg2(p.muw + pp).x;
+        G = r4<R>{mu * a.pi, mu * a.ri, mu * a.ui, mu * a.vi};
+        const r4<R> gg = ld4(p.g + (size_t)pp * p.J + j);
+        g = dir > 0 ? r2<R>{gg.x, gg.y} : r2<R>{gg.z, gg.w};
+    } else {
+        G = r4<R>{0, 0, 0, 0};
+        g = r2<R>{0, 0};
+    }
+}
+
+template <typename R>
+__device__ void si_sweep(const KParams<R> &p, int pp, int dir, int fb, R ink, R inh)
+{
+    __shared__ r4<R> sG[32];
+    __shared__ r2<R> sg[32];
+    __shared__ r2<R> so[32];
+    const int lane = threadIdx.x & 31;
+    const int J = p.J, P = p.P;
+    // cell visited at sweep position t
+    auto cell_at = [&](int t) { return dir > 0 ? t : J - 1 - t; };
+    r4<R> Gn; r2<R> gn;
+    si_stage(p, pp, dir, cell_at(lane), lane < J, Gn, gn);
+    for (int b0 = 0; b0 < J; b0 += 32) {
+        __syncwarp();
+        sG[lane] = Gn;
+        sg[lane] = gn;
+        __syncwarp();
+        const int t1 = b0 + 32 + lane;
+        si_stage(p, pp, dir, cell_at(t1 < J ? t1 : 0), t1 < J, Gn, gn);  // prefetch next batch
+        const int nb = J - b0 < 32 ? J - b0 : 32;
+#pragma unroll 8
+        for (int k = 0; k < nb; ++k) {
+            const r4<R> G = sG[k];
+            const r2<R> g = sg[k];
+            const R ok = G.x * ink + (G.y * inh + g.x);
+            const R oh = G.z * ink + (G.w * inh + g.y);
+            ink = ok;
+            inh = oh;
+            if (lane == 0) so[k] = r2<R>{ok, oh};
+        }
+        __syncwarp();
+        if (lane < nb) {
+            const int j = cell_at(b0 + lane);
+            const r2<R> o = so[lane];
+            if (dir > 0) st2(p.faceP[fb] + (size_t)(j + 1) * P + pp, o.x, o.y);
+            else st2(p.faceM[fb] + (size_t)j * P + pp, o.x, o.y);
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32) k_si_march(const KParams<R> p)
+{
+    IterState *st = p.st;
+    if (*(volatile int *)&st->status != ST_RUNNING) return;
+    const int fb = *(volatile int *)&st->base;
+    const int J = p.J, P = p.P;
+    const bool both = p.bc_left == BC_REFLECT;
+    const int pp = blockIdx.x % P;
+    const int dir = both ? -1 : (blockIdx.x < P ? -1 : 1);
+    if (dir < 0) {
+        // right face: prescribed / vacuum data, or (reflecting) the mirror
+        // flux of the previous iterate, staged in refl by the previous pass;
+        // it is copied into the face slot so later passes read what was used
+        r2<R> in;
+        if (p.bc_right == BC_REFLECT) {
+            in = ld2(p.refl + pp);
+            if ((threadIdx.x & 31) == 0) st2(p.faceM[fb] + (size_t)J * P + pp, in.x, in.y);
+        } else {
+            in = ld2(p.faceM[fb] + (size_t)J * P + pp);
+        }
+        si_sweep(p, pp, -1, fb, in.x, in.y);
+    }
+    if (both) {
+        __syncwarp();
+        const r2<R> v = ld2(p.faceM[fb] + pp);  // this sweep's -mu flux leaving through x = 0
+        if ((threadIdx.x & 31) == 0) st2(p.faceP[fb] + pp, v.x, v.y);
+        __syncwarp();
+        si_sweep(p, pp, 1, fb, v.x, v.y);
+    } else if (dir > 0) {
+        const r2<R> in = ld2(p.faceP[fb] + pp);
+        si_sweep(p, pp, 1, fb, in.x, in.y);
+    }
+}
+
+}  // namespace ocik

@@ -1,0 +1,35 @@
+// Template instantiations of the OCI / SI kernels for R = float.
+#include "oci_kernels.h"
+
+namespace ocik {
+
+template <int LPC, int PPL, int CHUNK>
+static void fill(KernelSet *k)
+{
+    k->cells_oci = (const void *)&k_cells<float, LPC, PPL, CHUNK, M_OCI>;
+    k->cells_si = (const void *)&k_cells<float, LPC, PPL, CHUNK, M_SI>;
+    k->commit_oci = (const void *)&k_percell<float, LPC, PPL, C_COMMIT_OCI>;
+    k->commit_si = (const void *)&k_percell<float, LPC, PPL, C_COMMIT_SI>;
+    k->si_prep = (const void *)&k_percell<float, LPC, PPL, C_SI_PREP>;
+    k->guess = (const void *)&k_percell<float, LPC, PPL, C_GUESS>;
+    k->march = (const void *)&k_si_march<float>;
+    k->cells_per_warp = CHUNK * (32 / LPC);
+    k->cells_per_warp_pc = 32 / LPC;
+}
+
+bool kernel_set_f32(int lpc, int ppl, KernelSet *out)
+{
+    switch (lpc * 16 + ppl) {
+    case 1 * 16 + 1: fill<1, 1, 8>(out); return true;
+    case 2 * 16 + 1: fill<2, 1, 8>(out); return true;
+    case 4 * 16 + 1: fill<4, 1, 8>(out); return true;
+    case 8 * 16 + 1: fill<8, 1, 8>(out); return true;
+    case 16 * 16 + 1: fill<16, 1, 8>(out); return true;
+    case 32 * 16 + 1: fill<32, 1, 8>(out); return true;
+    case 32 * 16 + 2: fill<32, 2, 8>(out); return true;
+    case 32 * 16 + 4: fill<32, 4, 4>(out); return true;
+    default: return false;
+    }
+}
+
+}  // namespace ocik

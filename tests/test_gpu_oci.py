@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+FP64 mode must agree with the oracle to 1e-12 relative (max-norm of the
+difference over the max-norm of the oracle's scalar flux / angular flux), both
+at a fixed iteration count (same algorithm, same iterate) and at convergence
+(same iteration counts).  FP32 mode stores the angular flux and per-ordinate
+blocks in float, so its bound is derived from float rounding: relative error
+of the scalar flux <= 2e-6 at convergence (a few float ulps, amplified by at
+most ~1/(1-c) through the scattering coupling of the test problems).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2305_13555_gb300 as pkg
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 2e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2305_13555_gb300 import build
+    build.build()
+    pkg.load_library()
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _gpu_fixed(prob, method, n_iter, n_steps, precision="fp64"):
+    phis, states = [], []
+    with pkg.Solver(prob, precision=precision) as s:
+        s.set_iteration(0.0, n_iter, commit_unconverged=True)
+        for _ in range(n_steps):
+            rc, st = s.step(method)
+            assert rc == pkg.OCI_ENOTCONV and st["iters"] == n_iter and st["committed"] == 1, (rc, st)
+            phis.append(s.fluxes())
+            states.append(s.get_state())
+    return np.array(phis), states[-1]
+
+
+# (N, J): J spans several warp chunks plus a ragged tail for each lane layout
+LAYOUTS = [(2, 300), (4, 150), (6, 70), (8, 200), (16, 77), (32, 45), (64, 45), (128, 21), (256, 11)]
+BCS = [("vacuum", "vacuum"), ("reflect", "vacuum"), ("incident", "reflect"), ("reflect", "reflect"),
+       ("vacuum", "incident")]
+
+
+@pytest.mark.parametrize("method", ["oci", "si"])
+@pytest.mark.parametrize("N,J", LAYOUTS)
+def test_fixed_iterations_fp64_layouts(method, N, J):
+    prob = workloads.random_small(seed=100 + N, J=J, N=N, bc_left="reflect", bc_right="incident")
+    ref = oracle.run(prob, method, 2, tol=0.0, max_iter=4, commit_unconverged=True)
+    phis, state = _gpu_fixed(prob, method, 4, 2)
+    assert _rel(phis, ref["phi_steps"]) < FP64_TOL
+    assert _rel(state, ref["psi_edge"]) < FP64_TOL
+
+
+@pytest.mark.parametrize("method", ["oci", "si"])
+@pytest.mark.parametrize("bcl,bcr", BCS)
+def test_fixed_iterations_fp64_boundaries(method, bcl, bcr):
+    prob = workloads.random_small(seed=7, J=37, N=8, bc_left=bcl, bc_right=bcr)
+    ref = oracle.run(prob, method, 3, tol=0.0, max_iter=3, commit_unconverged=True)
+    phis, state = _gpu_fixed(prob, method, 3, 3)
+    assert _rel(phis, ref["phi_steps"]) < FP64_TOL
+    assert _rel(state, ref["psi_edge"]) < FP64_TOL
+
+
+@pytest.mark.parametrize("method", ["oci", "si"])
+def test_converged_config1_fp64(method):
+    prob = workloads.config1()
+    ref = oracle.run(prob, method, prob["n_steps"], tol=prob["tol"], max_iter=100000)
+    assert ref["status"] == 0
+    with pkg.Solver(prob, precision="fp64") as s:
+        for k in range(prob["n_steps"]):
+            rc, st = s.step(method)
+            assert rc == pkg.OCI_OK, (rc, st)
+            assert st["iters"] == ref["iters"][k]
+            assert _rel(s.fluxes(), ref["phi_steps"][k]) < FP64_TOL
+        assert _rel(s.get_state(), ref["psi_edge"]) < FP64_TOL
+
+
+@pytest.mark.parametrize("method", ["oci", "si"])
+def test_converged_hetero_fp32_bound(method):
+    prob = workloads.hetero(seed=11, J=3000, N=16, n_steps=3, bc_left="reflect", bc_right="vacuum")
+    ref = oracle.run(prob, method, 3, tol=1e-8, max_iter=100000)
+    assert ref["status"] == 0
+    with pkg.Solver(prob, precision="fp32") as s:
+        for k in range(3):
+            rc, st = s.step(method)
+            assert rc == pkg.OCI_OK, (rc, st)
+            assert abs(st["iters"] - ref["iters"][k]) <= 2
+            assert _rel(s.fluxes(), ref["phi_steps"][k]) < FP32_TOL
+
+
+def test_fixed_iterations_fp32_bound():
+    prob = workloads.random_small(seed=5, J=500, N=64, bc_left="reflect", bc_right="vacuum")
+    ref = oracle.run(prob, "oci", 2, tol=0.0, max_iter=5, commit_unconverged=True)
+    phis, state = _gpu_fixed(prob, "oci", 5, 2, precision="fp32")
+    assert _rel(phis, ref["phi_steps"]) < FP32_TOL
+    assert _rel(state, ref["psi_edge"]) < FP32_TOL
+
+
+def test_full_size_config2_sampled_fp64_and_fp32():
+    """65536 cells, S_64 (the benchmark's launch configuration): three fixed
+    iterations of one step against the oracle on every output."""
+    prob = workloads.config2(N=64, c=0.9, dx=0.1, J=65536, n_steps=1)
+    ref = oracle.run(prob, "oci", 1, tol=0.0, max_iter=3, commit_unconverged=True)
+    phis, state = _gpu_fixed(prob, "oci", 3, 1, "fp64")
+    assert _rel(phis[0], ref["phi_steps"][0]) < FP64_TOL
+    assert _rel(state, ref["psi_edge"]) < FP64_TOL
+    phis, state = _gpu_fixed(prob, "oci", 3, 1, "fp32")
+    assert _rel(phis[0], ref["phi_steps"][0]) < FP32_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-6)])
+def test_infinite_medium_full_size(precision, tol):
+    """Reflecting both faces, uniform source: every cell follows the flat-mode
+    multiple-balance recurrence phi_{n+1/2} = g phi_{n-1/2} + h."""
+    J, N, c, dt = 65536, 64, 0.9, 0.05
+    prob = workloads.homogeneous(J, N, 1.0, c, 0.1, 1.0, dt, 1.0, "reflect", "reflect", tol=1e-13)
+    tau, sa = 1.0 / dt, 1.0 - c
+    den = sa * sa + 2 * sa * tau + 2 * tau * tau
+    g, h = 2 * tau * tau / den, (sa + 2 * tau) / den
+    prev = 0.0
+    with pkg.Solver(prob, precision=precision, tol=1e-13 if precision == "fp64" else 1e-7) as s:
+        for _ in range(4):
+            rc, st = s.step("oci")
+            assert rc == pkg.OCI_OK, (rc, st)
+            nxt = g * prev + h
+            avg = (1.0 + tau * prev - tau * nxt) / sa
+            phi = s.fluxes()
+            assert np.abs(phi[:, 2:] - nxt).max() < tol * nxt
+            assert np.abs(phi[:, :2] - avg).max() < tol * avg
+            prev = nxt
+
+
+def test_not_converged_keeps_state_then_recovers():
+    prob = workloads.config1()
+    with pkg.Solver(prob, precision="fp64") as s:
+        s.set_iteration(1e-14, 2)
+        before = s.fluxes().copy()
+        rc, st = s.step()
+        assert rc == pkg.OCI_ENOTCONV and st["committed"] == 0 and st["iters"] == 2
+        assert np.array_equal(s.fluxes(), before)
+        s.set_iteration(1e-10, 100000)
+        rc, st = s.step()
+        assert rc == pkg.OCI_OK
+    ref = oracle.run(prob, "oci", 1, tol=1e-10)
+    assert st["iters"] == ref["iters"][0]
+
+
+def test_nan_source_reported():
+    prob = workloads.config1()
+    with pkg.Solver(prob, precision="fp32") as s:
+        q = np.array(prob["q"], dtype=float)
+        q[30, 1] = np.nan
+        s.set_source(q)
+        rc, st = s.step()
+        assert rc == pkg.OCI_ENAN and st["committed"] == 0
+
+
+def test_state_roundtrip_and_time_dependent_source():
+    prob = workloads.random_small(seed=3, J=120, N=16, bc_left="vacuum", bc_right="reflect")
+    # oracle: step 1 with q, step 2 with 2q
+    r1 = oracle.run(prob, "oci", 1, tol=1e-12)
+    p2 = dict(prob)
+    p2["q"] = 2.0 * np.asarray(prob["q"])
+    r2 = oracle.run(p2, "oci", 1, tol=1e-12, psi_edge=r1["psi_edge"])
+    with pkg.Solver(prob, precision="fp64", tol=1e-12) as s:
+        s.step()
+        st1 = s.get_state()
+        assert _rel(st1, r1["psi_edge"]) < FP64_TOL
+        s.set_source(p2["q"])
+        s.step()
+        assert _rel(s.fluxes(), r2["phi_steps"][0]) < FP64_TOL
+    # resume from the oracle's state in a fresh handle
+    with pkg.Solver(p2, precision="fp64", tol=1e-12) as s:
+        s.set_state(r1["psi_edge"])
+        s.step()
+        assert _rel(s.fluxes(), r2["phi_steps"][0]) < FP64_TOL
+
+
+def test_steady_state_and_single_cell():
+    prob = workloads.random_small(seed=9, J=1, N=2, bc_left="incident", bc_right="incident")
+    prob["v"] = float("inf")
+    for method in ("oci", "si"):
+        ref = oracle.run(prob, method, 1, tol=1e-14)
+        with pkg.Solver(prob, precision="fp64", tol=1e-14) as s:
+            rc, _ = s.step(method)
+            assert rc == pkg.OCI_OK
+            assert _rel(s.fluxes(), ref["phi_steps"][0]) < FP64_TOL
+
+
+def test_mirror_symmetry_config1_fp32():
+    prob = workloads.config1()
+    with pkg.Solver(prob, precision="fp32", tol=1e-7) as s:
+        for _ in range(3):
+            s.step()
+        ph = s.fluxes()
+    assert np.abs(ph[:, 0] - ph[::-1, 1]).max() < 1e-6 * np.abs(ph).max()
+
+
+def test_torch_stream_and_device_fluxes():
+    import torch
+    prob = workloads.config1()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with pkg.Solver(prob, precision="fp64", stream=stream.cuda_stream) as s:
+            s.step()
+            out = torch.empty((prob["n_cells"], 4), dtype=torch.float64, device="cuda")
+            pkg.oci_fluxes_device(s.h, out.data_ptr())
+            stream.synchronize()
+            assert np.array_equal(out.cpu().numpy(), s.fluxes())
