@@ -5,7 +5,9 @@
 // device-side conditional WHILE node, so the host synchronises once per step.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <complex>
 #include <cstdio>
 #include <cstring>
@@ -102,6 +104,11 @@ struct oci_handle {
     IterState *h_st = nullptr;      // pinned
     IterConfig cfg{};
     int grid_cells = 1, grid_pc = 1;
+    // iteration kernels actually launched (staged TMA variant when available)
+    const void *cells_oci = nullptr, *cells_si = nullptr;
+    int cells_grid = 1, cells_block = 256;
+    unsigned cells_smem = 0;
+    bool staged = false;
     // graphs
     cudaGraph_t graph_oci = nullptr, graph_si = nullptr;
     cudaGraphExec_t exec_oci = nullptr, exec_si = nullptr;
@@ -281,14 +288,14 @@ int upload_boundaries(oci_handle *h, const double *bl, const double *br)
 
 // Kernel node helper.
 int add_kernel(oci_handle *h, cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *dep, int ndep,
-               const void *fn, dim3 grid, dim3 block, void **args)
+               const void *fn, dim3 grid, dim3 block, void **args, unsigned smem = 0)
 {
     cudaGraphNodeParams np{};
     np.type = cudaGraphNodeTypeKernel;
     np.kernel.func = const_cast<void *>(fn);
     np.kernel.gridDim = grid;
     np.kernel.blockDim = block;
-    np.kernel.sharedMemBytes = 0;
+    np.kernel.sharedMemBytes = smem;
     np.kernel.kernelParams = args;
     CK(h, cudaGraphAddNode(node, g, dep, nullptr, ndep, &np));
     return OCI_OK;
@@ -306,6 +313,8 @@ int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout
     KParams<R> loop = make_params<R>(h, 1, cond);
     void *a_plain[] = {&plain};
     void *a_loop[] = {&loop};
+    int n_mat = (int)h->mats.size();
+    void *a_march[] = {&plain, &n_mat};
     IterState *st = h->d_st;
     void *a_st[] = {&st};
     cudaGraphNode_t n_begin, n_prev, n_while, n_commit;
@@ -329,11 +338,13 @@ int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout
     if (si) {
         cudaGraphNode_t b_march;
         const int nm = h->bcl == OCI_BC_REFLECT ? h->P : 2 * h->P;
-        rc = add_kernel(h, body, &b_march, nullptr, 0, h->ks.march, dim3(nm), dim3(32), a_plain);
+        rc = add_kernel(h, body, &b_march, nullptr, 0, h->ks.march, dim3(nm), dim3(32), a_march);
         if (rc) return rc;
-        rc = add_kernel(h, body, &b_cells, &b_march, 1, h->ks.cells_si, dim3(h->grid_cells), dim3(kBlock), a_loop);
+        rc = add_kernel(h, body, &b_cells, &b_march, 1, h->cells_si, dim3(h->cells_grid), dim3(h->cells_block),
+                        a_loop, h->cells_smem);
     } else {
-        rc = add_kernel(h, body, &b_cells, nullptr, 0, h->ks.cells_oci, dim3(h->grid_cells), dim3(kBlock), a_loop);
+        rc = add_kernel(h, body, &b_cells, nullptr, 0, h->cells_oci, dim3(h->cells_grid), dim3(h->cells_block), a_loop,
+                        h->cells_smem);
     }
     if (rc) return rc;
     rc = add_kernel(h, g, &n_commit, &n_while, 1, si ? h->ks.commit_si : h->ks.commit_oci, dim3(h->grid_pc),
@@ -485,6 +496,55 @@ int oci_create(const oci_problem *p, oci_handle **out)
 
     int rc = OCI_OK;
     if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return OCI_ECUDA; }
+    h->cells_oci = h->ks.cells_oci;
+    h->cells_si = h->ks.cells_si;
+    h->cells_grid = h->grid_cells;
+    h->cells_block = kBlock;
+    h->cells_smem = 0;
+    if (h->ks.cells_oci_tma && P == h->lpc * h->ppl && P >= 2 && std::getenv("OCI_NO_TMA") == nullptr) {
+        // staged persistent kernel: as many warps per block as the ring fits in
+        // shared memory (<= 8), one block per SM
+        int sms = 0, smem_optin = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
+            delete h;
+            return OCI_ECUDA;
+        }
+        const unsigned sb = ocik::tma_stage_bytes(h->lpc, h->ppl, P);
+        const unsigned per_warp = (unsigned)h->ks.tma_stages * (sb + 8u) + ocik::kXposeBytes;
+        int warps = (int)((unsigned)(smem_optin - 2048) / per_warp);
+        if (warps > 12) warps = 12;
+        if (warps >= 1) {
+            h->staged = true;
+            h->cells_oci = h->ks.cells_oci_tma;
+            h->cells_si = h->ks.cells_si_tma;
+            h->cells_block = 32 * warps;
+            h->cells_smem = ocik::tma_bar_bytes(h->ks.tma_stages, warps) + (unsigned)warps * ocik::kXposeBytes +
+                            (unsigned)warps * h->ks.tma_stages * sb;
+            // every ring region must start on a 16-byte boundary (bulk copies, vector loads)
+            if ((ocik::tma_bar_bytes(h->ks.tma_stages, warps) % 128u) != 0u || (sb % 16u) != 0u ||
+                h->cells_smem > (unsigned)smem_optin) {
+                delete h;
+                return OCI_EINVAL;
+            }
+            for (const void *fn : {h->cells_oci, h->cells_si})
+                if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->cells_smem) !=
+                    cudaSuccess) {
+                    delete h;
+                    return OCI_ECUDA;
+                }
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->cells_oci, h->cells_block, h->cells_smem) !=
+                    cudaSuccess ||
+                per_sm < 1) {
+                delete h;
+                return OCI_ECUDA;
+            }
+            const int nch = (J + h->ks.cells_per_warp - 1) / h->ks.cells_per_warp;
+            const int want = (nch + warps - 1) / warps;
+            h->cells_grid = std::min(sms * per_sm, want);
+        }
+    }
     // device layout
     const size_t rs = rsize(h), nm = h->mats.size();
     const size_t face = (size_t)(J + 1) * P * 2 * rs;
@@ -499,13 +559,14 @@ int oci_create(const oci_problem *p, oci_handle **out)
                       (size_t)J * sizeof(int),                // mat
                       nm * sizeof(kmat),                      // matK
                       (size_t)J * 32, (size_t)J * 32, (size_t)J * 32, (size_t)J * 32,  // phi[2], phi0, phi_out
-                      (size_t)h->grid_cells * 16,             // partials
+                      (size_t)std::max(h->grid_cells, h->cells_grid) * 16,  // partials
                       sizeof(IterState), sizeof(IterConfig)};
     const int ns = sizeof(sizes) / sizeof(sizes[0]);
     size_t off[32], total = 0;
     for (int i = 0; i < ns; ++i) {
         off[i] = total;
-        total += (sizes[i] + 255) & ~(size_t)255;
+        // 256 B of slack: staged copies round sizes up to 16 B
+        total += (sizes[i] + 256 + 255) & ~(size_t)255;
     }
     if (cudaMalloc(&h->d_base, total) != cudaSuccess) { delete h; return OCI_ENOMEM; }
     h->d_bytes = total;
@@ -659,7 +720,8 @@ int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_la
     void *args[] = {h->prec == OCI_FP64 ? (void *)&pd : (void *)&pf};
     CK(h, cudaEventRecord(h->ev0, h->stream));
     for (int i = 0; i < n_iter; ++i)
-        CK(h, cudaLaunchKernel(h->ks.cells_oci, dim3(h->grid_cells), dim3(kBlock), args, 0, h->stream));
+        CK(h, cudaLaunchKernel(h->cells_oci, dim3(h->cells_grid), dim3(h->cells_block), args, h->cells_smem,
+                               h->stream));
     CK(h, cudaEventRecord(h->ev1, h->stream));
     CK(h, cudaEventSynchronize(h->ev1));
     float ms = 0.f;

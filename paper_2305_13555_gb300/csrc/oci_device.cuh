@@ -42,7 +42,7 @@ template <typename R> struct __align__(16) r4 { R x, y, z, w; };
 struct __align__(16) kmat { double k00, k01, k10, k11; };
 
 enum : int { BC_VACUUM = 0, BC_REFLECT = 1, BC_INCIDENT = 2 };
-enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NAN = 3, ST_GUARD = 4 };
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NAN = 3, ST_GUARD = 4, ST_TIMEOUT = 5 };
 // k_cells modes
 enum : int { M_OCI = 0, M_SI = 1 };
 // k_percell modes
@@ -313,6 +313,9 @@ __device__ __forceinline__ void finalize_iteration(double d2, double p2, double 
             else if (it >= cfg->max_iter) ns = ST_MAXITER;
             st->status = ns;
             if (use_cond) cudaGraphSetConditional(cond, ns == ST_RUNNING ? 1u : 0u);
+        } else if (use_cond) {
+            // stopped during this launch (guard or copy timeout): end the loop
+            cudaGraphSetConditional(cond, 0u);
         }
     }
 }
@@ -330,9 +333,9 @@ __device__ __forceinline__ bool iteration_prologue(const KParams<R> &p, int &ite
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int launches = atomicAdd(&st->launches, 1);
         if (status == ST_RUNNING && launches >= p.cfg->max_iter + 2) {
-            // The loop should have ended: stop it and report.
+            // The loop should have ended: report; this launch's last block
+            // ends the loop.
             st->status = ST_GUARD;
-            if (p.use_cond) cudaGraphSetConditional(p.cond, 0u);
         } else if (status != ST_RUNNING && p.use_cond) {
             cudaGraphSetConditional(p.cond, 0u);
         }
@@ -513,6 +516,333 @@ __global__ void __launch_bounds__(256) k_cells(const KParams<R> p)
 }
 
 // ---------------------------------------------------------------------------
+// Staged variant of k_cells for the bandwidth-bound FP32 path: a persistent
+// grid in which every warp streams its 8-row chunks through a STAGES-deep ring
+// in shared memory.  One lane issues bulk asynchronous copies (TMA,
+// cp.async.bulk) of the chunk's contiguous rows -- incident faces, time-edge
+// flux, source moments, material ids -- completing on a per-stage mbarrier;
+// the warp computes chunk i while chunks i+1 .. i+STAGES-1 are in flight.
+// Every mbarrier wait is bounded: on expiry the kernel records ST_TIMEOUT,
+// drains (again bounded) its own copies and finishes the iteration normally.
+// ---------------------------------------------------------------------------
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx_arrive(unsigned long long *bar, unsigned bytes)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; false when the limit expired.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    for (unsigned it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
+        "l"(src), "r"(bytes), "r"(b)
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__host__ __device__ constexpr unsigned round16(unsigned b) { return (b + 15u) & ~15u; }
+// Barrier region at the start of the dynamic shared memory, padded so that the
+// rings after it (bulk-copy destinations, 16-byte loads) stay 128-byte aligned.
+__host__ __device__ constexpr unsigned tma_bar_bytes(int stages, int warps)
+{
+    return ((unsigned)(8 * stages * warps) + 127u) & ~127u;
+}
+
+// u = c (fixed part + incident), the complex right-hand sides of one ordinate
+// pair, from the staged operands (u+ = c+, u- = conj(c-)).
+template <typename R>
+struct PairRhs { R ukr, uki, uhr, uhi, vkr, vki, vhr, vhi; };
+
+template <typename R>
+__device__ __forceinline__ PairRhs<R> pair_rhs_fixed(const r4<R> &qd, R e, const r4<R> &pe)
+{
+    return {qd.x + e * pe.x, qd.y + e * pe.y, qd.z, qd.w, qd.x + e * pe.z, -(qd.y + e * pe.w), qd.z, -qd.w};
+}
+
+// Per-warp transpose buffer of the staged kernel: 32 lanes x 32 partial sums
+// (8 rows x 4 moments), XOR-swizzled in 16-byte groups (with the lane's low and
+// segment bits) so that the row-wise vector stores and the column-wise scalar
+// loads are bank-conflict free.
+constexpr unsigned kXposeBytes = 32u * 32u * 4u;
+__device__ __forceinline__ int xpose_idx(int l, int v)
+{
+    return 32 * l + 4 * (((v >> 2) ^ l ^ (l >> 3)) & 7) + (v & 3);
+}
+
+template <int LPC, int PPL, int CHUNK, int STAGES, int MODE>
+__global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
+{
+    using R = float;
+    constexpr int SPW = 32 / LPC;
+    constexpr int CPC = CHUNK * SPW;
+    constexpr int V = 4 * CHUNK;           // partial sums per lane
+    constexpr int NOWN = (V * SPW) / 32 > 0 ? (V * SPW) / 32 : 1;  // (segment, value) sums owned per lane
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int seg = lane / LPC, ls = lane % LPC;
+    const int J = p.J, P = p.P;
+
+    int iter, base;
+    if (!iteration_prologue(p, iter, base)) return;
+    const int frd = MODE == M_OCI ? ((base + iter) & 1) : base;
+    const int fwr = frd ^ 1;
+    const double *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
+    double *phw = p.phi[(iter + 1) & 1];
+    const r2<R> *fPr = p.faceP[frd], *fMr = p.faceM[frd];
+    r2<R> *fPw = p.faceP[fwr], *fMw = p.faceM[fwr];
+    const bool refl_l = MODE == M_OCI && p.bc_left == BC_REFLECT;
+    const bool refl_r = MODE == M_OCI && p.bc_right == BC_REFLECT;
+
+    // shared memory: [barriers][per-warp transpose buffers][per-warp rings]
+    const unsigned oP = 0, oM = round16(CPC * P * 8u), oE = 2 * round16(CPC * P * 8u);
+    const unsigned oQ = oE + round16(CPC * P * 16u), oT = oQ + round16(CPC * 16u);
+    const unsigned sbytes = oT + round16(CPC * 4u);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem) + warp * STAGES;
+    float *xp = reinterpret_cast<float *>(smem + tma_bar_bytes(STAGES, wpb) + (size_t)warp * kXposeBytes);
+    unsigned char *ring = smem + tma_bar_bytes(STAGES, wpb) + (size_t)wpb * kXposeBytes + (size_t)warp * STAGES * sbytes;
+    if (lane == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(bars + s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    fence_proxy_async();
+    __syncwarp();
+
+    const int nchunks = (J + CPC - 1) / CPC;
+    const int gw = blockIdx.x * wpb + warp, tw = gridDim.x * wpb;
+    const int nmine = gw < nchunks ? (nchunks - 1 - gw) / tw + 1 : 0;
+    bool ok_all = true;
+    int broke_at = nmine;
+
+    auto issue = [&](int i) {  // lane 0: copies of local chunk i into stage i % STAGES
+        if (i >= nmine) return;
+        const int c0 = (gw + i * tw) * CPC;
+        const int nv = J - c0 < CPC ? J - c0 : CPC;
+        unsigned char *st = ring + (size_t)(i % STAGES) * sbytes;
+        unsigned long long *bar = bars + i % STAGES;
+        const unsigned bF = round16(nv * P * 8u), bE = round16(nv * P * 16u), bQ = nv * 16u, bT = round16(nv * 4u);
+        mbar_expect_tx_arrive(bar, 2 * bF + bE + bQ + bT);
+        bulk_g2s(st + oP, fPr + (size_t)c0 * P, bF, bar);
+        bulk_g2s(st + oM, fMr + (size_t)(c0 + 1) * P, bF, bar);
+        bulk_g2s(st + oE, p.psi_edge + (size_t)c0 * P, bE, bar);
+        bulk_g2s(st + oQ, p.cellq + c0, bQ, bar);
+        bulk_g2s(st + oT, p.mat + c0, bT, bar);
+    };
+    if (lane == 0)
+        for (int i = 0; i < STAGES - 1; ++i) issue(i);
+
+    // pair constants and a per-lane cache of the material coefficients
+    r2<R> mw[PPL];
+#pragma unroll
+    for (int t = 0; t < PPL; ++t) mw[t] = (ls + LPC * t < P) ? ldg2(p.muw + ls + LPC * t) : r2<R>{0, 0};
+    int mc = -1;
+    Coef<R> ac[PPL];
+    R ce = 0, cs = 0;
+    auto coefs = [&](int m) {
+        if (m != mc) {
+            mc = m;
+            const r2<R> es = ldg2(p.matpar + m);
+            ce = es.x;
+            cs = es.y;
+#pragma unroll
+            for (int t = 0; t < PPL; ++t) {
+                const int pp = ls + LPC * t;
+                if (pp < P) ac[t] = load_coef(p.tab, m, P, pp);
+            }
+        }
+    };
+
+    double acc_d2 = 0.0, acc_p2 = 0.0;
+    for (int i = 0; i < nmine; ++i) {
+        if (lane == 0) {
+            fence_proxy_async();
+            issue(i + STAGES - 1);
+        }
+        const int chunk = gw + i * tw;
+        const unsigned char *st = ring + (size_t)(i % STAGES) * sbytes;
+        if (!mbar_wait(bars + i % STAGES, (unsigned)(i / STAGES) & 1u)) {
+            ok_all = false;
+            broke_at = i;
+            break;
+        }
+        const r2<R> *sP = reinterpret_cast<const r2<R> *>(st + oP);
+        const r2<R> *sM = reinterpret_cast<const r2<R> *>(st + oM);
+        const r4<R> *sE = reinterpret_cast<const r4<R> *>(st + oE);
+        const r4<R> *sQ = reinterpret_cast<const r4<R> *>(st + oQ);
+        const int *sT = reinterpret_cast<const int *>(st + oT);
+        // ---------------- phase A: y = A^{-1} c per ordinate pair; lane partials
+        // of the moments w (y+ + conj(y-)) go to the transpose buffer
+#pragma unroll
+        for (int r = 0; r < CHUNK; ++r) {
+            const int cl = r * SPW + seg;
+            const int cell = chunk * CPC + cl;
+            R m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+            if (cell < J) {
+                coefs(sT[cl]);
+                const r4<R> qd = sQ[cl];
+                R fkl = 0, fkr = 0, fhl = 0, fhr = 0;
+                if (MODE == M_SI) {
+                    const double2 a = __ldcg(reinterpret_cast<const double2 *>(phr + 4 * (size_t)cell));
+                    const double2 b = __ldcg(reinterpret_cast<const double2 *>(phr + 4 * (size_t)cell) + 1);
+                    fkl = (R)a.x * cs; fkr = (R)a.y * cs; fhl = (R)b.x * cs; fhr = (R)b.y * cs;
+                }
+#pragma unroll
+                for (int t = 0; t < PPL; ++t) {
+                    const int pp = ls + LPC * t;
+                    if (pp >= P) continue;
+                    const Coef<R> &a = ac[t];
+                    const r2<R> inP = (refl_l && cell == 0) ? ld2(fMr + pp) : sP[cl * P + pp];
+                    const r2<R> inM = (refl_r && cell == J - 1) ? ld2(fPr + (size_t)J * P + pp) : sM[cl * P + pp];
+                    PairRhs<R> u = pair_rhs_fixed(qd, ce, sE[cl * P + pp]);
+                    if (MODE == M_SI) {
+                        u.ukr += fkl; u.uki += fkr; u.uhr += fhl; u.uhi += fhr;
+                        u.vkr += fkl; u.vki -= fkr; u.vhr += fhl; u.vhi -= fhr;
+                        if (cell == J - 1 && p.bc_right == BC_REFLECT)
+                            st2(p.refl + pp, ld2(fPr + (size_t)J * P + pp).x, ld2(fPr + (size_t)J * P + pp).y);
+                    }
+                    u.ukr += mw[t].x * inP.x; u.uhr += mw[t].x * inP.y;
+                    u.vki -= mw[t].x * inM.x; u.vhi -= mw[t].x * inM.y;
+                    R ykr, yki, yhr, yhi, zkr, zki, zhr, zhi;
+                    ainv(a, u.ukr, u.uki, u.uhr, u.uhi, ykr, yki, yhr, yhi);
+                    ainv(a, u.vkr, u.vki, u.vhr, u.vhi, zkr, zki, zhr, zhi);
+                    m0 += mw[t].y * (ykr + zkr); m1 += mw[t].y * (yki - zki);
+                    m2 += mw[t].y * (yhr + zhr); m3 += mw[t].y * (yhi - zhi);
+                }
+            }
+            *reinterpret_cast<float4 *>(xp + xpose_idx(lane, 4 * r)) = make_float4(m0, m1, m2, m3);
+        }
+        __syncwarp();
+        // ---------------- phase B: each lane sums the LPC lane partials of the
+        // (segment, moment) values it owns, compensated (Kahan)
+        float own_s[NOWN], own_c[NOWN];
+#pragma unroll
+        for (int k = 0; k < NOWN; ++k) {
+            const int f = lane * NOWN + k;
+            const int g = f / V, v = f % V;  // segment and value index (row * 4 + moment)
+            float sum = 0.f, cmp = 0.f;
+            if (g < SPW) {
+#pragma unroll
+                for (int q = 0; q < LPC; ++q) {
+                    const float x = xp[xpose_idx(g * LPC + q, v)];
+                    const float y = __fsub_rn(x, cmp);
+                    const float t = __fadd_rn(sum, y);
+                    cmp = __fsub_rn(__fsub_rn(t, sum), y);
+                    sum = t;
+                }
+            }
+            own_s[k] = sum;
+            own_c[k] = cmp;
+        }
+        __syncwarp();
+        // ---------------- phase C: capacitance solve + residual, in double
+#pragma unroll
+        for (int k = 0; k < NOWN; ++k) {
+            const int f = lane * NOWN + k;
+            const int g = f / V, v = f % V;
+            const int row = v >> 2, comp = v & 3;
+            const int cell = chunk * CPC + row * SPW + g;
+            const double r_own = (double)own_s[k] - (double)own_c[k];
+            double phi;
+            if (MODE == M_OCI) {
+                double r_par;
+                if constexpr (NOWN >= 4) r_par = (double)own_s[k ^ 2] - (double)own_c[k ^ 2];
+                else if constexpr (NOWN == 2) r_par = __shfl_xor_sync(FULL, r_own, 1);
+                else r_par = __shfl_xor_sync(FULL, r_own, 2);
+                const int m = (g < SPW && cell < J) ? sT[row * SPW + g] : 0;
+                const kmat K = p.matK[m];
+                phi = comp < 2 ? K.k00 * r_own + K.k01 * r_par : K.k10 * r_par + K.k11 * r_own;
+            } else {
+                phi = r_own;
+            }
+            if (g < SPW && cell < J) {
+                const double old = __ldcg(phr + 4 * (size_t)cell + comp);
+                const double d = phi - old;
+                acc_d2 += d * d;
+                acc_p2 += phi * phi;
+                phw[4 * (size_t)cell + comp] = phi;
+                xp[g * V + v] = (float)phi;  // phi of (segment g, value v) for phase D
+            }
+        }
+        __syncwarp();
+        // ---------------- phase D/E: outgoing corners from the staged operands
+#pragma unroll
+        for (int r = 0; r < CHUNK; ++r) {
+            const int cl = r * SPW + seg;
+            const int cell = chunk * CPC + cl;
+            if (cell >= J) continue;
+            coefs(sT[cl]);
+            const r4<R> qd = sQ[cl];
+            const float4 F = *reinterpret_cast<const float4 *>(xp + seg * V + 4 * r);
+            const R Fkl = F.x * cs, Fkr = F.y * cs, Fhl = F.z * cs, Fhr = F.w * cs;
+#pragma unroll
+            for (int t = 0; t < PPL; ++t) {
+                const int pp = ls + LPC * t;
+                if (pp >= P) continue;
+                const Coef<R> &a = ac[t];
+                PairRhs<R> u = pair_rhs_fixed(qd, ce, sE[cl * P + pp]);
+                if (MODE == M_OCI) {
+                    const r2<R> inP = (refl_l && cell == 0) ? ld2(fMr + pp) : sP[cl * P + pp];
+                    const r2<R> inM = (refl_r && cell == J - 1) ? ld2(fPr + (size_t)J * P + pp) : sM[cl * P + pp];
+                    u.ukr += mw[t].x * inP.x; u.uhr += mw[t].x * inP.y;
+                    u.vki -= mw[t].x * inM.x; u.vhi -= mw[t].x * inM.y;
+                }
+                // +mu: Im(A^{-1}(u + s Phi)); -mu: Re(A^{-1}(u + s conj(Phi)))
+                const R uk_i = u.uki + Fkr, uk_r = u.ukr + Fkl, uh_i = u.uhi + Fhr, uh_r = u.uhr + Fhl;
+                const R vk_r = u.vkr + Fkl, vk_i = u.vki - Fkr, vh_r = u.vhr + Fhl, vh_i = u.vhi - Fhr;
+                const R ok = a.pr * uk_i + a.pi * uk_r + a.rr * uh_i + a.ri * uh_r;
+                const R oh = a.ur * uk_i + a.ui * uk_r + a.vr * uh_i + a.vi * uh_r;
+                const R mk = a.pr * vk_r - a.pi * vk_i + a.rr * vh_r - a.ri * vh_i;
+                const R mh = a.ur * vk_r - a.ui * vk_i + a.vr * vh_r - a.vi * vh_i;
+                if (MODE == M_OCI) {
+                    st2(fPw + (size_t)(cell + 1) * P + pp, ok, oh);
+                    st2(fMw + (size_t)cell * P + pp, mk, mh);
+                } else {
+                    st4(p.g + (size_t)pp * J + cell, ok, oh, mk, mh);
+                }
+            }
+        }
+        __syncwarp();  // stage i and the transpose buffer fully read
+    }
+    if (!ok_all) {
+        // a copy never completed: record it and wait (bounded) for this warp's
+        // outstanding copies before the block's shared memory is released
+        if (lane == 0) atomicExch(&p.st->status, ST_TIMEOUT);
+        const int last = broke_at + STAGES - 1 < nmine ? broke_at + STAGES - 1 : nmine;
+        for (int k = broke_at; k < last; ++k) (void)mbar_wait(bars + k % STAGES, (unsigned)(k / STAGES) & 1u);
+    }
+    finalize_iteration(acc_d2, acc_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond);
+}
+
+// ---------------------------------------------------------------------------
 // Per-cell passes without reductions (LPC lanes per cell, PPL pairs per lane):
 //   C_COMMIT_OCI / C_COMMIT_SI: if the step is accepted, the end-of-step flux
 //     psi_{k+1/2} of every ordinate and corner, psi = A^{-1}(c + s phi), goes to
@@ -640,76 +970,151 @@ static __global__ void k_step_begin(IterState *st)
 // cells in the direction of travel.  With the lagged scattering source folded
 // into g, the outgoing corner pair of cell j is an affine map of the incident
 // pair: out = G in + g, G = mu [[Im P, Im Rr], [Im U, Im V]] (the same for
-// +mu and -mu).  One warp per (pair, direction); all lanes carry the chain,
-// lane k stages cell k of each 32-cell batch in shared memory.  A reflecting
-// left face needs the -mu sweep first, so then one warp runs both directions.
+// +mu and -mu).  One warp per (pair, direction): the pair's G for every
+// material sits in shared memory, the per-cell material ids and offsets g
+// stream through a SI_NB-batch cp.async ring (32 cells per batch, one cell per
+// lane), and lane 0 carries the dependent chain.  A reflecting left face needs
+// the -mu sweep first, so then one warp runs both directions.
 // ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ void si_stage(const KParams<R> &p, int pp, int dir, int j, bool ok, r4<R> &G, r2<R> &g)
+constexpr int SI_NB = 16;                 // ring depth in 32-cell batches
+constexpr int SI_SMAT_BYTES = 32768;      // shared-memory table budget
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 {
-    if (ok) {
-        const int m = __ldg(p.mat + j);
-        const Coef<R> a = load_coef(p.tab, m, p.P, pp);
-        const R mu = ldg2(p.muw + pp).x;
-        G = r4<R>{mu * a.pi, mu * a.ri, mu * a.ui, mu * a.vi};
-        const r4<R> gg = ld4(p.g + (size_t)pp * p.J + j);
-        g = dir > 0 ? r2<R>{gg.x, gg.y} : r2<R>{gg.z, gg.w};
-    } else {
-        G = r4<R>{0, 0, 0, 0};
-        g = r2<R>{0, 0};
-    }
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename R>
+__device__ __forceinline__ void cp_async_r2(r2<R> *smem, const r2<R> *gmem)
+{
+    if constexpr (sizeof(R) == 4) cp_async8(smem, gmem);
+    else cp_async16(smem, gmem);
 }
 
 template <typename R>
-__device__ void si_sweep(const KParams<R> &p, int pp, int dir, int fb, R ink, R inh)
+struct SiShared {
+    static constexpr int SMAT = SI_SMAT_BYTES / (int)sizeof(r4<R>);
+    r4<R> G[SMAT];                 // per material: mu (Im P, Im Rr, Im U, Im V)
+    int mat[SI_NB][32];
+    r2<R> g[SI_NB][32];
+    r4<R> Gc[32];                  // G of the current batch's cells
+    r2<R> out[32];
+};
+
+template <typename R>
+__device__ __forceinline__ r4<R> si_G(const KParams<R> &p, const SiShared<R> &sh, int m, int pp, bool in_smem)
 {
-    __shared__ r4<R> sG[32];
-    __shared__ r2<R> sg[32];
-    __shared__ r2<R> so[32];
+    if (in_smem) return sh.G[m];
+    const Coef<R> a = load_coef(p.tab, m, p.P, pp);
+    const R mu = ldg2(p.muw + pp).x;
+    return r4<R>{mu * a.pi, mu * a.ri, mu * a.ui, mu * a.vi};
+}
+
+template <typename R>
+__device__ void si_sweep(const KParams<R> &p, SiShared<R> &sh, int pp, int dir, int fb, R ink, R inh, bool in_smem)
+{
     const int lane = threadIdx.x & 31;
     const int J = p.J, P = p.P;
+    const int nb = (J + 31) / 32;
     // cell visited at sweep position t
     auto cell_at = [&](int t) { return dir > 0 ? t : J - 1 - t; };
-    r4<R> Gn; r2<R> gn;
-    si_stage(p, pp, dir, cell_at(lane), lane < J, Gn, gn);
-    for (int b0 = 0; b0 < J; b0 += 32) {
+    auto issue = [&](int b) {
+        const int t = 32 * b + lane;
+        if (b < nb && t < J) {
+            const int j = cell_at(t);
+            const int slot = b % SI_NB;
+            cp_async4(&sh.mat[slot][lane], p.mat + j);
+            const r2<R> *src = reinterpret_cast<const r2<R> *>(p.g + (size_t)pp * J + j) + (dir > 0 ? 0 : 1);
+            cp_async_r2(&sh.g[slot][lane], src);
+        }
+        cp_async_commit();
+    };
+#pragma unroll 1
+    for (int b = 0; b < SI_NB - 1; ++b) issue(b);
+#pragma unroll 1
+    for (int b = 0; b < nb; ++b) {
+        issue(b + SI_NB - 1);
+        cp_async_wait<SI_NB - 1>();
         __syncwarp();
-        sG[lane] = Gn;
-        sg[lane] = gn;
+        const int slot = b % SI_NB;
+        const int n = J - 32 * b < 32 ? J - 32 * b : 32;
+        if (lane < n) sh.Gc[lane] = si_G(p, sh, sh.mat[slot][lane], pp, in_smem);
         __syncwarp();
-        const int t1 = b0 + 32 + lane;
-        si_stage(p, pp, dir, cell_at(t1 < J ? t1 : 0), t1 < J, Gn, gn);  // prefetch next batch
-        const int nb = J - b0 < 32 ? J - b0 : 32;
-#pragma unroll 8
-        for (int k = 0; k < nb; ++k) {
-            const r4<R> G = sG[k];
-            const r2<R> g = sg[k];
-            const R ok = G.x * ink + (G.y * inh + g.x);
-            const R oh = G.z * ink + (G.w * inh + g.y);
-            ink = ok;
-            inh = oh;
-            if (lane == 0) so[k] = r2<R>{ok, oh};
+        if (lane == 0) {
+            const r4<R> *Gc = sh.Gc;
+            const r2<R> *gs = sh.g[slot];
+            r2<R> *o = sh.out;
+            // groups of 8 cells: all operands of a group are read before its
+            // dependent chain runs and before its results are stored
+#pragma unroll 1
+            for (int k0 = 0; k0 < n; k0 += 8) {
+                r4<R> G[8];
+                r2<R> g[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = k0 + u < n ? k0 + u : n - 1;
+                    G[u] = Gc[k];
+                    g[u] = gs[k];
+                }
+                R ok[8], oh[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    ok[u] = G[u].x * ink + (G[u].y * inh + g[u].x);
+                    oh[u] = G[u].z * ink + (G[u].w * inh + g[u].y);
+                    if (k0 + u < n) { ink = ok[u]; inh = oh[u]; }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (k0 + u < n) o[k0 + u] = r2<R>{ok[u], oh[u]};
+            }
         }
         __syncwarp();
-        if (lane < nb) {
-            const int j = cell_at(b0 + lane);
-            const r2<R> o = so[lane];
+        if (lane < n) {
+            const int j = cell_at(32 * b + lane);
+            const r2<R> o = sh.out[lane];
             if (dir > 0) st2(p.faceP[fb] + (size_t)(j + 1) * P + pp, o.x, o.y);
             else st2(p.faceM[fb] + (size_t)j * P + pp, o.x, o.y);
         }
+        __syncwarp();
     }
+    cp_async_wait<0>();
+    __syncwarp();
 }
 
 template <typename R>
-__global__ void __launch_bounds__(32) k_si_march(const KParams<R> p)
+__global__ void __launch_bounds__(32) k_si_march(const KParams<R> p, int n_mat)
 {
+    __shared__ SiShared<R> sh;
     IterState *st = p.st;
     if (*(volatile int *)&st->status != ST_RUNNING) return;
     const int fb = *(volatile int *)&st->base;
     const int J = p.J, P = p.P;
+    const int lane = threadIdx.x & 31;
     const bool both = p.bc_left == BC_REFLECT;
     const int pp = blockIdx.x % P;
     const int dir = both ? -1 : (blockIdx.x < P ? -1 : 1);
+    const bool in_smem = n_mat <= SiShared<R>::SMAT;
+    if (in_smem) {
+        const R mu = ldg2(p.muw + pp).x;
+        for (int m = lane; m < n_mat; m += 32) {
+            const Coef<R> a = load_coef(p.tab, m, P, pp);
+            sh.G[m] = r4<R>{mu * a.pi, mu * a.ri, mu * a.ui, mu * a.vi};
+        }
+    }
+    __syncwarp();
     if (dir < 0) {
         // right face: prescribed / vacuum data, or (reflecting) the mirror
         // flux of the previous iterate, staged in refl by the previous pass;
@@ -717,21 +1122,21 @@ __global__ void __launch_bounds__(32) k_si_march(const KParams<R> p)
         r2<R> in;
         if (p.bc_right == BC_REFLECT) {
             in = ld2(p.refl + pp);
-            if ((threadIdx.x & 31) == 0) st2(p.faceM[fb] + (size_t)J * P + pp, in.x, in.y);
+            if (lane == 0) st2(p.faceM[fb] + (size_t)J * P + pp, in.x, in.y);
         } else {
             in = ld2(p.faceM[fb] + (size_t)J * P + pp);
         }
-        si_sweep(p, pp, -1, fb, in.x, in.y);
+        si_sweep(p, sh, pp, -1, fb, in.x, in.y, in_smem);
     }
     if (both) {
         __syncwarp();
         const r2<R> v = ld2(p.faceM[fb] + pp);  // this sweep's -mu flux leaving through x = 0
-        if ((threadIdx.x & 31) == 0) st2(p.faceP[fb] + pp, v.x, v.y);
         __syncwarp();
-        si_sweep(p, pp, 1, fb, v.x, v.y);
+        if (lane == 0) st2(p.faceP[fb] + pp, v.x, v.y);
+        si_sweep(p, sh, pp, 1, fb, v.x, v.y, in_smem);
     } else if (dir > 0) {
         const r2<R> in = ld2(p.faceP[fb] + pp);
-        si_sweep(p, pp, 1, fb, in.x, in.y);
+        si_sweep(p, sh, pp, 1, fb, in.x, in.y, in_smem);
     }
 }
 

@@ -13,12 +13,17 @@ struct KernelSet {
     const void *si_prep;     // k_percell<C_SI_PREP>
     const void *guess;       // k_percell<C_GUESS>
     const void *march;       // k_si_march
+    const void *cells_oci_tma;  // k_cells_tma<M_OCI> (FP32, even P) or nullptr
+    const void *cells_si_tma;   // k_cells_tma<M_SI>
+    int tma_stages;             // ring depth of the staged kernels
     int cells_per_warp;      // cells handled by one warp pass of k_cells (CHUNK * 32 / LPC)
     int cells_per_warp_pc;   // cells per warp of k_percell (32 / LPC)
 };
 
 // Returns false if (lpc, ppl) has no instantiation.
 bool kernel_set_f32(int lpc, int ppl, KernelSet *out);
+// Shared-memory bytes per stage of the staged FP32 kernels for P pairs.
+unsigned tma_stage_bytes(int lpc, int ppl, int P);
 bool kernel_set_f64(int lpc, int ppl, KernelSet *out);
 
 }  // namespace ocik

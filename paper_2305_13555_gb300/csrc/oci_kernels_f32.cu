@@ -3,6 +3,8 @@
 
 namespace ocik {
 
+constexpr int kStages = 2;
+
 template <int LPC, int PPL, int CHUNK>
 static void fill(KernelSet *k)
 {
@@ -13,6 +15,14 @@ static void fill(KernelSet *k)
     k->si_prep = (const void *)&k_percell<float, LPC, PPL, C_SI_PREP>;
     k->guess = (const void *)&k_percell<float, LPC, PPL, C_GUESS>;
     k->march = (const void *)&k_si_march<float>;
+    k->cells_oci_tma = nullptr;
+    k->cells_si_tma = nullptr;
+    k->tma_stages = 0;
+    if constexpr (LPC >= 2) {
+        k->cells_oci_tma = (const void *)&k_cells_tma<LPC, PPL, CHUNK, kStages, M_OCI>;
+        k->cells_si_tma = (const void *)&k_cells_tma<LPC, PPL, CHUNK, kStages, M_SI>;
+        k->tma_stages = kStages;
+    }
     k->cells_per_warp = CHUNK * (32 / LPC);
     k->cells_per_warp_pc = 32 / LPC;
 }
@@ -30,6 +40,13 @@ bool kernel_set_f32(int lpc, int ppl, KernelSet *out)
     case 32 * 16 + 4: fill<32, 4, 4>(out); return true;
     default: return false;
     }
+}
+
+unsigned tma_stage_bytes(int lpc, int ppl, int P)
+{
+    const int chunk = ppl >= 4 ? 4 : 8;
+    const unsigned cpc = (unsigned)(chunk * (32 / lpc));
+    return round16(cpc * P * 8u) * 2u + round16(cpc * P * 16u) + round16(cpc * 16u) + round16(cpc * 4u);
 }
 
 }  // namespace ocik

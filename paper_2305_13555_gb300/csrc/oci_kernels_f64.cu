@@ -13,6 +13,9 @@ static void fill(KernelSet *k)
     k->si_prep = (const void *)&k_percell<double, LPC, PPL, C_SI_PREP>;
     k->guess = (const void *)&k_percell<double, LPC, PPL, C_GUESS>;
     k->march = (const void *)&k_si_march<double>;
+    k->cells_oci_tma = nullptr;
+    k->cells_si_tma = nullptr;
+    k->tma_stages = 0;
     k->cells_per_warp = CHUNK * (32 / LPC);
     k->cells_per_warp_pc = 32 / LPC;
 }

@@ -216,3 +216,17 @@ def test_torch_stream_and_device_fluxes():
             pkg.oci_fluxes_device(s.h, out.data_ptr())
             stream.synchronize()
             assert np.array_equal(out.cpu().numpy(), s.fluxes())
+
+
+@pytest.mark.parametrize("N,J", [(4, 333), (16, 1000), (32, 515), (64, 2049), (128, 300)])
+def test_staged_kernel_matches_unstaged(N, J, monkeypatch):
+    """The TMA-staged persistent FP32 kernel and the plain one compute the same
+    iterates up to float rounding order (the staged back-substitution forms
+    A^{-1}(u + s phi) in one pass), and both match the oracle."""
+    prob = workloads.random_small(seed=40 + N, J=J, N=N, bc_left="reflect", bc_right="reflect")
+    ref = oracle.run(prob, "oci", 2, tol=0.0, max_iter=4, commit_unconverged=True)
+    a = _gpu_fixed(prob, "oci", 4, 2, precision="fp32")
+    monkeypatch.setenv("OCI_NO_TMA", "1")
+    b = _gpu_fixed(prob, "oci", 4, 2, precision="fp32")
+    assert _rel(a[0], b[0]) < 1e-6 and _rel(a[1], b[1]) < 1e-6
+    assert _rel(a[0], ref["phi_steps"]) < FP32_TOL and _rel(b[0], ref["phi_steps"]) < FP32_TOL
