@@ -98,6 +98,7 @@ struct oci_handle {
          *refl = nullptr;
     int *d_mat = nullptr;
     kmat *d_matK = nullptr;
+    void *d_matKf = nullptr;        // FP32 mode: capacitance as double-float pairs
     double *phi[2] = {nullptr, nullptr}, *phi0 = nullptr, *phi_out = nullptr, *partials = nullptr;
     IterState *d_st = nullptr;
     IterConfig *d_cfg = nullptr;
@@ -156,13 +157,14 @@ KParams<R> make_params(const oci_handle *h, int use_cond, cudaGraphConditionalHa
     for (int b = 0; b < 2; ++b) {
         p.faceP[b] = (r2<R> *)h->faceP[b];
         p.faceM[b] = (r2<R> *)h->faceM[b];
-        p.phi[b] = h->phi[b];
+        p.phi[b] = (ocik::phi_t<R> *)h->phi[b];
     }
     p.psi_edge = (r4<R> *)h->psi_edge;
     p.g = (r4<R> *)h->g;
     p.refl = (r2<R> *)h->refl;
-    p.phi0 = h->phi0;
+    p.phi0 = (ocik::phi_t<R> *)h->phi0;
     p.phi_out = h->phi_out;
+    p.matKf = (const float4 *)h->d_matKf;
     p.partials = h->partials;
     p.st = h->d_st;
     p.cfg = h->d_cfg;
@@ -210,7 +212,18 @@ int load_state(oci_handle *h, const double *psi)
     }
     int rc = upload_real(h, h->psi_edge, pe);
     if (rc) return rc;
-    CK(h, cudaMemcpyAsync(h->phi0, ph0.data(), ph0.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    if (h->prec == OCI_FP32) {
+        // double-float iterate storage: (h, l) with h = fl(x), l = fl(x - h)
+        std::vector<float> f(ph0.size() * 2);
+        for (size_t i = 0; i < ph0.size(); ++i) {
+            f[2 * i] = (float)ph0[i];
+            f[2 * i + 1] = (float)(ph0[i] - (double)f[2 * i]);
+        }
+        CK(h, cudaMemcpyAsync(h->phi0, f.data(), f.size() * 4, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    } else {
+        CK(h, cudaMemcpyAsync(h->phi0, ph0.data(), ph0.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    }
     CK(h, cudaMemcpyAsync(h->phi_out, ph0.data(), ph0.size() * 8, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     h->guess_valid = false;
@@ -266,6 +279,17 @@ int build_tables(oci_handle *h)
     if (!rc) rc = upload_real(h, h->muw, muw);
     if (rc) return rc;
     CK(h, cudaMemcpy(h->d_matK, K.data(), sizeof(kmat) * nm, cudaMemcpyHostToDevice));
+    {
+        std::vector<float> kf((size_t)nm * 8);
+        for (int m = 0; m < nm; ++m) {
+            const double k[4] = {K[m].k00, K[m].k01, K[m].k10, K[m].k11};
+            for (int i = 0; i < 4; ++i) {
+                kf[(size_t)m * 8 + 2 * i] = (float)k[i];
+                kf[(size_t)m * 8 + 2 * i + 1] = (float)(k[i] - (double)(float)k[i]);
+            }
+        }
+        CK(h, cudaMemcpy(h->d_matKf, kf.data(), sizeof(float) * kf.size(), cudaMemcpyHostToDevice));
+    }
     CK(h, cudaMemcpy(h->d_mat, h->mat.data(), sizeof(int) * h->J, cudaMemcpyHostToDevice));
     return OCI_OK;
 }
@@ -558,6 +582,7 @@ int oci_create(const oci_problem *p, oci_handle **out)
                       (size_t)P * 2 * rs,                     // refl
                       (size_t)J * sizeof(int),                // mat
                       nm * sizeof(kmat),                      // matK
+                      nm * 32,                                // matKf
                       (size_t)J * 32, (size_t)J * 32, (size_t)J * 32, (size_t)J * 32,  // phi[2], phi0, phi_out
                       (size_t)std::max(h->grid_cells, h->cells_grid) * 16,  // partials
                       sizeof(IterState), sizeof(IterConfig)};
@@ -575,11 +600,12 @@ int oci_create(const oci_problem *p, oci_handle **out)
     h->psi_edge = b + off[4]; h->g = b + off[5]; h->cellq = b + off[6]; h->tab = b + off[7];
     h->matpar = b + off[8]; h->muw = b + off[9]; h->refl = b + off[10]; h->d_mat = (int *)(b + off[11]);
     h->d_matK = (kmat *)(b + off[12]);
-    h->phi[0] = (double *)(b + off[13]); h->phi[1] = (double *)(b + off[14]);
-    h->phi0 = (double *)(b + off[15]); h->phi_out = (double *)(b + off[16]);
-    h->partials = (double *)(b + off[17]);
-    h->d_st = (IterState *)(b + off[18]);
-    h->d_cfg = (IterConfig *)(b + off[19]);
+    h->d_matKf = b + off[13];
+    h->phi[0] = (double *)(b + off[14]); h->phi[1] = (double *)(b + off[15]);
+    h->phi0 = (double *)(b + off[16]); h->phi_out = (double *)(b + off[17]);
+    h->partials = (double *)(b + off[18]);
+    h->d_st = (IterState *)(b + off[19]);
+    h->d_cfg = (IterConfig *)(b + off[20]);
     if (cudaMallocHost(&h->h_st, sizeof(IterState)) != cudaSuccess) { oci_destroy(h); return OCI_ENOMEM; }
     if (cudaMemsetAsync(h->d_base, 0, total, h->stream) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {

@@ -14,7 +14,8 @@
 //   mat[j]           int material id; tab[m][p] = complex entries of A_{+mu}^{-1};
 //                        matpar[m] = (e = dx/(2 v dt), s = dx Sigma_s / 4);
 //                        matK[m] = (I - s M)^{-1} in double (Woodbury capacitance)
-//   phi[2][j][4]     double scalar-flux moments, ping-pong over iterations
+//   phi[2][j][4]     scalar-flux moment iterates, ping-pong (double in FP64
+//                        mode, double-float (h, l) pairs in FP32 mode)
 //   g[p][j]          r4  SI affine offsets (pair-major for the march)
 //   refl[p]          r2  SI: +mu flux leaving x = X in the previous iterate
 //
@@ -68,31 +69,6 @@ struct IterConfig {
     double tol;
 };
 
-template <typename R>
-struct KParams {
-    int J, P;
-    int bc_left, bc_right;
-    int use_cond;
-    int pad0;
-    cudaGraphConditionalHandle cond;
-    const int *mat;
-    const r4<R> *cellq;
-    const r4<R> *tab;      // [n_mat][P][2]: (Pr, Pi, Rr, Ri), (Ur, Ui, Vr, Vi)
-    const r2<R> *matpar;   // [n_mat]: (e, s)
-    const kmat *matK;      // [n_mat]
-    const r2<R> *muw;      // [P]: (mu, w)
-    r2<R> *faceP[2];
-    r2<R> *faceM[2];
-    r4<R> *psi_edge;
-    r4<R> *g;
-    r2<R> *refl;           // [P] SI: lagged mirror flux at a reflecting right face
-    double *phi[2];
-    double *phi0;
-    double *phi_out;
-    double *partials;      // [gridDim.x][2]
-    IterState *st;
-    const IterConfig *cfg;
-};
 
 // ------------------------------------------------------------ load helpers
 __device__ __forceinline__ r4<float> ldg4(const r4<float> *p)
@@ -174,6 +150,97 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
     s = a + b;
     e = 0.0;
 }
+
+// Double-float ("FF") numbers: value = h + l with |l| <= ulp(h)/2, ~48-bit
+// significand, built from FP32 operations with explicit rounding (Dekker /
+// Knuth error-free transformations).  The FP32 path uses them where a double
+// is needed -- the Woodbury capacitance solve and the iterate difference of
+// the residual -- because FP64 throughput on this part is 1/58 of FP32.
+struct ff { float h, l; };
+
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b)  // requires |a| >= |b| or a == 0
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_norm(float a, float b)
+{
+    float s, e;
+    two_sum(a, b, s, e);
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    return ff_fast_two_sum(s, e);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float ff_diff(ff a, ff b)  // (a - b) rounded to float
+{
+    return __fadd_rn(__fsub_rn(a.h, b.h), __fsub_rn(a.l, b.l));
+}
+
+// Storage of the scalar-flux iterates: double in FP64 mode, FF pairs (h, l)
+// in FP32 mode (8 bytes either way).
+template <typename R> struct PhiStore;
+template <> struct PhiStore<double> {
+    using S = double;
+    static __device__ __forceinline__ double real(S v) { return v; }
+    static __device__ __forceinline__ double wide(S v) { return v; }
+};
+template <> struct PhiStore<float> {
+    using S = float2;
+    static __device__ __forceinline__ float real(S v) { return __fadd_rn(v.x, v.y); }
+    static __device__ __forceinline__ double wide(S v) { return (double)v.x + (double)v.y; }
+};
+template <typename R> using phi_t = typename PhiStore<R>::S;
+
+// The 4 moments of one cell as R (for the s phi terms).
+template <typename R>
+__device__ __forceinline__ void load_phi4(const phi_t<R> *ph, int cell, R &a, R &b, R &c, R &d)
+{
+    const phi_t<R> *q = ph + 4 * (size_t)cell;
+    a = PhiStore<R>::real(__ldcg(q));
+    b = PhiStore<R>::real(__ldcg(q + 1));
+    c = PhiStore<R>::real(__ldcg(q + 2));
+    d = PhiStore<R>::real(__ldcg(q + 3));
+}
+
+template <typename R>
+struct KParams {
+    int J, P;
+    int bc_left, bc_right;
+    int use_cond;
+    int pad0;
+    cudaGraphConditionalHandle cond;
+    const int *mat;
+    const r4<R> *cellq;
+    const r4<R> *tab;      // [n_mat][P][2]: (Pr, Pi, Rr, Ri), (Ur, Ui, Vr, Vi)
+    const r2<R> *matpar;   // [n_mat]: (e, s)
+    const kmat *matK;      // [n_mat]
+    const r2<R> *muw;      // [P]: (mu, w)
+    r2<R> *faceP[2];
+    r2<R> *faceM[2];
+    r4<R> *psi_edge;
+    r4<R> *g;
+    r2<R> *refl;           // [P] SI: lagged mirror flux at a reflecting right face
+    phi_t<R> *phi[2];      // iterates l / l+1 (ping-pong)
+    phi_t<R> *phi0;        // initial iterate of the step
+    double *phi_out;       // published moments of the last committed step
+    const float4 *matKf;   // [n_mat][2] FF capacitance (k00h,k00l,k01h,k01l),(k10h,k10l,k11h,k11l)
+    double *partials;      // [gridDim.x][2]
+    IterState *st;
+    const IterConfig *cfg;
+};
 
 // Reduce V values per lane (s with compensation e) over the LPC lanes of a
 // segment.  Afterwards lane holds NV = max(V/LPC, 1) sums in s[0..NV-1] for
@@ -371,14 +438,15 @@ __global__ void __launch_bounds__(256) k_cells(const KParams<R> p)
     if (!iteration_prologue(p, iter, base)) return;
     const int frd = MODE == M_OCI ? ((base + iter) & 1) : base;
     const int fwr = frd ^ 1;
-    const double *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
-    double *phw = p.phi[(iter + 1) & 1];
+    const phi_t<R> *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
+    phi_t<R> *phw = p.phi[(iter + 1) & 1];
     const r2<R> *fPr = p.faceP[frd], *fMr = p.faceM[frd];
     r2<R> *fPw = p.faceP[fwr], *fMw = p.faceM[fwr];
     const bool refl_l = MODE == M_OCI && p.bc_left == BC_REFLECT;
     const bool refl_r = MODE == M_OCI && p.bc_right == BC_REFLECT;
 
     double acc_d2 = 0.0, acc_p2 = 0.0;
+    float accf_d2 = 0.f, accf_p2 = 0.f;  // FP32 mode: per-lane partials (grid sums in double)
     const int nchunks = (J + CPC - 1) / CPC;
     for (int chunk = blockIdx.x * wpb + warp; chunk < nchunks; chunk += gridDim.x * wpb) {
         R s_acc[V], e_acc[V];
@@ -393,9 +461,8 @@ __global__ void __launch_bounds__(256) k_cells(const KParams<R> p)
             const r2<R> es = ldg2(p.matpar + m);
             R fkl = 0, fkr = 0, fhl = 0, fhr = 0;
             if (MODE == M_SI && valid) {
-                const double2 a = __ldcg(reinterpret_cast<const double2 *>(phr + 4 * (size_t)cell));
-                const double2 b = __ldcg(reinterpret_cast<const double2 *>(phr + 4 * (size_t)cell) + 1);
-                fkl = (R)a.x * es.y; fkr = (R)a.y * es.y; fhl = (R)b.x * es.y; fhr = (R)b.y * es.y;
+                load_phi4<R>(phr, cell, fkl, fkr, fhl, fhr);
+                fkl *= es.y; fkr *= es.y; fhl *= es.y; fhr *= es.y;
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) { s_acc[4 * r + k] = 0; e_acc[4 * r + k] = 0; }
@@ -461,27 +528,57 @@ __global__ void __launch_bounds__(256) k_cells(const KParams<R> p)
             const int gi = base_idx + t;
             const int row = gi >> 2, comp = gi & 3;
             const int cell = chunk * CPC + row * SPW + seg;
-            const double r_own = (double)s_acc[t] + (double)e_acc[t];
-            double phi;
-            if (MODE == M_OCI) {
-                double r_par;
-                if constexpr (NV >= 4) r_par = (double)s_acc[t ^ 2] + (double)e_acc[t ^ 2];
-                else if constexpr (NV == 2) r_par = __shfl_xor_sync(FULL, r_own, 1);
-                else r_par = __shfl_xor_sync(FULL, r_own, 2);
-                const int m = cell < J ? __ldg(p.mat + cell) : 0;
-                const kmat K = p.matK[m];
-                phi = comp < 2 ? K.k00 * r_own + K.k01 * r_par : K.k10 * r_par + K.k11 * r_own;
+            if constexpr (sizeof(R) == 4) {
+                // FP32 mode: double-float capacitance solve and iterate difference
+                const ff r_own = ff_norm(s_acc[t], e_acc[t]);
+                ff phi;
+                if (MODE == M_OCI) {
+                    ff r_par;
+                    if constexpr (NV >= 4) {
+                        r_par = ff_norm(s_acc[t ^ 2], e_acc[t ^ 2]);
+                    } else {
+                        constexpr int o = NV == 2 ? 1 : 2;
+                        r_par.h = __shfl_xor_sync(FULL, r_own.h, o);
+                        r_par.l = __shfl_xor_sync(FULL, r_own.l, o);
+                    }
+                    const int m = cell < J ? __ldg(p.mat + cell) : 0;
+                    const float4 k0 = __ldg(p.matKf + 2 * m), k1 = __ldg(p.matKf + 2 * m + 1);
+                    phi = comp < 2 ? ff_add(ff_mul(ff{k0.x, k0.y}, r_own), ff_mul(ff{k0.z, k0.w}, r_par))
+                                   : ff_add(ff_mul(ff{k1.x, k1.y}, r_par), ff_mul(ff{k1.z, k1.w}, r_own));
+                } else {
+                    phi = r_own;
+                }
+                if (owner_lane && cell < J) {
+                    const float2 old = __ldcg(reinterpret_cast<const float2 *>(phr) + 4 * (size_t)cell + comp);
+                    const float d = ff_diff(phi, ff{old.x, old.y});
+                    accf_d2 = __fmaf_rn(d, d, accf_d2);
+                    accf_p2 = __fmaf_rn(phi.h, phi.h, accf_p2);
+                    reinterpret_cast<float2 *>(phw)[4 * (size_t)cell + comp] = make_float2(phi.h, phi.l);
+                }
+                phiR[t] = (R)__fadd_rn(phi.h, phi.l);
             } else {
-                phi = r_own;
+                const double r_own = (double)s_acc[t] + (double)e_acc[t];
+                double phi;
+                if (MODE == M_OCI) {
+                    double r_par;
+                    if constexpr (NV >= 4) r_par = (double)s_acc[t ^ 2] + (double)e_acc[t ^ 2];
+                    else if constexpr (NV == 2) r_par = __shfl_xor_sync(FULL, r_own, 1);
+                    else r_par = __shfl_xor_sync(FULL, r_own, 2);
+                    const int m = cell < J ? __ldg(p.mat + cell) : 0;
+                    const kmat K = p.matK[m];
+                    phi = comp < 2 ? K.k00 * r_own + K.k01 * r_par : K.k10 * r_par + K.k11 * r_own;
+                } else {
+                    phi = r_own;
+                }
+                if (owner_lane && cell < J) {
+                    const double old = __ldcg(reinterpret_cast<const double *>(phr) + 4 * (size_t)cell + comp);
+                    const double d = phi - old;
+                    acc_d2 += d * d;
+                    acc_p2 += phi * phi;
+                    reinterpret_cast<double *>(phw)[4 * (size_t)cell + comp] = phi;
+                }
+                phiR[t] = (R)phi;
             }
-            if (owner_lane && cell < J) {
-                const double old = __ldcg(phr + 4 * (size_t)cell + comp);
-                const double d = phi - old;
-                acc_d2 += d * d;
-                acc_p2 += phi * phi;
-                phw[4 * (size_t)cell + comp] = phi;
-            }
-            phiR[t] = (R)phi;
         }
         // ---------------- phase D: every lane of the segment gets phi of its cells
         all_gather<LPC, V>(phiR, lane);
@@ -512,7 +609,8 @@ __global__ void __launch_bounds__(256) k_cells(const KParams<R> p)
             }
         }
     }
-    finalize_iteration(acc_d2, acc_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond);
+    finalize_iteration(acc_d2 + (double)accf_d2, acc_p2 + (double)accf_p2, p.partials, p.st, p.cfg, iter,
+                       p.use_cond, p.cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -616,8 +714,8 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
     if (!iteration_prologue(p, iter, base)) return;
     const int frd = MODE == M_OCI ? ((base + iter) & 1) : base;
     const int fwr = frd ^ 1;
-    const double *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
-    double *phw = p.phi[(iter + 1) & 1];
+    const phi_t<R> *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
+    phi_t<R> *phw = p.phi[(iter + 1) & 1];
     const r2<R> *fPr = p.faceP[frd], *fMr = p.faceM[frd];
     r2<R> *fPw = p.faceP[fwr], *fMw = p.faceM[fwr];
     const bool refl_l = MODE == M_OCI && p.bc_left == BC_REFLECT;
@@ -681,7 +779,9 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
         }
     };
 
-    double acc_d2 = 0.0, acc_p2 = 0.0;
+    float accf_d2 = 0.f, accf_p2 = 0.f;  // per-lane partials; block and grid sums in double
+    int mK = -1;
+    float4 kA = make_float4(0.f, 0.f, 0.f, 0.f), kB = kA;
     for (int i = 0; i < nmine; ++i) {
         if (lane == 0) {
             fence_proxy_async();
@@ -699,6 +799,16 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
         const r4<R> *sE = reinterpret_cast<const r4<R> *>(st + oE);
         const r4<R> *sQ = reinterpret_cast<const r4<R> *>(st + oQ);
         const int *sT = reinterpret_cast<const int *>(st + oT);
+        // phi^l of the values this lane owns in phase C, fetched now so the
+        // load overlaps phases A and B
+        float2 old_phi[NOWN];
+#pragma unroll
+        for (int k = 0; k < NOWN; ++k) {
+            const int f = lane * NOWN + k;
+            const int g = f / V, v = f % V;
+            const int cell = chunk * CPC + (v >> 2) * SPW + g;
+            old_phi[k] = (g < SPW && cell < J) ? __ldcg(phr + 4 * (size_t)cell + (v & 3)) : make_float2(0.f, 0.f);
+        }
         // ---------------- phase A: y = A^{-1} c per ordinate pair; lane partials
         // of the moments w (y+ + conj(y-)) go to the transpose buffer
 #pragma unroll
@@ -711,9 +821,8 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                 const r4<R> qd = sQ[cl];
                 R fkl = 0, fkr = 0, fhl = 0, fhr = 0;
                 if (MODE == M_SI) {
-                    const double2 a = __ldcg(reinterpret_cast<const double2 *>(phr + 4 * (size_t)cell));
-                    const double2 b = __ldcg(reinterpret_cast<const double2 *>(phr + 4 * (size_t)cell) + 1);
-                    fkl = (R)a.x * cs; fkr = (R)a.y * cs; fhl = (R)b.x * cs; fhr = (R)b.y * cs;
+                    load_phi4<R>(phr, cell, fkl, fkr, fhl, fhr);
+                    fkl *= cs; fkr *= cs; fhl *= cs; fhr *= cs;
                 }
 #pragma unroll
                 for (int t = 0; t < PPL; ++t) {
@@ -743,24 +852,33 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
         __syncwarp();
         // ---------------- phase B: each lane sums the LPC lane partials of the
         // (segment, moment) values it owns, compensated (Kahan)
-        float own_s[NOWN], own_c[NOWN];
+        ff own[NOWN];
 #pragma unroll
         for (int k = 0; k < NOWN; ++k) {
             const int f = lane * NOWN + k;
             const int g = f / V, v = f % V;  // segment and value index (row * 4 + moment)
-            float sum = 0.f, cmp = 0.f;
+            // KC interleaved Kahan sums over the segment's lanes, joined exactly
+            constexpr int KC = LPC >= 4 ? 4 : LPC;
+            float sk[KC], ck[KC];
+#pragma unroll
+            for (int a = 0; a < KC; ++a) { sk[a] = 0.f; ck[a] = 0.f; }
             if (g < SPW) {
 #pragma unroll
-                for (int q = 0; q < LPC; ++q) {
-                    const float x = xp[xpose_idx(g * LPC + q, v)];
-                    const float y = __fsub_rn(x, cmp);
-                    const float t = __fadd_rn(sum, y);
-                    cmp = __fsub_rn(__fsub_rn(t, sum), y);
-                    sum = t;
+                for (int q = 0; q < LPC; q += KC) {
+#pragma unroll
+                    for (int a = 0; a < KC; ++a) {
+                        const float x = xp[xpose_idx(g * LPC + q + a, v)];
+                        const float y = __fsub_rn(x, ck[a]);
+                        const float t = __fadd_rn(sk[a], y);
+                        ck[a] = __fsub_rn(__fsub_rn(t, sk[a]), y);
+                        sk[a] = t;
+                    }
                 }
             }
-            own_s[k] = sum;
-            own_c[k] = cmp;
+            ff acc = ff_norm(sk[0], -ck[0]);
+#pragma unroll
+            for (int a = 1; a < KC; ++a) acc = ff_add(acc, ff_norm(sk[a], -ck[a]));
+            own[k] = acc;
         }
         __syncwarp();
         // ---------------- phase C: capacitance solve + residual, in double
@@ -770,26 +888,34 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
             const int g = f / V, v = f % V;
             const int row = v >> 2, comp = v & 3;
             const int cell = chunk * CPC + row * SPW + g;
-            const double r_own = (double)own_s[k] - (double)own_c[k];
-            double phi;
+            ff phi;
             if (MODE == M_OCI) {
-                double r_par;
-                if constexpr (NOWN >= 4) r_par = (double)own_s[k ^ 2] - (double)own_c[k ^ 2];
-                else if constexpr (NOWN == 2) r_par = __shfl_xor_sync(FULL, r_own, 1);
-                else r_par = __shfl_xor_sync(FULL, r_own, 2);
+                ff r_par;
+                if constexpr (NOWN >= 4) {
+                    r_par = own[k ^ 2];
+                } else {
+                    constexpr int o = NOWN == 2 ? 1 : 2;
+                    r_par.h = __shfl_xor_sync(FULL, own[k].h, o);
+                    r_par.l = __shfl_xor_sync(FULL, own[k].l, o);
+                }
                 const int m = (g < SPW && cell < J) ? sT[row * SPW + g] : 0;
-                const kmat K = p.matK[m];
-                phi = comp < 2 ? K.k00 * r_own + K.k01 * r_par : K.k10 * r_par + K.k11 * r_own;
+                if (m != mK) {  // capacitance of this value's material (cached per lane)
+                    mK = m;
+                    kA = __ldg(p.matKf + 2 * m);
+                    kB = __ldg(p.matKf + 2 * m + 1);
+                }
+                phi = comp < 2 ? ff_add(ff_mul(ff{kA.x, kA.y}, own[k]), ff_mul(ff{kA.z, kA.w}, r_par))
+                               : ff_add(ff_mul(ff{kB.x, kB.y}, r_par), ff_mul(ff{kB.z, kB.w}, own[k]));
             } else {
-                phi = r_own;
+                phi = own[k];
             }
             if (g < SPW && cell < J) {
-                const double old = __ldcg(phr + 4 * (size_t)cell + comp);
-                const double d = phi - old;
-                acc_d2 += d * d;
-                acc_p2 += phi * phi;
-                phw[4 * (size_t)cell + comp] = phi;
-                xp[g * V + v] = (float)phi;  // phi of (segment g, value v) for phase D
+                const float2 old = old_phi[k];
+                const float d = ff_diff(phi, ff{old.x, old.y});
+                accf_d2 = __fmaf_rn(d, d, accf_d2);
+                accf_p2 = __fmaf_rn(phi.h, phi.h, accf_p2);
+                phw[4 * (size_t)cell + comp] = make_float2(phi.h, phi.l);
+                xp[g * V + v] = __fadd_rn(phi.h, phi.l);  // phi of (segment g, value v) for phase D
             }
         }
         __syncwarp();
@@ -839,7 +965,7 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
         const int last = broke_at + STAGES - 1 < nmine ? broke_at + STAGES - 1 : nmine;
         for (int k = broke_at; k < last; ++k) (void)mbar_wait(bars + k % STAGES, (unsigned)(k / STAGES) & 1u);
     }
-    finalize_iteration(acc_d2, acc_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond);
+    finalize_iteration((double)accf_d2, (double)accf_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -863,7 +989,7 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
     const int status = st->status, iter = st->iter, base = st->base;
     bool go = true;
     int frd = 0, fgs = 0;
-    const double *phi_psi = nullptr, *phi_pub = nullptr;
+    const phi_t<R> *phi_psi = nullptr, *phi_pub = nullptr;
     if (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI) {
         go = iter >= 1 && (status == ST_CONVERGED || (status == ST_MAXITER && p.cfg->commit_unconverged));
         if (MODE == C_COMMIT_OCI) {
@@ -898,9 +1024,8 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
         const r2<R> es = ldg2(p.matpar + m);
         R Fkl = 0, Fkr = 0, Fhl = 0, Fhr = 0;
         if (MODE != C_GUESS) {
-            const double2 a = __ldcg(reinterpret_cast<const double2 *>(phi_psi + 4 * (size_t)cell));
-            const double2 b = __ldcg(reinterpret_cast<const double2 *>(phi_psi + 4 * (size_t)cell) + 1);
-            Fkl = (R)a.x * es.y; Fkr = (R)a.y * es.y; Fhl = (R)b.x * es.y; Fhr = (R)b.y * es.y;
+            load_phi4<R>(phi_psi, cell, Fkl, Fkr, Fhl, Fhr);
+            Fkl *= es.y; Fkr *= es.y; Fhl *= es.y; Fhr *= es.y;
         }
 #pragma unroll
         for (int i = 0; i < PPL; ++i) {
@@ -947,7 +1072,7 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
         }
         if (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI) {
             for (int c = ls; c < 4; c += LPC) {
-                p.phi_out[4 * (size_t)cell + c] = __ldcg(phi_pub + 4 * (size_t)cell + c);
+                p.phi_out[4 * (size_t)cell + c] = PhiStore<R>::wide(__ldcg(phi_pub + 4 * (size_t)cell + c));
                 p.phi0[4 * (size_t)cell + c] = __ldcg(phi_pub + 4 * (size_t)cell + 2 + (c & 1));
             }
         }

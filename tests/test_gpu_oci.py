@@ -230,3 +230,17 @@ def test_staged_kernel_matches_unstaged(N, J, monkeypatch):
     b = _gpu_fixed(prob, "oci", 4, 2, precision="fp32")
     assert _rel(a[0], b[0]) < 1e-6 and _rel(a[1], b[1]) < 1e-6
     assert _rel(a[0], ref["phi_steps"]) < FP32_TOL and _rel(b[0], ref["phi_steps"]) < FP32_TOL
+
+
+@pytest.mark.parametrize("method", ["oci", "si"])
+def test_fp32_ill_conditioned_capacitance(method):
+    """c = 0.999 in optically thick cells: (I - s M)^{-1} has entries ~1/(1-c);
+    the FP32 path's double-float capacitance solve keeps the FP32 bound."""
+    prob = workloads.homogeneous(400, 16, 1.0, 0.999, 5.0, 1.0, 2.0, 1.0, "reflect", "vacuum", tol=1e-9)
+    ref = oracle.run(prob, method, 3, tol=1e-9, max_iter=200000)
+    assert ref["status"] == 0
+    with pkg.Solver(prob, precision="fp32", tol=1e-8) as s:
+        for k in range(3):
+            rc, st = s.step(method)
+            assert rc == pkg.OCI_OK, (rc, st)
+            assert _rel(s.fluxes(), ref["phi_steps"][k]) < 5 * FP32_TOL
