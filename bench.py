@@ -124,6 +124,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(dev_time, units, device="cpu"):
+    """Replicas: the job's time is the slowest rank's, its work the sum over ranks."""
+    import torch
+    t = torch.tensor([dev_time, units], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def algorithmic_bytes(J, N, rs):
     """Bytes one OCI iteration must move: per cell-ordinate 2 incident values,
     2 time-edge values, 2 outgoing values (6 words); per cell phi^l in and
@@ -167,11 +177,7 @@ def run_ours(args, rank, world):
     dev_time = float(sum(secs))
     units = float(J) * N * float(sum(iters))
     if world > 1:
-        t = torch.tensor([dev_time, units], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        dev_time, units = float(tmax[0]), float(t[1])
+        dev_time, units = aggregate(dev_time, units, "cuda")
     value = units / dev_time
 
     # roofline: the iteration kernel alone, CUDA events on the same stream

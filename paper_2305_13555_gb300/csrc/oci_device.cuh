@@ -982,6 +982,7 @@ template <typename R, int LPC, int PPL, int MODE>
 __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
 {
     constexpr int SPW = 32 / LPC;
+    constexpr int ROWS = 4;  // cells per segment in flight per pass (loads issued together)
     const int lane = threadIdx.x & 31;
     const int seg = lane / LPC, ls = lane % LPC;
     const int J = p.J, P = p.P;
@@ -1017,63 +1018,90 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
     const bool refl_r = MODE == C_COMMIT_OCI && p.bc_right == BC_REFLECT;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int cell = gw * SPW + seg; cell - seg < J; cell += nwarps * SPW) {
-        if (cell >= J) continue;
-        const int m = __ldg(p.mat + cell);
-        const r4<R> qd = ldg4(p.cellq + cell);
-        const r2<R> es = ldg2(p.matpar + m);
-        R Fkl = 0, Fkr = 0, Fhl = 0, Fhr = 0;
-        if (MODE != C_GUESS) {
-            load_phi4<R>(phi_psi, cell, Fkl, Fkr, Fhl, Fhr);
-            Fkl *= es.y; Fkr *= es.y; Fhl *= es.y; Fhr *= es.y;
+    R mu[PPL];
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) mu[i] = (ls + LPC * i < P) ? ldg2(p.muw + ls + LPC * i).x : R(0);
+    // a pass covers ROWS rows of SPW cells per warp
+    for (int c0 = gw * SPW * ROWS; c0 < J; c0 += nwarps * SPW * ROWS) {
+        int cellr[ROWS], mr[ROWS];
+        r4<R> qdr[ROWS];
+        R F[ROWS][4];
+        r4<R> per[ROWS][PPL];
+        r2<R> inPr[ROWS][PPL], inMr[ROWS][PPL];
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const int cell = c0 + r * SPW + seg;
+            cellr[r] = cell;
+            const bool valid = cell < J;
+            mr[r] = valid ? __ldg(p.mat + cell) : 0;
+            qdr[r] = valid ? ldg4(p.cellq + cell) : r4<R>{0, 0, 0, 0};
+            F[r][0] = F[r][1] = F[r][2] = F[r][3] = 0;
+            if (MODE != C_GUESS && valid) load_phi4<R>(phi_psi, cell, F[r][0], F[r][1], F[r][2], F[r][3]);
+#pragma unroll
+            for (int i = 0; i < PPL; ++i) {
+                const int pp = ls + LPC * i;
+                const bool ok = valid && pp < P;
+                per[r][i] = ok ? ld4(p.psi_edge + (size_t)cell * P + pp) : r4<R>{0, 0, 0, 0};
+                inPr[r][i] = inMr[r][i] = r2<R>{0, 0};
+                if (ok && (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI)) {
+                    inPr[r][i] = (refl_l && cell == 0) ? ld2(p.faceM[frd] + pp) : ld2(p.faceP[frd] + (size_t)cell * P + pp);
+                    inMr[r][i] = (refl_r && cell == J - 1) ? ld2(p.faceP[frd] + (size_t)J * P + pp)
+                                                          : ld2(p.faceM[frd] + (size_t)(cell + 1) * P + pp);
+                }
+            }
         }
 #pragma unroll
-        for (int i = 0; i < PPL; ++i) {
-            const int pp = ls + LPC * i;
-            if (pp >= P) continue;
-            const r4<R> pe = ld4(p.psi_edge + (size_t)cell * P + pp);
-            if (MODE == C_GUESS) {
-                st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, pe.y, pe.y);
-                st2(p.faceM[fgs] + (size_t)cell * P + pp, pe.z, pe.z);
-                continue;
-            }
-            const Coef<R> a = load_coef(p.tab, m, P, pp);
-            const R mu = ldg2(p.muw + pp).x;
-            R ukr = qd.x + es.x * pe.x + Fkl, uki = qd.y + es.x * pe.y + Fkr, uhr = qd.z + Fhl, uhi = qd.w + Fhr;
-            R vkr = qd.x + es.x * pe.z + Fkl, vki = -(qd.y + es.x * pe.w) - Fkr, vhr = qd.z + Fhl, vhi = -qd.w - Fhr;
-            if (MODE == C_SI_PREP) {
-                const R ok = a.pr * uki + a.pi * ukr + a.rr * uhi + a.ri * uhr;
-                const R oh = a.ur * uki + a.ui * ukr + a.vr * uhi + a.vi * uhr;
-                const R mk = a.pr * vkr - a.pi * vki + a.rr * vhr - a.ri * vhi;
-                const R mh = a.ur * vkr - a.ui * vki + a.vr * vhr - a.vi * vhi;
-                st4(p.g + (size_t)pp * J + cell, ok, oh, mk, mh);
-                if (cell == J - 1 && p.bc_right == BC_REFLECT) {
-                    // SI lags a reflecting right face: the first sweep sees the
-                    // initial iterate's outgoing +mu flux there.
-                    const r2<R> v = ld2(p.faceP[frd] + (size_t)J * P + pp);
-                    st2(p.refl + pp, v.x, v.y);
+        for (int r = 0; r < ROWS; ++r) {
+            const int cell = cellr[r];
+            if (cell >= J) continue;
+            const int m = mr[r];
+            const r4<R> qd = qdr[r];
+            const r2<R> es = ldg2(p.matpar + m);
+            const R Fkl = F[r][0] * es.y, Fkr = F[r][1] * es.y, Fhl = F[r][2] * es.y, Fhr = F[r][3] * es.y;
+#pragma unroll
+            for (int i = 0; i < PPL; ++i) {
+                const int pp = ls + LPC * i;
+                if (pp >= P) continue;
+                const r4<R> pe = per[r][i];
+                if (MODE == C_GUESS) {
+                    st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, pe.y, pe.y);
+                    st2(p.faceM[fgs] + (size_t)cell * P + pp, pe.z, pe.z);
+                    continue;
                 }
-                continue;
+                const Coef<R> a = load_coef(p.tab, m, P, pp);
+                R ukr = qd.x + es.x * pe.x + Fkl, uki = qd.y + es.x * pe.y + Fkr, uhr = qd.z + Fhl, uhi = qd.w + Fhr;
+                R vkr = qd.x + es.x * pe.z + Fkl, vki = -(qd.y + es.x * pe.w) - Fkr, vhr = qd.z + Fhl, vhi = -qd.w - Fhr;
+                if (MODE == C_SI_PREP) {
+                    const R ok = a.pr * uki + a.pi * ukr + a.rr * uhi + a.ri * uhr;
+                    const R oh = a.ur * uki + a.ui * ukr + a.vr * uhi + a.vi * uhr;
+                    const R mk = a.pr * vkr - a.pi * vki + a.rr * vhr - a.ri * vhi;
+                    const R mh = a.ur * vkr - a.ui * vki + a.vr * vhr - a.vi * vhi;
+                    st4(p.g + (size_t)pp * J + cell, ok, oh, mk, mh);
+                    if (cell == J - 1 && p.bc_right == BC_REFLECT) {
+                        // SI lags a reflecting right face: the first sweep sees the
+                        // initial iterate's outgoing +mu flux there.
+                        const r2<R> v = ld2(p.faceP[frd] + (size_t)J * P + pp);
+                        st2(p.refl + pp, v.x, v.y);
+                    }
+                    continue;
+                }
+                ukr += mu[i] * inPr[r][i].x; uhr += mu[i] * inPr[r][i].y;
+                vki -= mu[i] * inMr[r][i].x; vhi -= mu[i] * inMr[r][i].y;
+                // end-of-step components only (k+1/2): second rows of A^{-1}
+                const R phr_ = a.ur * ukr - a.ui * uki + a.vr * uhr - a.vi * uhi;
+                const R phi_ = a.ur * uki + a.ui * ukr + a.vr * uhi + a.vi * uhr;
+                const R mhr = a.ur * vkr - a.ui * vki + a.vr * vhr - a.vi * vhi;
+                const R mhi = a.ur * vki + a.ui * vkr + a.vr * vhi + a.vi * vhr;
+                // psi+ = (L, R) = (Re, Im); psi- = conj(z): (Re z, -Im z)
+                st4(p.psi_edge + (size_t)cell * P + pp, phr_, phi_, mhr, -mhi);
+                st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, phi_, phi_);
+                st2(p.faceM[fgs] + (size_t)cell * P + pp, mhr, mhr);
             }
-            const r2<R> inP = (refl_l && cell == 0) ? ld2(p.faceM[frd] + pp) : ld2(p.faceP[frd] + (size_t)cell * P + pp);
-            const r2<R> inM = (refl_r && cell == J - 1) ? ld2(p.faceP[frd] + (size_t)J * P + pp)
-                                                        : ld2(p.faceM[frd] + (size_t)(cell + 1) * P + pp);
-            ukr += mu * inP.x; uhr += mu * inP.y;
-            vki -= mu * inM.x; vhi -= mu * inM.y;
-            // end-of-step components only (k+1/2): second rows of A^{-1}
-            const R phr_ = a.ur * ukr - a.ui * uki + a.vr * uhr - a.vi * uhi;
-            const R phi_ = a.ur * uki + a.ui * ukr + a.vr * uhi + a.vi * uhr;
-            const R mhr = a.ur * vkr - a.ui * vki + a.vr * vhr - a.vi * vhi;
-            const R mhi = a.ur * vki + a.ui * vkr + a.vr * vhi + a.vi * vhr;
-            // psi+ = (L, R) = (Re, Im); psi- = conj(z): (Re z, -Im z)
-            st4(p.psi_edge + (size_t)cell * P + pp, phr_, phi_, mhr, -mhi);
-            st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, phi_, phi_);
-            st2(p.faceM[fgs] + (size_t)cell * P + pp, mhr, mhr);
-        }
-        if (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI) {
-            for (int c = ls; c < 4; c += LPC) {
-                p.phi_out[4 * (size_t)cell + c] = PhiStore<R>::wide(__ldcg(phi_pub + 4 * (size_t)cell + c));
-                p.phi0[4 * (size_t)cell + c] = __ldcg(phi_pub + 4 * (size_t)cell + 2 + (c & 1));
+            if (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI) {
+                for (int c = ls; c < 4; c += LPC) {
+                    p.phi_out[4 * (size_t)cell + c] = PhiStore<R>::wide(__ldcg(phi_pub + 4 * (size_t)cell + c));
+                    p.phi0[4 * (size_t)cell + c] = __ldcg(phi_pub + 4 * (size_t)cell + 2 + (c & 1));
+                }
             }
         }
     }

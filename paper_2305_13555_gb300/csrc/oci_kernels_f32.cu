@@ -1,4 +1,6 @@
 // Template instantiations of the OCI / SI kernels for R = float.
+#include <cstdlib>
+
 #include "oci_kernels.h"
 
 namespace ocik {
@@ -35,7 +37,14 @@ bool kernel_set_f32(int lpc, int ppl, KernelSet *out)
     case 4 * 16 + 1: fill<4, 1, 8>(out); return true;
     case 8 * 16 + 1: fill<8, 1, 8>(out); return true;
     case 16 * 16 + 1: fill<16, 1, 8>(out); return true;
-    case 32 * 16 + 1: fill<32, 1, 8>(out); return true;
+    case 32 * 16 + 1:
+        fill<32, 1, 8>(out);
+        if (const char *e = std::getenv("OCI_TMA_STAGES"); e && e[0] == '3') {
+            out->cells_oci_tma = (const void *)&k_cells_tma<32, 1, 8, 3, M_OCI>;
+            out->cells_si_tma = (const void *)&k_cells_tma<32, 1, 8, 3, M_SI>;
+            out->tma_stages = 3;
+        }
+        return true;
     case 32 * 16 + 2: fill<32, 2, 8>(out); return true;
     case 32 * 16 + 4: fill<32, 4, 4>(out); return true;
     default: return false;
