@@ -38,6 +38,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "oci_nn.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -158,6 +160,29 @@ int oci_set_state(oci_handle *h, const double *psi_edge);
  * committed state (psi_{k-1/2}, published phi) is untouched and the next step
  * restarts from it.  Used by the benchmark's roofline figure. */
 int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_launch);
+
+/* ------------------------------------------------- learned guess (oci_nn.h) */
+enum { OCI_NN_OFF = 0, OCI_NN_GUESS = 1, OCI_NN_GUESS_CORRECT = 2 };
+
+/* Attach a trained network (parameters: host FP32 array of
+ * oci_nn_param_count() elements, layout in oci_nn.h) to the handle, or detach
+ * it (mode OCI_NN_OFF, params may be NULL).  With OCI_NN_GUESS each oci_step
+ * first predicts the step's scalar-flux moments phat from the last two
+ * committed steps and moves the initial iterate toward them: every incident
+ * angular flux gets the isotropic correction (phat - phi)/2 of the upstream
+ * corner that feeds it.  With OCI_NN_GUESS_CORRECT the iteration also pauses
+ * every k_corr iterations, applies the same correction to the current
+ * iterate, iterates min(k_corr, 8) more times and, if the relative change of
+ * phi is then larger than before the correction, restores the saved iterate
+ * (plain OCI) and makes no further corrections in that step.  The tolerance
+ * is unchanged, so the network changes iteration counts only.  The paper has
+ * no counterpart; OCI_EINVAL for a bad mode, k_corr < 1 or NULL params. */
+int oci_nn_attach(oci_handle *h, const float *params, int32_t mode, int32_t k_corr);
+
+/* The handle's static network inputs, as device arrays: stat [J][4] float
+ * (log10(sigma_t)/2, c, log10(sigma_t dx), log10(sigma_t v dt)) and qfeat [J]
+ * float (v dt (Q_kL + Q_kR)/2), written to caller-owned device memory. */
+int oci_nn_static_features(const oci_handle *h, void *stat, void *qfeat);
 
 /* Problem sizes and quadrature of the handle: mu[N], w[N] host (may be NULL). */
 int oci_query(const oci_handle *h, int32_t *n_cells, int32_t *n_ord, double *mu, double *w);

@@ -65,6 +65,19 @@ SIGNATURES = {
     "oci_query": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "oci_profile_iterations": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(ctypes.c_double)]),
     "oci_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "oci_nn_attach": (ctypes.c_int, [_VP, _VP, _I32, _I32]),
+    "oci_nn_static_features": (ctypes.c_int, [_VP, _VP, _VP]),
+    # include/oci_nn.h
+    "oci_nn_param_count": (ctypes.c_int32, []),
+    "oci_nn_workspace_bytes": (ctypes.c_size_t, [_I32, _I32]),
+    "oci_nn_features": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _I32, _VP, _VP, _VP]),
+    "oci_nn_targets": (ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _VP, _VP]),
+    "oci_nn_forward": (ctypes.c_int, [_VP, _VP, _I32, _I32, _VP, _VP, ctypes.c_size_t, _VP]),
+    "oci_nn_predict": (ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _VP, _VP]),
+    "oci_nn_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _VP, ctypes.POINTER(ctypes.c_double), _VP,
+                                        ctypes.c_size_t, _VP]),
+    "oci_nn_train_step": (ctypes.c_int, [_VP, _VP, _VP, _I32, ctypes.c_float, _VP, _VP, _I32, _I32,
+                                         ctypes.POINTER(ctypes.c_double), _VP, ctypes.c_size_t, _VP]),
     "oci_last_cuda_error": (ctypes.c_char_p, [_VP]),
 }
 
@@ -267,3 +280,83 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ learned guess
+# Thin wrappers of include/oci_nn.h taking torch CUDA tensors (device pointers).
+
+def _dp(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    return _current_stream()
+
+
+OCI_NN_OFF, OCI_NN_GUESS, OCI_NN_GUESS_CORRECT = 0, 1, 2
+
+
+def oci_nn_attach(h, params, mode=OCI_NN_GUESS, k_corr=50):
+    """Attach trained parameters (host float32 array) to a handle (see oci.h)."""
+    p = None if params is None else np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    _check(load_library().oci_nn_attach(h, None if p is None else p.ctypes.data, int(mode), int(k_corr)),
+           "oci_nn_attach", h)
+
+
+def oci_nn_static_features(h, stat, qfeat):
+    _check(load_library().oci_nn_static_features(h, _dp(stat), _dp(qfeat)), "oci_nn_static_features", h)
+
+
+def oci_nn_param_count():
+    return int(load_library().oci_nn_param_count())
+
+
+def oci_nn_workspace_bytes(batch, n_cells):
+    return int(load_library().oci_nn_workspace_bytes(int(batch), int(n_cells)))
+
+
+def oci_nn_features(phi1, phi2, stat, qfeat, inp, scale, stream=None):
+    B, J = phi1.shape[0], phi1.shape[1]
+    _check(load_library().oci_nn_features(_dp(phi1), _dp(phi2), _dp(stat), _dp(qfeat), B, J, _dp(inp), _dp(scale),
+                                          _stream(stream)), "oci_nn_features")
+
+
+def oci_nn_targets(phin, phi1, scale, tgt, stream=None):
+    B, J = phin.shape[0], phin.shape[1]
+    _check(load_library().oci_nn_targets(_dp(phin), _dp(phi1), _dp(scale), B, J, _dp(tgt), _stream(stream)),
+           "oci_nn_targets")
+
+
+def oci_nn_forward(params, inp, out, workspace, stream=None):
+    B, J = inp.shape[0], inp.shape[2]
+    _check(load_library().oci_nn_forward(_dp(params), _dp(inp), B, J, _dp(out), _dp(workspace),
+                                         workspace.numel() * workspace.element_size(), _stream(stream)),
+           "oci_nn_forward")
+
+
+def oci_nn_predict(phi1, out, scale, phat, stream=None):
+    B, J = phi1.shape[0], phi1.shape[1]
+    _check(load_library().oci_nn_predict(_dp(phi1), _dp(out), _dp(scale), B, J, _dp(phat), _stream(stream)),
+           "oci_nn_predict")
+
+
+def oci_nn_loss_grad(params, inp, tgt, grad, workspace, stream=None):
+    B, J = inp.shape[0], inp.shape[2]
+    loss = ctypes.c_double()
+    _check(load_library().oci_nn_loss_grad(_dp(params), _dp(inp), _dp(tgt), B, J, _dp(grad), ctypes.byref(loss),
+                                           _dp(workspace), workspace.numel() * workspace.element_size(),
+                                           _stream(stream)), "oci_nn_loss_grad")
+    return loss.value
+
+
+def oci_nn_train_step(params, m, v, step, lr, inp, tgt, workspace, want_loss=True, stream=None):
+    B, J = inp.shape[0], inp.shape[2]
+    loss = ctypes.c_double()
+    _check(load_library().oci_nn_train_step(_dp(params), _dp(m), _dp(v), int(step), float(lr), _dp(inp), _dp(tgt),
+                                            B, J, ctypes.byref(loss) if want_loss else None, _dp(workspace),
+                                            workspace.numel() * workspace.element_size(), _stream(stream)),
+           "oci_nn_train_step")
+    return loss.value if want_loss else None
+

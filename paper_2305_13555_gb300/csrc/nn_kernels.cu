@@ -1,0 +1,470 @@
+// 1-D convolutional network over cells (learned initial guess / corrector of
+// the OCI iteration): forward, backward, Adam, feature and target builders.
+//
+// Network: 5 convolution layers along the cell index, kernel width 5, zero
+// padding of 2 cells at the slab ends, channels 13 -> 32 -> 32 -> 32 -> 32 -> 4,
+// ReLU after layers 1-4.  Weights are used in BF16 (rounded from FP32 master
+// copies), activations and all accumulations are FP32.  Parameter layout: per
+// layer W[co][ci][5] then b[co] (flat FP32).  Activations: [B][C][J] FP32.
+// Reductions over cells (weight gradients, loss) are per-tile partials summed
+// in a fixed order, so results are deterministic.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/oci_nn.h"
+
+namespace ocinn {
+
+constexpr int KW = 5, PAD = 2, NL = 5;
+constexpr int CH[NL + 1] = {13, 32, 32, 32, 32, 4};
+constexpr int TX = 128;      // cells per tile
+constexpr int MAXC = 32;
+
+constexpr int layer_w(int l) { return CH[l + 1] * CH[l] * KW; }
+constexpr int layer_off(int l)
+{
+    int o = 0;
+    for (int i = 0; i < l; ++i) o += layer_w(i) + CH[i + 1];
+    return o;
+}
+constexpr int NPARAM = layer_off(NL);
+
+// ------------------------------------------------------------- forward conv
+// out[b][co][x] = bias[co] + sum_ci sum_k W[co][ci][k] in[b][ci][x+k-2]; one
+// thread per cell x computes every output channel.  If FLIP, the kernel runs
+// the data gradient instead: W is read as W'[ci'][co'][k] = W[co'][ci'][4-k]
+// (input channels = the layer's outputs), no bias, and the incoming gradient is
+// masked by the ReLU derivative of `mask` (the layer's own output) on load.
+template <int CI, int CO, bool RELU, bool FLIP>
+__global__ void __launch_bounds__(TX) k_conv(const float *__restrict__ in, const float *__restrict__ mask,
+                                             const __nv_bfloat16 *__restrict__ W, const float *__restrict__ bias,
+                                             float *__restrict__ out, int J)
+{
+    __shared__ float s_in[CI][TX + 2 * PAD];
+    __shared__ __align__(16) float s_w[CI][KW][CO];   // [ci][k][co] for vector loads over co
+    const int b = blockIdx.y, x0 = blockIdx.x * TX, t = threadIdx.x;
+    // weights: natural layout W[o][i][k] (o = CO or CI of the forward layer)
+    for (int e = t; e < CI * KW * CO; e += TX) {
+        const int co = e % CO, k = (e / CO) % KW, ci = e / (CO * KW);
+        float w;
+        if (!FLIP) w = __bfloat162float(W[(co * CI + ci) * KW + k]);
+        else w = __bfloat162float(W[(ci * CO + co) * KW + (KW - 1 - k)]);  // forward layer had CO' = CI inputs
+        s_w[ci][k][co] = w;
+    }
+    for (int e = t; e < CI * (TX + 2 * PAD); e += TX) {
+        const int ci = e / (TX + 2 * PAD), xx = e % (TX + 2 * PAD);
+        const int x = x0 + xx - PAD;
+        float v = 0.f;
+        if (x >= 0 && x < J) {
+            v = in[((size_t)b * CI + ci) * J + x];
+            if (FLIP && mask) v = mask[((size_t)b * CI + ci) * J + x] > 0.f ? v : 0.f;
+        }
+        s_in[ci][xx] = v;
+    }
+    __syncthreads();
+    const int x = x0 + t;
+    if (x >= J) return;
+    float acc[CO];
+#pragma unroll
+    for (int co = 0; co < CO; ++co) acc[co] = (!FLIP && bias) ? bias[co] : 0.f;
+    for (int ci = 0; ci < CI; ++ci) {
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            const float v = s_in[ci][t + k];
+            if constexpr (CO % 4 == 0) {
+#pragma unroll
+                for (int c4 = 0; c4 < CO / 4; ++c4) {
+                    const float4 w = *reinterpret_cast<const float4 *>(&s_w[ci][k][4 * c4]);
+                    acc[4 * c4 + 0] = __fmaf_rn(w.x, v, acc[4 * c4 + 0]);
+                    acc[4 * c4 + 1] = __fmaf_rn(w.y, v, acc[4 * c4 + 1]);
+                    acc[4 * c4 + 2] = __fmaf_rn(w.z, v, acc[4 * c4 + 2]);
+                    acc[4 * c4 + 3] = __fmaf_rn(w.w, v, acc[4 * c4 + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int co = 0; co < CO; ++co) acc[co] = __fmaf_rn(s_w[ci][k][co], v, acc[co]);
+            }
+        }
+    }
+#pragma unroll
+    for (int co = 0; co < CO; ++co) {
+        float r = acc[co];
+        if (RELU) r = fmaxf(r, 0.f);
+        out[((size_t)b * CO + co) * J + x] = r;
+    }
+}
+
+// ------------------------------------------------------------- weight grad
+// Per tile of TX cells of one sample: partial dW[co][ci][k] = sum_x g[co][x]
+// in[ci][x+k-2] and db[co] = sum_x g[co][x], where g is the output gradient
+// masked by the ReLU derivative (when the layer has one).
+template <int CI, int CO, bool RELU>
+__global__ void __launch_bounds__(256) k_wgrad(const float *__restrict__ in, const float *__restrict__ g,
+                                               const float *__restrict__ outv, float *__restrict__ partial, int J)
+{
+    __shared__ float s_in[CI][TX + 2 * PAD];
+    __shared__ float s_g[CO][TX];
+    const int b = blockIdx.y, x0 = blockIdx.x * TX, t = threadIdx.x;
+    for (int e = t; e < CI * (TX + 2 * PAD); e += blockDim.x) {
+        const int ci = e / (TX + 2 * PAD), xx = e % (TX + 2 * PAD);
+        const int x = x0 + xx - PAD;
+        s_in[ci][xx] = (x >= 0 && x < J) ? in[((size_t)b * CI + ci) * J + x] : 0.f;
+    }
+    for (int e = t; e < CO * TX; e += blockDim.x) {
+        const int co = e / TX, xx = e % TX;
+        const int x = x0 + xx;
+        float v = 0.f;
+        if (x < J) {
+            v = g[((size_t)b * CO + co) * J + x];
+            if (RELU) v = outv[((size_t)b * CO + co) * J + x] > 0.f ? v : 0.f;
+        }
+        s_g[co][xx] = v;
+    }
+    __syncthreads();
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    float *part = partial + (size_t)tile * (CO * CI * KW + CO);
+    const int nx = J - x0 < TX ? J - x0 : TX;
+    for (int pr = t; pr < CO * CI; pr += blockDim.x) {
+        const int co = pr / CI, ci = pr % CI;
+        float a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+        for (int xx = 0; xx < nx; ++xx) {
+            const float gv = s_g[co][xx];
+            a0 = __fmaf_rn(gv, s_in[ci][xx + 0], a0);
+            a1 = __fmaf_rn(gv, s_in[ci][xx + 1], a1);
+            a2 = __fmaf_rn(gv, s_in[ci][xx + 2], a2);
+            a3 = __fmaf_rn(gv, s_in[ci][xx + 3], a3);
+            a4 = __fmaf_rn(gv, s_in[ci][xx + 4], a4);
+        }
+        float *w = part + (co * CI + ci) * KW;
+        w[0] = a0; w[1] = a1; w[2] = a2; w[3] = a3; w[4] = a4;
+    }
+    for (int co = t; co < CO; co += blockDim.x) {
+        float a = 0.f;
+        for (int xx = 0; xx < nx; ++xx) a += s_g[co][xx];
+        part[CO * CI * KW + co] = a;
+    }
+}
+
+// Sum the per-tile partials (fixed order) into grad[off .. off + n).
+__global__ void k_reduce_partials(const float *__restrict__ partial, int ntiles, int n, float *__restrict__ grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float a = 0.f;
+    for (int tile = 0; tile < ntiles; ++tile) a += partial[(size_t)tile * n + i];
+    grad[i] = a;
+}
+
+// Mean squared error: per-tile partial sums of (out - t)^2 and the output
+// gradient 2 (out - t) / count.
+__global__ void __launch_bounds__(256) k_mse(const float *__restrict__ out, const float *__restrict__ tgt, size_t n,
+                                             float *__restrict__ g, double *__restrict__ partial)
+{
+    __shared__ double sh[8];
+    double acc = 0.0;
+    const float scale = 2.f / (float)n;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float d = out[i] - tgt[i];
+        acc += (double)d * d;
+        if (g) g[i] = scale * d;
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_sum_doubles(const double *__restrict__ v, int n, double denom, double *__restrict__ out)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += v[i];
+        *out = s / denom;
+    }
+}
+
+// Adam (Kingma & Ba) on the FP32 master weights; refreshes the BF16 copy.
+__global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                       const float *__restrict__ grad, int n, float lr, float b1, float b2, float eps, float c1,
+                       float c2, __nv_bfloat16 *__restrict__ pb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gr = grad[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gr;
+    const float vi = b2 * v[i] + (1.f - b2) * gr * gr;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    pb[i] = __float2bfloat16_rn(pi);
+}
+
+__global__ void k_to_bf16(const float *__restrict__ p, int n, __nv_bfloat16 *__restrict__ pb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) pb[i] = __float2bfloat16_rn(p[i]);
+}
+
+// ------------------------------------------------------------- features
+// Per-sample scale S = sqrt(mean over cells and moments of phi1^2), floored by
+// the source scale, so that the network sees O(1) inputs at every flux level.
+__global__ void __launch_bounds__(256) k_scale(const double *__restrict__ phi1, const float *__restrict__ qfeat,
+                                               int J, float *__restrict__ scale)
+{
+    __shared__ double sh[2][8];
+    const int b = blockIdx.x;
+    double a = 0.0, q = 0.0;
+    for (int i = threadIdx.x; i < 4 * J; i += blockDim.x) {
+        const double v = phi1[(size_t)b * 4 * J + i];
+        a += v * v;
+    }
+    for (int j = threadIdx.x; j < J; j += blockDim.x) {
+        const double v = qfeat[(size_t)b * J + j];
+        q += v * v;
+    }
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = a; sh[1][threadIdx.x >> 5] = q; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sq = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sa += sh[0][w]; sq += sh[1][w]; }
+        double s = sqrt(sa / (4.0 * J));
+        const double sqv = sqrt(sq / J);
+        if (s < sqv) s = sqv;
+        if (!(s > 1e-30)) s = 1.0;
+        scale[b] = (float)s;
+    }
+}
+
+__global__ void k_features(const double *__restrict__ phi1, const double *__restrict__ phi2,
+                           const float *__restrict__ stat, const float *__restrict__ qfeat,
+                           const float *__restrict__ scale, int J, float *__restrict__ in)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (j >= J) return;
+    const float inv = 1.f / scale[b];
+    float *o = in + (size_t)b * 13 * J + j;
+    const double *p1 = phi1 + ((size_t)b * J + j) * 4, *p2 = phi2 + ((size_t)b * J + j) * 4;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        o[(size_t)c * J] = (float)p1[c] * inv;
+        o[(size_t)(4 + c) * J] = (float)(p1[c] - p2[c]) * inv;
+    }
+    const float *s = stat + ((size_t)b * J + j) * 4;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[(size_t)(8 + c) * J] = s[c];
+    o[(size_t)12 * J] = qfeat[(size_t)b * J + j] * inv;
+}
+
+__global__ void k_targets(const double *__restrict__ phin, const double *__restrict__ phi1,
+                          const float *__restrict__ scale, int J, float *__restrict__ tgt)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (j >= J) return;
+    const float inv = 1.f / scale[b];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        tgt[((size_t)b * 4 + c) * J + j] = (float)(phin[((size_t)b * J + j) * 4 + c] - phi1[((size_t)b * J + j) * 4 + c]) * inv;
+}
+
+// prediction phi_hat = phi1 + S * out, as double [B][J][4]
+__global__ void k_predict(const double *__restrict__ phi1, const float *__restrict__ out,
+                          const float *__restrict__ scale, int J, double *__restrict__ phat)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (j >= J) return;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        phat[((size_t)b * J + j) * 4 + c] =
+            phi1[((size_t)b * J + j) * 4 + c] + (double)scale[b] * (double)out[((size_t)b * 4 + c) * J + j];
+}
+
+// ------------------------------------------------------------- workspace
+struct Work {
+    __nv_bfloat16 *wb;     // BF16 weights [NPARAM]
+    float *act[NL + 1];    // act[0] = input (caller's), act[l] = output of layer l
+    float *g[2];           // gradient ping-pong [B][32][J]
+    float *grad;           // [NPARAM]
+    float *partial;        // [tiles][max layer params]
+    double *lpart;         // loss partials
+    double *loss;          // [1]
+};
+
+size_t workspace_layout(int B, int J, Work *w, char *base)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + off : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    const size_t cells = (size_t)B * J;
+    const int tiles = B * ((J + TX - 1) / TX);
+    int maxp = 0;
+    for (int l = 0; l < NL; ++l) maxp = layer_w(l) + CH[l + 1] > maxp ? layer_w(l) + CH[l + 1] : maxp;
+    Work tmp{};
+    Work &o = w ? *w : tmp;
+    o.wb = (__nv_bfloat16 *)take(sizeof(__nv_bfloat16) * NPARAM);
+    o.act[0] = nullptr;
+    for (int l = 1; l <= NL; ++l) o.act[l] = (float *)take(sizeof(float) * cells * CH[l]);
+    o.g[0] = (float *)take(sizeof(float) * cells * MAXC);
+    o.g[1] = (float *)take(sizeof(float) * cells * MAXC);
+    o.grad = (float *)take(sizeof(float) * NPARAM);
+    o.partial = (float *)take(sizeof(float) * (size_t)tiles * maxp);
+    o.lpart = (double *)take(sizeof(double) * 1024);
+    o.loss = (double *)take(sizeof(double));
+    return off;
+}
+
+template <int L>
+void launch_fwd(const Work &w, const float *bias, int B, int J, cudaStream_t s)
+{
+    constexpr int CI = CH[L], CO = CH[L + 1];
+    const dim3 grid((J + TX - 1) / TX, B);
+    k_conv<CI, CO, (L < NL - 1), false><<<grid, TX, 0, s>>>(w.act[L], nullptr, w.wb + layer_off(L), bias, w.act[L + 1], J);
+}
+
+void forward_all(const Work &w, const float *params, int B, int J, cudaStream_t s)
+{
+    launch_fwd<0>(w, params + layer_off(0) + layer_w(0), B, J, s);
+    launch_fwd<1>(w, params + layer_off(1) + layer_w(1), B, J, s);
+    launch_fwd<2>(w, params + layer_off(2) + layer_w(2), B, J, s);
+    launch_fwd<3>(w, params + layer_off(3) + layer_w(3), B, J, s);
+    launch_fwd<4>(w, params + layer_off(4) + layer_w(4), B, J, s);
+}
+
+// Backward of layer L: gin = gradient w.r.t. the layer's output (before the
+// ReLU mask), produces the parameter gradient and (L > 0) the gradient w.r.t.
+// the layer's input in gout.
+template <int L>
+void launch_bwd(const Work &w, const float *gin, float *gout, int B, int J, cudaStream_t s)
+{
+    constexpr int CI = CH[L], CO = CH[L + 1];
+    constexpr bool RELU = L < NL - 1;
+    const dim3 grid((J + TX - 1) / TX, B);
+    const int tiles = grid.x * grid.y;
+    k_wgrad<CI, CO, RELU><<<grid, 256, 0, s>>>(w.act[L], gin, w.act[L + 1], w.partial, J);
+    const int n = CO * CI * KW + CO;
+    k_reduce_partials<<<(n + 255) / 256, 256, 0, s>>>(w.partial, tiles, n, w.grad + layer_off(L));
+    if constexpr (L > 0)  // data gradient: transposed, flipped conv of the masked gradient
+        k_conv<CO, CI, false, true><<<grid, TX, 0, s>>>(gin, RELU ? w.act[L + 1] : nullptr, w.wb + layer_off(L),
+                                                         nullptr, gout, J);
+}
+
+int loss_grad(const float *params, const float *in, const float *tgt, int B, int J, void *ws, size_t ws_bytes,
+              double *loss_host, float *grad_out, cudaStream_t s)
+{
+    Work w{};
+    if (workspace_layout(B, J, nullptr, nullptr) > ws_bytes) return 1;
+    workspace_layout(B, J, &w, (char *)ws);
+    w.act[0] = const_cast<float *>(in);
+    k_to_bf16<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, NPARAM, w.wb);
+    forward_all(w, params, B, J, s);
+    const size_t n = (size_t)B * 4 * J;
+    const int nb = 256;
+    k_mse<<<nb, 256, 0, s>>>(w.act[NL], tgt, n, w.g[0], w.lpart);
+    k_sum_doubles<<<1, 32, 0, s>>>(w.lpart, nb, 1.0 * n, w.loss);
+    launch_bwd<4>(w, w.g[0], w.g[1], B, J, s);
+    launch_bwd<3>(w, w.g[1], w.g[0], B, J, s);
+    launch_bwd<2>(w, w.g[0], w.g[1], B, J, s);
+    launch_bwd<1>(w, w.g[1], w.g[0], B, J, s);
+    launch_bwd<0>(w, w.g[0], w.g[1], B, J, s);
+    if (grad_out) cudaMemcpyAsync(grad_out, w.grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, s);
+    if (loss_host) {
+        cudaMemcpyAsync(loss_host, w.loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+}  // namespace ocinn
+
+using namespace ocinn;
+
+extern "C" {
+
+int32_t oci_nn_param_count(void) { return NPARAM; }
+
+size_t oci_nn_workspace_bytes(int32_t batch, int32_t n_cells)
+{
+    if (batch < 1 || n_cells < 1) return 0;
+    return workspace_layout(batch, n_cells, nullptr, nullptr);
+}
+
+int oci_nn_features(const double *phi1, const double *phi2, const float *stat, const float *qfeat, int32_t batch,
+                    int32_t n_cells, float *in, float *scale, void *stream)
+{
+    if (!phi1 || !phi2 || !stat || !qfeat || !in || !scale || batch < 1 || n_cells < 1) return 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_scale<<<batch, 256, 0, s>>>(phi1, qfeat, n_cells, scale);
+    k_features<<<dim3((n_cells + 255) / 256, batch), 256, 0, s>>>(phi1, phi2, stat, qfeat, scale, n_cells, in);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int oci_nn_targets(const double *phin, const double *phi1, const float *scale, int32_t batch, int32_t n_cells,
+                   float *tgt, void *stream)
+{
+    if (!phin || !phi1 || !scale || !tgt || batch < 1 || n_cells < 1) return 1;
+    k_targets<<<dim3((n_cells + 255) / 256, batch), 256, 0, (cudaStream_t)stream>>>(phin, phi1, scale, n_cells, tgt);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int oci_nn_forward(const float *params, const float *in, int32_t batch, int32_t n_cells, float *out, void *ws,
+                   size_t ws_bytes, void *stream)
+{
+    if (!params || !in || !out || !ws || batch < 1 || n_cells < 1) return 1;
+    Work w{};
+    if (workspace_layout(batch, n_cells, nullptr, nullptr) > ws_bytes) return 1;
+    workspace_layout(batch, n_cells, &w, (char *)ws);
+    w.act[0] = const_cast<float *>(in);
+    cudaStream_t s = (cudaStream_t)stream;
+    k_to_bf16<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, NPARAM, w.wb);
+    forward_all(w, params, batch, n_cells, s);
+    cudaMemcpyAsync(out, w.act[NL], sizeof(float) * (size_t)batch * 4 * n_cells, cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int oci_nn_predict(const double *phi1, const float *out, const float *scale, int32_t batch, int32_t n_cells,
+                   double *phat, void *stream)
+{
+    if (!phi1 || !out || !scale || !phat || batch < 1 || n_cells < 1) return 1;
+    k_predict<<<dim3((n_cells + 255) / 256, batch), 256, 0, (cudaStream_t)stream>>>(phi1, out, scale, n_cells, phat);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int oci_nn_loss_grad(const float *params, const float *in, const float *tgt, int32_t batch, int32_t n_cells,
+                     float *grad, double *loss, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!params || !in || !tgt || batch < 1 || n_cells < 1 || !ws) return 1;
+    return loss_grad(params, in, tgt, batch, n_cells, ws, ws_bytes, loss, grad, (cudaStream_t)stream);
+}
+
+int oci_nn_train_step(float *params, float *adam_m, float *adam_v, int32_t step, float lr, const float *in,
+                      const float *tgt, int32_t batch, int32_t n_cells, double *loss, void *ws, size_t ws_bytes,
+                      void *stream)
+{
+    if (!params || !adam_m || !adam_v || step < 1 || !in || !tgt || batch < 1 || n_cells < 1 || !ws) return 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int rc = loss_grad(params, in, tgt, batch, n_cells, ws, ws_bytes, loss, nullptr, s);
+    if (rc) return rc;
+    Work w{};
+    workspace_layout(batch, n_cells, &w, (char *)ws);
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    k_adam<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, adam_m, adam_v, w.grad, NPARAM, lr, b1, b2, 1e-8f, c1, c2,
+                                                 w.wb);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+}  // extern "C"

@@ -116,6 +116,17 @@ struct oci_handle {
     bool guess_valid = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string err;
+    // learned guess
+    int nn_mode = OCI_NN_OFF, nn_kcorr = 50;
+    void *nn_mem = nullptr;          // one allocation for everything below
+    float *nn_params = nullptr, *nn_in = nullptr, *nn_out = nullptr, *nn_scale = nullptr, *nn_stat = nullptr,
+          *nn_qfeat = nullptr;
+    double *nn_phat = nullptr, *nn_hist[2] = {nullptr, nullptr}, *nn_phi_bak = nullptr;
+    void *nn_ws = nullptr, *nn_face_bak = nullptr;
+    size_t nn_ws_bytes = 0;
+    cudaGraph_t graph_cont = nullptr;
+    cudaGraphExec_t exec_cont = nullptr;
+    std::vector<double> q_host;      // sources (for the network's inputs)
 };
 
 namespace {
@@ -230,8 +241,34 @@ int load_state(oci_handle *h, const double *psi)
     return OCI_OK;
 }
 
+// Static network inputs per cell (see oci_nn.h) and the source input qfeat.
+void nn_host_features(const oci_handle *h, std::vector<float> &stat, std::vector<float> &qf)
+{
+    const int J = h->J;
+    const double vdt = std::isinf(h->v) ? 1.0 : h->v * h->dt;
+    stat.assign((size_t)J * 4, 0.f);
+    qf.assign(J, 0.f);
+    for (int j = 0; j < J; ++j) {
+        const Material &m = h->mats[h->mat[j]];
+        const double st = std::max(m.st, 1e-30);
+        stat[4 * j + 0] = (float)(0.5 * std::log10(st));
+        stat[4 * j + 1] = (float)(m.st > 0.0 ? m.ss / m.st : 0.0);
+        stat[4 * j + 2] = (float)std::log10(std::max(m.st * m.dx, 1e-30));
+        stat[4 * j + 3] = (float)std::log10(std::max(m.st * vdt, 1e-30));
+        if (!h->q_host.empty()) qf[j] = (float)(vdt * 0.5 * (h->q_host[4 * (size_t)j] + h->q_host[4 * (size_t)j + 1]));
+    }
+}
+
 int upload_source(oci_handle *h, const double *q)
 {
+    if (q) h->q_host.assign(q, q + (size_t)h->J * 4);
+    else h->q_host.assign((size_t)h->J * 4, 0.0);
+    if (h->nn_mem) {
+        std::vector<float> st, qf;
+        nn_host_features(h, st, qf);
+        CK(h, cudaMemcpyAsync(h->nn_qfeat, qf.data(), sizeof(float) * qf.size(), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
     std::vector<double> cq((size_t)h->J * 4, 0.0);
     if (q)
         for (int j = 0; j < h->J; ++j)
@@ -379,6 +416,35 @@ int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout
     return OCI_OK;
 }
 
+// Continuation of a paused OCI step: WHILE { cells } -> commit.
+template <typename R>
+int build_cont_graph(oci_handle *h)
+{
+    cudaGraph_t g;
+    CK(h, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    CK(h, cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
+    KParams<R> plain = make_params<R>(h, 0, 0);
+    KParams<R> loop = make_params<R>(h, 1, cond);
+    void *a_plain[] = {&plain};
+    void *a_loop[] = {&loop};
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t n_while, n_commit, b_cells;
+    CK(h, cudaGraphAddNode(&n_while, g, nullptr, nullptr, 0, &cp));
+    int rc = add_kernel(h, cp.conditional.phGraph_out[0], &b_cells, nullptr, 0, h->cells_oci, dim3(h->cells_grid),
+                        dim3(h->cells_block), a_loop, h->cells_smem);
+    if (rc) return rc;
+    rc = add_kernel(h, g, &n_commit, &n_while, 1, h->ks.commit_oci, dim3(h->grid_pc), dim3(kBlock), a_plain);
+    if (rc) return rc;
+    CK(h, cudaGraphInstantiate(&h->exec_cont, g, 0));
+    h->graph_cont = g;
+    return OCI_OK;
+}
+
 int ensure_graphs(oci_handle *h)
 {
     if (h->exec_oci) return OCI_OK;
@@ -391,6 +457,20 @@ int ensure_graphs(oci_handle *h)
         if (!rc) rc = build_graph<float>(h, true, &h->graph_si, &h->exec_si);
     }
     return rc;
+}
+
+int launch_lift(oci_handle *h, const void *fn)
+{
+    if (h->prec == OCI_FP64) {
+        KParams<double> p = make_params<double>(h, 0, 0);
+        void *a[] = {&p, &h->nn_phat};
+        CK(h, cudaLaunchKernel(fn, dim3(h->grid_pc), dim3(kBlock), a, 0, h->stream));
+    } else {
+        KParams<float> p = make_params<float>(h, 0, 0);
+        void *a[] = {&p, &h->nn_phat};
+        CK(h, cudaLaunchKernel(fn, dim3(h->grid_pc), dim3(kBlock), a, 0, h->stream));
+    }
+    return OCI_OK;
 }
 
 int launch_guess(oci_handle *h)
@@ -407,6 +487,64 @@ int launch_guess(oci_handle *h)
     return OCI_OK;
 }
 
+int upload_cfg(oci_handle *h)
+{
+    CK(h, cudaMemcpyAsync(h->d_cfg, &h->cfg, sizeof(IterConfig), cudaMemcpyHostToDevice, h->stream));
+    return OCI_OK;
+}
+
+int read_state(oci_handle *h, IterState *s)
+{
+    CK(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *s = *h->h_st;
+    return OCI_OK;
+}
+
+size_t face_bytes(const oci_handle *h) { return (size_t)(h->J + 1) * h->P * 2 * rsize(h); }
+
+// Save / restore the iterate the next iteration will read (both face arrays
+// and the scalar-flux moments) for the corrector's safeguard.
+int corr_copy(oci_handle *h, const IterState &s, bool save)
+{
+    const int fb = (s.base + s.iter) & 1;
+    const size_t fbytes = face_bytes(h);
+    char *bak = (char *)h->nn_face_bak;
+    void *ph = h->phi[s.iter & 1];
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    if (save) {
+        CK(h, cudaMemcpyAsync(bak, h->faceP[fb], fbytes, k, h->stream));
+        CK(h, cudaMemcpyAsync(bak + fbytes, h->faceM[fb], fbytes, k, h->stream));
+        CK(h, cudaMemcpyAsync(h->nn_phi_bak, ph, (size_t)h->J * 32, k, h->stream));
+    } else {
+        CK(h, cudaMemcpyAsync(h->faceP[fb], bak, fbytes, k, h->stream));
+        CK(h, cudaMemcpyAsync(h->faceM[fb], bak + fbytes, fbytes, k, h->stream));
+        CK(h, cudaMemcpyAsync(ph, h->nn_phi_bak, (size_t)h->J * 32, k, h->stream));
+    }
+    return OCI_OK;
+}
+
+// phat = network(phi_{n-1}, phi_{n-2}, static inputs), then lift into the guess.
+int nn_guess(oci_handle *h)
+{
+    cudaStream_t s = h->stream;
+    if (oci_nn_features(h->nn_hist[0], h->nn_hist[1], h->nn_stat, h->nn_qfeat, 1, h->J, h->nn_in, h->nn_scale, s) ||
+        oci_nn_forward(h->nn_params, h->nn_in, 1, h->J, h->nn_out, h->nn_ws, h->nn_ws_bytes, s) ||
+        oci_nn_predict(h->nn_hist[0], h->nn_out, h->nn_scale, 1, h->J, h->nn_phat, s))
+        return cuda_fail(h, cudaGetLastError(), "network inference");
+    return launch_lift(h, h->ks.lift_guess);
+}
+
+int map_status(int s)
+{
+    switch (s) {
+    case ocik::ST_CONVERGED: return OCI_OK;
+    case ocik::ST_MAXITER: return OCI_ENOTCONV;
+    case ocik::ST_NAN: return OCI_ENAN;
+    default: return OCI_ETIMEOUT;
+    }
+}
+
 int run_step(oci_handle *h, bool si, oci_stats *st)
 {
     if (!h) return OCI_EINVAL;
@@ -417,31 +555,76 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         rc = launch_guess(h);
         if (rc) return rc;
     }
+    const bool nn = !si && h->nn_mode != OCI_NN_OFF;
+    int accepts = 0, rejects = 0;
     CK(h, cudaEventRecord(h->ev0, h->stream));
-    CK(h, cudaGraphLaunch(si ? h->exec_si : h->exec_oci, h->stream));
+    if (nn) {
+        rc = nn_guess(h);
+        if (rc) return rc;
+        h->guess_valid = false;
+        ++accepts;
+    }
+    IterState s{};
+    if (nn && h->nn_mode == OCI_NN_GUESS_CORRECT) {
+        if (!h->exec_cont) {
+            rc = h->prec == OCI_FP64 ? build_cont_graph<double>(h) : build_cont_graph<float>(h);
+            if (rc) return rc;
+        }
+        const int k = h->nn_kcorr, m_check = std::min(h->nn_kcorr, 8);
+        bool correcting = true;
+        h->cfg.pause_at = k;
+        if ((rc = upload_cfg(h))) return rc;
+        CK(h, cudaGraphLaunch(h->exec_oci, h->stream));
+        for (;;) {
+            if ((rc = read_state(h, &s))) return rc;
+            if (s.status != ocik::ST_RUNNING) break;
+            if (correcting) {
+                // pause: try a correction toward phat, keep it only if it helped
+                const double before = s.resid;
+                if ((rc = corr_copy(h, s, true)) || (rc = launch_lift(h, h->ks.lift_corr))) return rc;
+                h->cfg.pause_at = s.iter + m_check;
+                if ((rc = upload_cfg(h))) return rc;
+                CK(h, cudaGraphLaunch(h->exec_cont, h->stream));
+                IterState s2{};
+                if ((rc = read_state(h, &s2))) return rc;
+                if (s2.status != ocik::ST_RUNNING) { s = s2; ++accepts; break; }
+                if (s2.resid > before) {
+                    if ((rc = corr_copy(h, s2, false))) return rc;  // back to the saved iterate
+                    ++rejects;
+                    correcting = false;
+                } else {
+                    ++accepts;
+                }
+                s = s2;
+            }
+            h->cfg.pause_at = correcting ? s.iter + k : -1;
+            if ((rc = upload_cfg(h))) return rc;
+            CK(h, cudaGraphLaunch(h->exec_cont, h->stream));
+        }
+        h->cfg.pause_at = -1;
+        if ((rc = upload_cfg(h))) return rc;
+    } else {
+        CK(h, cudaGraphLaunch(si ? h->exec_si : h->exec_oci, h->stream));
+    }
     CK(h, cudaEventRecord(h->ev1, h->stream));
-    CK(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
+    if ((rc = read_state(h, &s))) return rc;
     float ms = 0.f;
     CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-    const IterState s = *h->h_st;
     h->guess_valid = s.committed != 0;
-    int status;
-    switch (s.status) {
-    case ocik::ST_CONVERGED: status = OCI_OK; break;
-    case ocik::ST_MAXITER: status = OCI_ENOTCONV; break;
-    case ocik::ST_NAN: status = OCI_ENAN; break;
-    case ocik::ST_GUARD: status = OCI_ETIMEOUT; break;
-    default: status = OCI_ETIMEOUT; break;
+    if (s.committed && h->nn_mem) {
+        // history of committed moments for the network: hist[1] <- hist[0] <- phi_out
+        std::swap(h->nn_hist[0], h->nn_hist[1]);
+        CK(h, cudaMemcpyAsync(h->nn_hist[0], h->phi_out, (size_t)h->J * 32, cudaMemcpyDeviceToDevice, h->stream));
     }
+    const int status = map_status(s.status);
     if (st) {
         st->iters = s.iter;
         st->status = status;
         st->residual = s.resid;
         st->seconds = ms * 1e-3;
         st->committed = s.committed;
-        st->nn_accepts = 0;
-        st->nn_rejects = 0;
+        st->nn_accepts = accepts;
+        st->nn_rejects = rejects;
         st->reserved = 0;
     }
     return status;
@@ -483,6 +666,7 @@ int oci_create(const oci_problem *p, oci_handle **out)
     h->cfg.max_iter = p->max_iter;
     h->cfg.tol = p->tol;
     h->cfg.commit_unconverged = 0;
+    h->cfg.pause_at = -1;
     gauss_legendre(N, h->mu, h->w);
     h->dx.assign(p->dx, p->dx + J);
     // materials: distinct (dx, sigma_t, sigma_s)
@@ -632,6 +816,9 @@ void oci_destroy(oci_handle *h)
     if (h->exec_si) cudaGraphExecDestroy(h->exec_si);
     if (h->graph_oci) cudaGraphDestroy(h->graph_oci);
     if (h->graph_si) cudaGraphDestroy(h->graph_si);
+    if (h->exec_cont) cudaGraphExecDestroy(h->exec_cont);
+    if (h->graph_cont) cudaGraphDestroy(h->graph_cont);
+    if (h->nn_mem) cudaFree(h->nn_mem);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->h_st) cudaFreeHost(h->h_st);
@@ -755,6 +942,68 @@ int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_la
     *seconds_per_launch = ms * 1e-3 / n_iter;
     CK(h, cudaMemcpy(h->d_cfg, &h->cfg, sizeof(IterConfig), cudaMemcpyHostToDevice));
     h->guess_valid = false;  // the face buffers now hold timing iterates
+    return OCI_OK;
+}
+
+int oci_nn_attach(oci_handle *h, const float *params, int32_t mode, int32_t k_corr)
+{
+    if (!h || mode < OCI_NN_OFF || mode > OCI_NN_GUESS_CORRECT) return OCI_EINVAL;
+    if (mode != OCI_NN_OFF && (!params || k_corr < 1)) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    if (mode == OCI_NN_OFF) {
+        h->nn_mode = OCI_NN_OFF;
+        return OCI_OK;
+    }
+    const int J = h->J;
+    const size_t npar = (size_t)oci_nn_param_count();
+    if (!h->nn_mem) {
+        const size_t ws = oci_nn_workspace_bytes(1, J);
+        size_t sizes[] = {npar * 4, (size_t)J * 13 * 4, (size_t)J * 16, 256, (size_t)J * 16, (size_t)J * 4,
+                          (size_t)J * 32, (size_t)J * 32, (size_t)J * 32, (size_t)J * 32, ws, 2 * face_bytes(h)};
+        size_t off[12], total = 0;
+        for (int i = 0; i < 12; ++i) {
+            off[i] = total;
+            total += (sizes[i] + 255) & ~(size_t)255;
+        }
+        if (cudaMalloc(&h->nn_mem, total) != cudaSuccess) return OCI_ENOMEM;
+        char *b = (char *)h->nn_mem;
+        h->nn_params = (float *)(b + off[0]);
+        h->nn_in = (float *)(b + off[1]);
+        h->nn_out = (float *)(b + off[2]);
+        h->nn_scale = (float *)(b + off[3]);
+        h->nn_stat = (float *)(b + off[4]);
+        h->nn_qfeat = (float *)(b + off[5]);
+        h->nn_phat = (double *)(b + off[6]);
+        h->nn_hist[0] = (double *)(b + off[7]);
+        h->nn_hist[1] = (double *)(b + off[8]);
+        h->nn_phi_bak = (double *)(b + off[9]);
+        h->nn_ws = b + off[10];
+        h->nn_ws_bytes = ws;
+        h->nn_face_bak = b + off[11];
+        std::vector<float> st, qf;
+        nn_host_features(h, st, qf);
+        CK(h, cudaMemcpy(h->nn_stat, st.data(), sizeof(float) * st.size(), cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->nn_qfeat, qf.data(), sizeof(float) * qf.size(), cudaMemcpyHostToDevice));
+        // history starts at the current committed moments (both entries)
+        CK(h, cudaStreamSynchronize(h->stream));
+        CK(h, cudaMemcpy(h->nn_hist[0], h->phi_out, (size_t)J * 32, cudaMemcpyDeviceToDevice));
+        CK(h, cudaMemcpy(h->nn_hist[1], h->phi_out, (size_t)J * 32, cudaMemcpyDeviceToDevice));
+    }
+    CK(h, cudaMemcpy(h->nn_params, params, npar * 4, cudaMemcpyHostToDevice));
+    h->nn_mode = mode;
+    h->nn_kcorr = k_corr;
+    return OCI_OK;
+}
+
+int oci_nn_static_features(const oci_handle *hc, void *stat, void *qfeat)
+{
+    oci_handle *h = const_cast<oci_handle *>(hc);
+    if (!h || !stat || !qfeat) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    std::vector<float> st, qf;
+    nn_host_features(h, st, qf);
+    CK(h, cudaMemcpy(stat, st.data(), sizeof(float) * st.size(), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(qfeat, qf.data(), sizeof(float) * qf.size(), cudaMemcpyHostToDevice));
     return OCI_OK;
 }
 

@@ -67,6 +67,8 @@ struct IterConfig {
     int max_iter;
     int commit_unconverged;
     double tol;
+    int pause_at;      // iteration count at which the loop stops with the step still running (-1: never)
+    int pad0;
 };
 
 
@@ -379,7 +381,8 @@ __device__ __forceinline__ void finalize_iteration(double d2, double p2, double 
             else if (resid < cfg->tol) ns = ST_CONVERGED;
             else if (it >= cfg->max_iter) ns = ST_MAXITER;
             st->status = ns;
-            if (use_cond) cudaGraphSetConditional(cond, ns == ST_RUNNING ? 1u : 0u);
+            const bool go_on = ns == ST_RUNNING && it != cfg->pause_at;  // pause: host resumes the step
+            if (use_cond) cudaGraphSetConditional(cond, go_on ? 1u : 0u);
         } else if (use_cond) {
             // stopped during this launch (guard or copy timeout): end the loop
             cudaGraphSetConditional(cond, 0u);
@@ -1104,6 +1107,71 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
                 }
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Learned-guess lift: move an iterate toward a predicted scalar flux phat by
+// adding the isotropic correction (phat - phi)/2 of each upstream corner to
+// every incident angular flux it feeds (an isotropic angular flux psi = phi/2
+// carries scalar flux phi with weights summing to 2), and make phat the
+// iterate's scalar flux.  LIFT_GUESS works on the step's initial iterate
+// (faces[base_next], phi0); LIFT_CORR on the current iterate of a paused step
+// (faces[(base + iter) & 1], phi[iter & 1]).  One warp row per cell.
+// ---------------------------------------------------------------------------
+enum : int { LIFT_GUESS = 0, LIFT_CORR = 1 };
+
+template <typename R>
+__device__ __forceinline__ phi_t<R> phi_from_double(double x);
+template <> __device__ __forceinline__ double phi_from_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ float2 phi_from_double<float>(double x)
+{
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+
+template <typename R, int LPC, int PPL, int MODE>
+__global__ void __launch_bounds__(256) k_lift(const KParams<R> p, const double *__restrict__ phat)
+{
+    constexpr int SPW = 32 / LPC;
+    const int lane = threadIdx.x & 31;
+    const int seg = lane / LPC, ls = lane % LPC;
+    const int J = p.J, P = p.P;
+    const IterState *st = p.st;
+    int fb;
+    phi_t<R> *ph;
+    if (MODE == LIFT_GUESS) {
+        fb = st->base_next;
+        ph = p.phi0;
+    } else {
+        fb = (st->base + st->iter) & 1;
+        ph = p.phi[st->iter & 1];
+    }
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int cell = gw * SPW + seg; cell - seg < J; cell += nwarps * SPW) {
+        const bool valid = cell < J;  // all lanes stay in the loop body (warp barriers below)
+        double d[4] = {0.0, 0.0, 0.0, 0.0};
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                d[c] = phat[4 * (size_t)cell + c] - PhiStore<R>::wide(ph[4 * (size_t)cell + c]);
+        }
+        __syncwarp();
+        if (!valid) continue;
+#pragma unroll
+        for (int i = 0; i < PPL; ++i) {
+            const int pp = ls + LPC * i;
+            if (pp >= P) continue;
+            r2<R> *fp = p.faceP[fb] + (size_t)(cell + 1) * P + pp;  // +mu leaves through the right face (corner R)
+            r2<R> *fm = p.faceM[fb] + (size_t)cell * P + pp;        // -mu leaves through the left face (corner L)
+            const r2<R> a = *fp, b = *fm;
+            *fp = r2<R>{a.x + (R)(0.5 * d[1]), a.y + (R)(0.5 * d[3])};
+            *fm = r2<R>{b.x + (R)(0.5 * d[0]), b.y + (R)(0.5 * d[2])};
+        }
+        // the lanes of a cell belong to one segment: after their reads above,
+        // its first lanes overwrite the cell's moments
+        for (int c = ls; c < 4; c += LPC) ph[4 * (size_t)cell + c] = phi_from_double<R>(phat[4 * (size_t)cell + c]);
     }
 }
 

@@ -17,6 +17,8 @@ static void fill(KernelSet *k)
     k->si_prep = (const void *)&k_percell<float, LPC, PPL, C_SI_PREP>;
     k->guess = (const void *)&k_percell<float, LPC, PPL, C_GUESS>;
     k->march = (const void *)&k_si_march<float>;
+    k->lift_guess = (const void *)&k_lift<float, LPC, PPL, LIFT_GUESS>;
+    k->lift_corr = (const void *)&k_lift<float, LPC, PPL, LIFT_CORR>;
     k->cells_oci_tma = nullptr;
     k->cells_si_tma = nullptr;
     k->tma_stages = 0;

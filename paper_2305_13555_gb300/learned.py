@@ -1,0 +1,182 @@
+"""Learned initial guess for the OCI iteration: training data and training loop.
+
+The network (include/oci_nn.h) predicts a time step's converged scalar-flux
+moments from the two previous steps' moments and per-cell material / source
+inputs.  Its training data are trajectories produced by this library's own OCI
+solver on seeded slabs (``workloads.config5_train``); training runs the
+library's forward / backward / Adam kernels.  PyTorch only holds device arrays
+and gathers minibatches.  The paper has no learned component.
+
+Usage (on a GPU):
+    python -m paper_2305_13555_gb300.learned --trajectories 2000 --epochs 20 \
+        --out paper_2305_13555_gb300/data/cnn_weights.npy
+"""
+import argparse
+import math
+import os
+import time
+
+import numpy as np
+
+from . import (OCI_OK, Solver, oci_fluxes_device, oci_nn_features, oci_nn_forward, oci_nn_param_count,
+               oci_nn_predict, oci_nn_static_features, oci_nn_targets, oci_nn_train_step, oci_nn_workspace_bytes)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_WEIGHTS = os.path.join(HERE, "data", "cnn_weights.npy")
+
+
+def trajectories(seeds, J=4096, N=16, n_steps=20, precision="fp32", problem=None):
+    """Run the OCI solver on one seeded slab per seed; returns device tensors
+    phi [T][n_steps+1][J][4] (float64; index 0 = initial moments), stat
+    [T][J][4] and qfeat [T][J] (float32), and the iteration counts."""
+    import torch
+    import workloads
+    problem = problem or (lambda s: workloads.config5_train(s, J=J, N=N, n_steps=n_steps))
+    T = len(seeds)
+    phi = torch.zeros((T, n_steps + 1, J, 4), dtype=torch.float64, device="cuda")
+    stat = torch.zeros((T, J, 4), dtype=torch.float32, device="cuda")
+    qfeat = torch.zeros((T, J), dtype=torch.float32, device="cuda")
+    iters = np.zeros((T, n_steps), dtype=np.int32)
+    for i, seed in enumerate(seeds):
+        prob = problem(seed)
+        with Solver(prob, precision=precision, tol=1e-8) as s:
+            oci_nn_static_features(s.h, stat[i], qfeat[i])
+            oci_fluxes_device(s.h, phi[i, 0].data_ptr())
+            for n in range(n_steps):
+                rc, st = s.step()
+                if rc != OCI_OK:
+                    raise RuntimeError(f"trajectory seed {seed} step {n}: status {rc}")
+                iters[i, n] = st["iters"]
+                oci_fluxes_device(s.h, phi[i, n + 1].data_ptr())
+    torch.cuda.synchronize()
+    return {"phi": phi, "stat": stat, "qfeat": qfeat, "iters": iters}
+
+
+def init_params(seed=0):
+    """He-uniform weights for the ReLU layers, zero biases (layout of oci_nn.h)."""
+    g = np.random.default_rng(seed)
+    ch = (13, 32, 32, 32, 32, 4)
+    out = []
+    for ci, co in zip(ch[:-1], ch[1:]):
+        bound = math.sqrt(6.0 / (ci * 5))
+        out.append(g.uniform(-bound, bound, co * ci * 5))
+        out.append(np.zeros(co))
+    p = np.concatenate(out).astype(np.float32)
+    assert p.size == oci_nn_param_count()
+    return p
+
+
+def _batch(data, idx, t):
+    """Gather phi_n, phi_{n-1}, phi_{n-2} (clamped at 0) of samples (traj, n)."""
+    import torch
+    tr = torch.as_tensor(idx[:, 0], device="cuda")
+    n = torch.as_tensor(idx[:, 1], device="cuda")
+    phi = data["phi"]
+    return (phi[tr, n].contiguous(), phi[tr, n - 1].contiguous(),
+            phi[tr, torch.clamp(n - 2, min=0)].contiguous(), data["stat"][tr].contiguous(),
+            data["qfeat"][tr].contiguous())
+
+
+def train(data, epochs=20, batch=32, lr=1e-3, seed=0, params=None, log=print, val_frac=0.05):
+    """Minibatch Adam on all (trajectory, step) samples; returns (params, history)."""
+    import torch
+    T, S1, J, _ = data["phi"].shape
+    g = np.random.default_rng(seed)
+    samples = np.array([(t, n) for t in range(T) for n in range(1, S1)], dtype=np.int64)
+    g.shuffle(samples)
+    n_val = max(1, int(len(samples) * val_frac))
+    val, tr = samples[:n_val], samples[n_val:]
+    p = torch.tensor(init_params(seed) if params is None else params, device="cuda")
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    ws = torch.empty(oci_nn_workspace_bytes(batch, J), dtype=torch.uint8, device="cuda")
+    inp = torch.empty((batch, 13, J), dtype=torch.float32, device="cuda")
+    tgt = torch.empty((batch, 4, J), dtype=torch.float32, device="cuda")
+    scale = torch.empty(batch, dtype=torch.float32, device="cuda")
+    hist, step = [], 0
+    for ep in range(epochs):
+        g.shuffle(tr)
+        t0 = time.time()
+        losses = []
+        lr_ep = lr * 0.5 * (1 + math.cos(math.pi * ep / max(epochs, 1)))  # cosine decay
+        for b0 in range(0, len(tr) - batch + 1, batch):
+            phin, phi1, phi2, st, qf = _batch(data, tr[b0:b0 + batch], None)
+            oci_nn_features(phi1, phi2, st, qf, inp, scale)
+            oci_nn_targets(phin, phi1, scale, tgt)
+            step += 1
+            want = (b0 // batch) % 50 == 0
+            l = oci_nn_train_step(p, m, v, step, lr_ep, inp, tgt, ws, want_loss=want)
+            if want:
+                losses.append(l)
+        vl = evaluate_loss(p, data, val, batch)
+        hist.append({"epoch": ep, "train_loss": float(np.mean(losses)), "val_loss": vl, "seconds": time.time() - t0})
+        if log:
+            log(f"epoch {ep}: train {hist[-1]['train_loss']:.3e} val {vl:.3e} ({hist[-1]['seconds']:.1f} s)")
+    return p.cpu().numpy(), hist
+
+
+def evaluate_loss(p, data, idx, batch):
+    """Mean squared error of the network on samples idx (no update)."""
+    import torch
+    from . import oci_nn_loss_grad
+    J = data["phi"].shape[2]
+    ws = torch.empty(oci_nn_workspace_bytes(batch, J), dtype=torch.uint8, device="cuda")
+    inp = torch.empty((batch, 13, J), dtype=torch.float32, device="cuda")
+    tgt = torch.empty((batch, 4, J), dtype=torch.float32, device="cuda")
+    scale = torch.empty(batch, dtype=torch.float32, device="cuda")
+    tot, cnt = 0.0, 0
+    for b0 in range(0, len(idx) - batch + 1, batch):
+        phin, phi1, phi2, st, qf = _batch(data, idx[b0:b0 + batch], None)
+        oci_nn_features(phi1, phi2, st, qf, inp, scale)
+        oci_nn_targets(phin, phi1, scale, tgt)
+        tot += oci_nn_loss_grad(p, inp, tgt, None, ws)
+        cnt += 1
+    return tot / max(cnt, 1)
+
+
+def predict(params, phi1, phi2, stat, qfeat):
+    """Network prediction phat [B][J][4] (float64) for device inputs."""
+    import torch
+    B, J = phi1.shape[0], phi1.shape[1]
+    ws = torch.empty(oci_nn_workspace_bytes(B, J), dtype=torch.uint8, device="cuda")
+    inp = torch.empty((B, 13, J), dtype=torch.float32, device="cuda")
+    out = torch.empty((B, 4, J), dtype=torch.float32, device="cuda")
+    scale = torch.empty(B, dtype=torch.float32, device="cuda")
+    phat = torch.empty((B, J, 4), dtype=torch.float64, device="cuda")
+    p = torch.as_tensor(params, device="cuda")
+    oci_nn_features(phi1, phi2, stat, qfeat, inp, scale)
+    oci_nn_forward(p, inp, out, ws)
+    oci_nn_predict(phi1, out, scale, phat)
+    return phat
+
+
+def load_weights(path=DEFAULT_WEIGHTS):
+    return np.load(path).astype(np.float32)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--trajectories", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--cells", type=int, default=4096)
+    ap.add_argument("--ordinates", type=int, default=16)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed0", type=int, default=100000)
+    ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    a = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    data = trajectories(range(a.seed0, a.seed0 + a.trajectories), J=a.cells, N=a.ordinates, n_steps=a.steps)
+    print(f"generated {a.trajectories} trajectories x {a.steps} steps in {time.time() - t0:.1f} s; "
+          f"mean OCI iterations per step {data['iters'].mean():.1f}", flush=True)
+    params, hist = train(data, epochs=a.epochs, batch=a.batch, lr=a.lr)
+    os.makedirs(os.path.dirname(a.out), exist_ok=True)
+    np.save(a.out, params)
+    print(f"saved {params.size} parameters to {a.out}; final val loss {hist[-1]['val_loss']:.3e}")
+
+
+if __name__ == "__main__":
+    main()
