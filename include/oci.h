@@ -93,7 +93,7 @@ typedef struct oci_stats {
     int32_t committed;   /* 1 if the step advanced the state */
     int32_t nn_accepts;  /* learned guess / corrections kept (0 without a network) */
     int32_t nn_rejects;  /* learned corrections reverted by the safeguard */
-    int32_t reserved;
+    int32_t refined;     /* 1 if the FP32 path finished the step with its refinement (see oci_step) */
 } oci_stats;
 
 typedef struct oci_handle oci_handle;
@@ -128,7 +128,17 @@ int oci_set_stream(oci_handle *h, void *cuda_stream);
  * rank-4 (Woodbury) form; iterate until the relative change of phi < tol.
  * The initial iterate has both time moments equal to psi_{k-1/2}.  Returns
  * OCI_OK, OCI_ENOTCONV (state kept unless commit_unconverged), OCI_ENAN,
- * OCI_ETIMEOUT or OCI_ECUDA.  Synchronises the handle's stream once. */
+ * OCI_ETIMEOUT or OCI_ECUDA.  Synchronises the handle's stream once (more
+ * often with a learned corrector or a refinement).
+ * FP32 mode: when the relative change stops falling (no 10% improvement in 8
+ * iterations while below 1e-5 -- float rounding noise near the tolerance), the
+ * step is finished by mixed-precision refinement: the current halo h0 is kept,
+ * r0 = G(h0) - h0 and phi(h0) are evaluated once in FP64 (counted as one
+ * iteration), and the correction d = B d + r0 (B: the OCI map without sources,
+ * homogeneous boundary data) is iterated in FP32 to the same tolerance on the
+ * relative change of phi(h0) + phi(d); h0 + d is committed.  Available for
+ * N/2 a power of two (the staged kernels); otherwise a stall ends the step with
+ * OCI_ENOTCONV at max_iter as usual. */
 int oci_step(oci_handle *h, oci_stats *st);
 
 /* Same contract with source iteration (Sec. "Source Iteration (SI)"): the

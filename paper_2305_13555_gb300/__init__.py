@@ -41,11 +41,11 @@ class OciStats(ctypes.Structure):
     _fields_ = [
         ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("residual", ctypes.c_double),
         ("seconds", ctypes.c_double), ("committed", ctypes.c_int32), ("nn_accepts", ctypes.c_int32),
-        ("nn_rejects", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("nn_rejects", ctypes.c_int32), ("refined", ctypes.c_int32),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 # Every entry point declared in include/oci.h, with its ctypes signature.

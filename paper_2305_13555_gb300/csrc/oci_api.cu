@@ -104,9 +104,10 @@ struct oci_handle {
     IterConfig *d_cfg = nullptr;
     IterState *h_st = nullptr;      // pinned
     IterConfig cfg{};
+    IterConfig cfg_dev{};            // what the device copy holds
     int grid_cells = 1, grid_pc = 1;
     // iteration kernels actually launched (staged TMA variant when available)
-    const void *cells_oci = nullptr, *cells_si = nullptr;
+    const void *cells_oci = nullptr, *cells_si = nullptr, *cells_lin = nullptr;
     int cells_grid = 1, cells_block = 256;
     unsigned cells_smem = 0;
     bool staged = false;
@@ -127,6 +128,13 @@ struct oci_handle {
     cudaGraph_t graph_cont = nullptr;
     cudaGraphExec_t exec_cont = nullptr;
     std::vector<double> q_host;      // sources (for the network's inputs)
+    std::vector<double> bc_left_host, bc_right_host;  // prescribed incident data
+    // FP32 refinement (stalled steps): FP64 tables, saved halo, residual, phi(h0)
+    double *ref_tab = nullptr, *ref_par = nullptr, *ref_muw = nullptr;
+    void *ref_h0P = nullptr, *ref_h0M = nullptr, *ref_r0 = nullptr, *ref_phi = nullptr;
+    cudaGraph_t graph_lin = nullptr;
+    cudaGraphExec_t exec_lin = nullptr;
+    int refinements = 0;
 };
 
 namespace {
@@ -176,6 +184,10 @@ KParams<R> make_params(const oci_handle *h, int use_cond, cudaGraphConditionalHa
     p.phi0 = (ocik::phi_t<R> *)h->phi0;
     p.phi_out = h->phi_out;
     p.matKf = (const float4 *)h->d_matKf;
+    p.h0P = (const r2<R> *)h->ref_h0P;
+    p.h0M = (const r2<R> *)h->ref_h0M;
+    p.r0 = (const r4<R> *)h->ref_r0;
+    p.phi_ref = (const float2 *)h->ref_phi;
     p.partials = h->partials;
     p.st = h->d_st;
     p.cfg = h->d_cfg;
@@ -315,6 +327,11 @@ int build_tables(oci_handle *h)
     if (!rc) rc = upload_real(h, h->matpar, par);
     if (!rc) rc = upload_real(h, h->muw, muw);
     if (rc) return rc;
+    if (h->ref_tab) {  // FP64 copies for the refinement's residual pass
+        CK(h, cudaMemcpy(h->ref_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->ref_par, par.data(), sizeof(double) * par.size(), cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->ref_muw, muw.data(), sizeof(double) * muw.size(), cudaMemcpyHostToDevice));
+    }
     CK(h, cudaMemcpy(h->d_matK, K.data(), sizeof(kmat) * nm, cudaMemcpyHostToDevice));
     {
         std::vector<float> kf((size_t)nm * 8);
@@ -333,6 +350,8 @@ int build_tables(oci_handle *h)
 
 int upload_boundaries(oci_handle *h, const double *bl, const double *br)
 {
+    if (bl && bl != h->bc_left_host.data()) h->bc_left_host.assign(bl, bl + (size_t)h->P * 2);
+    if (br && br != h->bc_right_host.data()) h->bc_right_host.assign(br, br + (size_t)h->P * 2);
     const int J = h->J, P = h->P;
     const size_t rs = rsize(h);
     std::vector<double> l((size_t)P * 2, 0.0), r((size_t)P * 2, 0.0);
@@ -445,6 +464,34 @@ int build_cont_graph(oci_handle *h)
     return OCI_OK;
 }
 
+// Correction iteration of a stalled FP32 step: WHILE { cells_lin } -> commit_lin.
+int build_lin_graph(oci_handle *h)
+{
+    cudaGraph_t g;
+    CK(h, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    CK(h, cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
+    KParams<float> plain = make_params<float>(h, 0, 0);
+    KParams<float> loop = make_params<float>(h, 1, cond);
+    void *a_plain[] = {&plain};
+    void *a_loop[] = {&loop};
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t n_while, n_commit, b_cells;
+    CK(h, cudaGraphAddNode(&n_while, g, nullptr, nullptr, 0, &cp));
+    int rc = add_kernel(h, cp.conditional.phGraph_out[0], &b_cells, nullptr, 0, h->cells_lin, dim3(h->cells_grid),
+                        dim3(h->cells_block), a_loop, h->cells_smem);
+    if (rc) return rc;
+    rc = add_kernel(h, g, &n_commit, &n_while, 1, h->ks.commit_lin, dim3(h->grid_pc), dim3(kBlock), a_plain);
+    if (rc) return rc;
+    CK(h, cudaGraphInstantiate(&h->exec_lin, g, 0));
+    h->graph_lin = g;
+    return OCI_OK;
+}
+
 int ensure_graphs(oci_handle *h)
 {
     if (h->exec_oci) return OCI_OK;
@@ -487,11 +534,17 @@ int launch_guess(oci_handle *h)
     return OCI_OK;
 }
 
-int upload_cfg(oci_handle *h)
+// Make the device's iteration controls equal to c (copied only when they differ).
+int set_device_cfg(oci_handle *h, const IterConfig &c)
 {
-    CK(h, cudaMemcpyAsync(h->d_cfg, &h->cfg, sizeof(IterConfig), cudaMemcpyHostToDevice, h->stream));
+    if (std::memcmp(&c, &h->cfg_dev, sizeof(IterConfig)) == 0) return OCI_OK;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(h->d_cfg, &c, sizeof(IterConfig), cudaMemcpyHostToDevice));
+    h->cfg_dev = c;
     return OCI_OK;
 }
+
+int upload_cfg(oci_handle *h) { return set_device_cfg(h, h->cfg); }
 
 int read_state(oci_handle *h, IterState *s)
 {
@@ -535,12 +588,48 @@ int nn_guess(oci_handle *h)
     return launch_lift(h, h->ks.lift_guess);
 }
 
+// A stalled FP32 step: save the halo h0, evaluate r0 = G(h0) - h0 and phi(h0)
+// in FP64, iterate d = B d + r0 from d = 0 in FP32, commit h0 + d.
+int refine_step(oci_handle *h, IterState *s)
+{
+    if (!h->exec_lin) {
+        int rc = build_lin_graph(h);
+        if (rc) return rc;
+    }
+    const int fb = (s->base + s->iter) & 1;
+    const size_t fbytes = face_bytes(h);
+    CK(h, cudaMemcpyAsync(h->ref_h0P, h->faceP[fb], fbytes, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->ref_h0M, h->faceM[fb], fbytes, cudaMemcpyDeviceToDevice, h->stream));
+    KParams<float> p = make_params<float>(h, 0, 0);
+    ocik::RefineArgs q{h->ref_tab, h->ref_par, h->ref_muw, (r4<float> *)h->ref_r0, (float2 *)h->ref_phi};
+    void *a[] = {&p, &q};
+    CK(h, cudaLaunchKernel(h->ks.refine, dim3(h->grid_pc), dim3(kBlock), a, 0, h->stream));
+    IterState *st = h->d_st;
+    void *a_st[] = {&st};
+    CK(h, cudaLaunchKernel((const void *)&ocik::k_refine_setup, dim3(1), dim3(1), a_st, 0, h->stream));
+    // the correction starts from d = 0 and phi_lin = 0 and has homogeneous
+    // boundary data: clear both face buffers (boundary slots included; h0 is saved)
+    for (int b = 0; b < 2; ++b) {
+        CK(h, cudaMemsetAsync(h->faceP[b], 0, fbytes, h->stream));
+        CK(h, cudaMemsetAsync(h->faceM[b], 0, fbytes, h->stream));
+    }
+    CK(h, cudaMemsetAsync(h->phi[(s->iter + 1) & 1], 0, (size_t)h->J * 32, h->stream));
+    CK(h, cudaGraphLaunch(h->exec_lin, h->stream));
+    int rc = read_state(h, s);
+    if (rc) return rc;
+    ++h->refinements;
+    // boundary data slots of both face buffers (zeroed for the correction)
+    return upload_boundaries(h, h->bc_left_host.empty() ? nullptr : h->bc_left_host.data(),
+                             h->bc_right_host.empty() ? nullptr : h->bc_right_host.data());
+}
+
 int map_status(int s)
 {
     switch (s) {
     case ocik::ST_CONVERGED: return OCI_OK;
     case ocik::ST_MAXITER: return OCI_ENOTCONV;
     case ocik::ST_NAN: return OCI_ENAN;
+    case ocik::ST_STALL: return OCI_ENOTCONV;
     default: return OCI_ETIMEOUT;
     }
 }
@@ -604,7 +693,16 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         h->cfg.pause_at = -1;
         if ((rc = upload_cfg(h))) return rc;
     } else {
+        IterConfig c = h->cfg;
+        if (si) c.stall_floor = 0.0;  // SI has no refinement: no stall stop
+        if ((rc = set_device_cfg(h, c))) return rc;
         CK(h, cudaGraphLaunch(si ? h->exec_si : h->exec_oci, h->stream));
+    }
+    if ((rc = read_state(h, &s))) return rc;
+    int refined = 0;
+    if (s.status == ocik::ST_STALL && !si && h->cells_lin && h->ks.refine) {
+        if ((rc = refine_step(h, &s))) return rc;
+        refined = 1;
     }
     CK(h, cudaEventRecord(h->ev1, h->stream));
     if ((rc = read_state(h, &s))) return rc;
@@ -625,7 +723,7 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         st->committed = s.committed;
         st->nn_accepts = accepts;
         st->nn_rejects = rejects;
-        st->reserved = 0;
+        st->refined = refined;
     }
     return status;
 }
@@ -667,6 +765,8 @@ int oci_create(const oci_problem *p, oci_handle **out)
     h->cfg.tol = p->tol;
     h->cfg.commit_unconverged = 0;
     h->cfg.pause_at = -1;
+    h->cfg.stall_iters = 8;
+    h->cfg.stall_floor = 0.0;  // enabled below for the FP32 path with refinement
     gauss_legendre(N, h->mu, h->w);
     h->dx.assign(p->dx, p->dx + J);
     // materials: distinct (dx, sigma_t, sigma_s)
@@ -769,7 +869,12 @@ int oci_create(const oci_problem *p, oci_handle **out)
                       nm * 32,                                // matKf
                       (size_t)J * 32, (size_t)J * 32, (size_t)J * 32, (size_t)J * 32,  // phi[2], phi0, phi_out
                       (size_t)std::max(h->grid_cells, h->cells_grid) * 16,  // partials
-                      sizeof(IterState), sizeof(IterConfig)};
+                      sizeof(IterState), sizeof(IterConfig),
+                      // refinement (FP32 mode): tab64, par64, muw64, h0P, h0M, r0, phi_ref
+                      h->prec == OCI_FP32 ? nm * P * 64 : 0, h->prec == OCI_FP32 ? nm * 16 : 0,
+                      h->prec == OCI_FP32 ? (size_t)P * 16 : 0, h->prec == OCI_FP32 ? face : 0,
+                      h->prec == OCI_FP32 ? face : 0, h->prec == OCI_FP32 ? (size_t)J * P * 16 : 0,
+                      h->prec == OCI_FP32 ? (size_t)J * 32 : 0};
     const int ns = sizeof(sizes) / sizeof(sizes[0]);
     size_t off[32], total = 0;
     for (int i = 0; i < ns; ++i) {
@@ -790,6 +895,26 @@ int oci_create(const oci_problem *p, oci_handle **out)
     h->partials = (double *)(b + off[18]);
     h->d_st = (IterState *)(b + off[19]);
     h->d_cfg = (IterConfig *)(b + off[20]);
+    if (h->prec == OCI_FP32) {
+        h->ref_tab = (double *)(b + off[21]);
+        h->ref_par = (double *)(b + off[22]);
+        h->ref_muw = (double *)(b + off[23]);
+        h->ref_h0P = b + off[24];
+        h->ref_h0M = b + off[25];
+        h->ref_r0 = b + off[26];
+        h->ref_phi = b + off[27];
+        if (h->staged && h->ks.cells_lin_tma) {
+            h->cells_lin = h->ks.cells_lin_tma;
+            h->cfg.stall_floor = 1e-5;
+            if (const char *e = std::getenv("OCI_STALL_FLOOR")) h->cfg.stall_floor = std::atof(e);
+            if (const char *e = std::getenv("OCI_STALL_ITERS")) h->cfg.stall_iters = std::atoi(e);
+            if (cudaFuncSetAttribute(h->cells_lin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->cells_smem) !=
+                cudaSuccess) {
+                oci_destroy(h);
+                return OCI_ECUDA;
+            }
+        }
+    }
     if (cudaMallocHost(&h->h_st, sizeof(IterState)) != cudaSuccess) { oci_destroy(h); return OCI_ENOMEM; }
     if (cudaMemsetAsync(h->d_base, 0, total, h->stream) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
@@ -801,6 +926,7 @@ int oci_create(const oci_problem *p, oci_handle **out)
     if (!rc) rc = upload_boundaries(h, p->psi_bc_left, p->psi_bc_right);
     if (!rc) rc = load_state(h, p->psi0);
     if (!rc && cudaMemcpy(h->d_cfg, &h->cfg, sizeof(IterConfig), cudaMemcpyHostToDevice) != cudaSuccess) rc = OCI_ECUDA;
+    h->cfg_dev = h->cfg;
     if (rc) { oci_destroy(h); return rc; }
     *out = h;
     return OCI_OK;
@@ -816,6 +942,8 @@ void oci_destroy(oci_handle *h)
     if (h->exec_si) cudaGraphExecDestroy(h->exec_si);
     if (h->graph_oci) cudaGraphDestroy(h->graph_oci);
     if (h->graph_si) cudaGraphDestroy(h->graph_si);
+    if (h->exec_lin) cudaGraphExecDestroy(h->exec_lin);
+    if (h->graph_lin) cudaGraphDestroy(h->graph_lin);
     if (h->exec_cont) cudaGraphExecDestroy(h->exec_cont);
     if (h->graph_cont) cudaGraphDestroy(h->graph_cont);
     if (h->nn_mem) cudaFree(h->nn_mem);
@@ -840,9 +968,7 @@ int oci_set_iteration(oci_handle *h, double tol, int32_t max_iter, int32_t commi
     h->cfg.tol = tol;
     h->cfg.max_iter = max_iter;
     h->cfg.commit_unconverged = commit_unconverged ? 1 : 0;
-    CK(h, cudaStreamSynchronize(h->stream));
-    CK(h, cudaMemcpy(h->d_cfg, &h->cfg, sizeof(IterConfig), cudaMemcpyHostToDevice));
-    return OCI_OK;
+    return set_device_cfg(h, h->cfg);
 }
 
 int oci_set_stream(oci_handle *h, void *cuda_stream)
@@ -923,8 +1049,8 @@ int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_la
     timing.max_iter = 0x3fffffff;
     timing.tol = 0.0;
     timing.commit_unconverged = 0;
-    CK(h, cudaStreamSynchronize(h->stream));
-    CK(h, cudaMemcpy(h->d_cfg, &timing, sizeof(IterConfig), cudaMemcpyHostToDevice));
+    int rc0 = set_device_cfg(h, timing);
+    if (rc0) return rc0;
     IterState *st = h->d_st;
     void *a_st[] = {&st};
     CK(h, cudaLaunchKernel((const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st, 0, h->stream));
@@ -940,7 +1066,7 @@ int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_la
     float ms = 0.f;
     CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     *seconds_per_launch = ms * 1e-3 / n_iter;
-    CK(h, cudaMemcpy(h->d_cfg, &h->cfg, sizeof(IterConfig), cudaMemcpyHostToDevice));
+    if ((rc = set_device_cfg(h, h->cfg))) return rc;
     h->guess_valid = false;  // the face buffers now hold timing iterates
     return OCI_OK;
 }

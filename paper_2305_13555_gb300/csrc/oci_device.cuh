@@ -43,11 +43,11 @@ template <typename R> struct __align__(16) r4 { R x, y, z, w; };
 struct __align__(16) kmat { double k00, k01, k10, k11; };
 
 enum : int { BC_VACUUM = 0, BC_REFLECT = 1, BC_INCIDENT = 2 };
-enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NAN = 3, ST_GUARD = 4, ST_TIMEOUT = 5 };
-// k_cells modes
-enum : int { M_OCI = 0, M_SI = 1 };
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NAN = 3, ST_GUARD = 4, ST_TIMEOUT = 5, ST_STALL = 6 };
+// k_cells modes (M_LIN: correction equation of the FP32 refinement, staged kernel only)
+enum : int { M_OCI = 0, M_SI = 1, M_LIN = 2 };
 // k_percell modes
-enum : int { C_COMMIT_OCI = 0, C_COMMIT_SI = 1, C_SI_PREP = 2, C_GUESS = 3 };
+enum : int { C_COMMIT_OCI = 0, C_COMMIT_SI = 1, C_SI_PREP = 2, C_GUESS = 3, C_COMMIT_LIN = 4 };
 
 // Iteration state of the current time step (device memory, one per handle).
 struct IterState {
@@ -58,9 +58,10 @@ struct IterState {
     unsigned int arrive;  // blocks of the current launch that finished
     int launches;      // launches of the iteration kernel in this step (guard)
     int committed;     // last step advanced the state
-    int pad0;
+    int stall;         // iterations since the relative change last fell by 10%
     double resid;      // last relative change of phi
     double d2, p2;     // sum (dphi)^2, sum phi^2 of the last iteration
+    double best;       // smallest relative change since the last 10% improvement
 };
 
 struct IterConfig {
@@ -68,7 +69,8 @@ struct IterConfig {
     int commit_unconverged;
     double tol;
     int pause_at;      // iteration count at which the loop stops with the step still running (-1: never)
-    int pad0;
+    int stall_iters;   // stop with ST_STALL after this many iterations without a 10% improvement ...
+    double stall_floor;  // ... once the relative change is below this (0 disables)
 };
 
 
@@ -239,6 +241,11 @@ struct KParams {
     phi_t<R> *phi0;        // initial iterate of the step
     double *phi_out;       // published moments of the last committed step
     const float4 *matKf;   // [n_mat][2] FF capacitance (k00h,k00l,k01h,k01l),(k10h,k10l,k11h,k11l)
+    // FP32 refinement: saved halo h0, its high-precision residual r0 (per producing
+    // cell: +mu k, +mu k+1/2, -mu k, -mu k+1/2) and scalar flux phi(h0) (FF)
+    const r2<R> *h0P, *h0M;
+    const r4<R> *r0;
+    const float2 *phi_ref;
     double *partials;      // [gridDim.x][2]
     IterState *st;
     const IterConfig *cfg;
@@ -380,6 +387,18 @@ __device__ __forceinline__ void finalize_iteration(double d2, double p2, double 
             if (!(resid == resid) || !(a == a) || !(b == b) || isinf(b)) ns = ST_NAN;
             else if (resid < cfg->tol) ns = ST_CONVERGED;
             else if (it >= cfg->max_iter) ns = ST_MAXITER;
+            if (ns == ST_RUNNING && cfg->stall_floor > 0.0) {
+                // rounding-noise floor: the change stopped falling well above tol
+                // (stall_iters < 0: stop as soon as it is below stall_floor)
+                if (cfg->stall_iters < 0) {
+                    if (resid < cfg->stall_floor) ns = ST_STALL;
+                } else if (resid < 0.9 * st->best) {
+                    st->best = resid;
+                    st->stall = 0;
+                } else if (++st->stall >= cfg->stall_iters && resid < cfg->stall_floor) {
+                    ns = ST_STALL;
+                }
+            }
             st->status = ns;
             const bool go_on = ns == ST_RUNNING && it != cfg->pause_at;  // pause: host resumes the step
             if (use_cond) cudaGraphSetConditional(cond, go_on ? 1u : 0u);
@@ -715,14 +734,17 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
 
     int iter, base;
     if (!iteration_prologue(p, iter, base)) return;
-    const int frd = MODE == M_OCI ? ((base + iter) & 1) : base;
+    constexpr bool PING = MODE == M_OCI || MODE == M_LIN;  // iterate in the face buffers
+    const int frd = PING ? ((base + iter) & 1) : base;
     const int fwr = frd ^ 1;
     const phi_t<R> *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
     phi_t<R> *phw = p.phi[(iter + 1) & 1];
     const r2<R> *fPr = p.faceP[frd], *fMr = p.faceM[frd];
     r2<R> *fPw = p.faceP[fwr], *fMw = p.faceM[fwr];
-    const bool refl_l = MODE == M_OCI && p.bc_left == BC_REFLECT;
-    const bool refl_r = MODE == M_OCI && p.bc_right == BC_REFLECT;
+    const bool refl_l = PING && p.bc_left == BC_REFLECT;
+    const bool refl_r = PING && p.bc_right == BC_REFLECT;
+    // M_LIN: the time-edge slot of the ring carries r0 instead of psi_{k-1/2}
+    const r4<R> *edge_src = MODE == M_LIN ? p.r0 : p.psi_edge;
 
     // shared memory: [barriers][per-warp transpose buffers][per-warp rings]
     const unsigned oP = 0, oM = round16(CPC * P * 8u), oE = 2 * round16(CPC * P * 8u);
@@ -754,7 +776,7 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
         mbar_expect_tx_arrive(bar, 2 * bF + bE + bQ + bT);
         bulk_g2s(st + oP, fPr + (size_t)c0 * P, bF, bar);
         bulk_g2s(st + oM, fMr + (size_t)(c0 + 1) * P, bF, bar);
-        bulk_g2s(st + oE, p.psi_edge + (size_t)c0 * P, bE, bar);
+        bulk_g2s(st + oE, edge_src + (size_t)c0 * P, bE, bar);
         bulk_g2s(st + oQ, p.cellq + c0, bQ, bar);
         bulk_g2s(st + oT, p.mat + c0, bT, bar);
     };
@@ -804,13 +826,15 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
         const int *sT = reinterpret_cast<const int *>(st + oT);
         // phi^l of the values this lane owns in phase C, fetched now so the
         // load overlaps phases A and B
-        float2 old_phi[NOWN];
+        float2 old_phi[NOWN], ref_phi[NOWN];
 #pragma unroll
         for (int k = 0; k < NOWN; ++k) {
             const int f = lane * NOWN + k;
             const int g = f / V, v = f % V;
             const int cell = chunk * CPC + (v >> 2) * SPW + g;
-            old_phi[k] = (g < SPW && cell < J) ? __ldcg(phr + 4 * (size_t)cell + (v & 3)) : make_float2(0.f, 0.f);
+            const bool ok = g < SPW && cell < J;
+            old_phi[k] = ok ? __ldcg(phr + 4 * (size_t)cell + (v & 3)) : make_float2(0.f, 0.f);
+            ref_phi[k] = (MODE == M_LIN && ok) ? __ldg(p.phi_ref + 4 * (size_t)cell + (v & 3)) : make_float2(0.f, 0.f);
         }
         // ---------------- phase A: y = A^{-1} c per ordinate pair; lane partials
         // of the moments w (y+ + conj(y-)) go to the transpose buffer
@@ -834,7 +858,8 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                     const Coef<R> &a = ac[t];
                     const r2<R> inP = (refl_l && cell == 0) ? ld2(fMr + pp) : sP[cl * P + pp];
                     const r2<R> inM = (refl_r && cell == J - 1) ? ld2(fPr + (size_t)J * P + pp) : sM[cl * P + pp];
-                    PairRhs<R> u = pair_rhs_fixed(qd, ce, sE[cl * P + pp]);
+                    PairRhs<R> u = MODE == M_LIN ? PairRhs<R>{0, 0, 0, 0, 0, 0, 0, 0}
+                                                 : pair_rhs_fixed(qd, ce, sE[cl * P + pp]);
                     if (MODE == M_SI) {
                         u.ukr += fkl; u.uki += fkr; u.uhr += fhl; u.uhi += fhr;
                         u.vkr += fkl; u.vki -= fkr; u.vhr += fhl; u.vhi -= fhr;
@@ -892,7 +917,7 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
             const int row = v >> 2, comp = v & 3;
             const int cell = chunk * CPC + row * SPW + g;
             ff phi;
-            if (MODE == M_OCI) {
+            if (MODE != M_SI) {
                 ff r_par;
                 if constexpr (NOWN >= 4) {
                     r_par = own[k ^ 2];
@@ -916,7 +941,9 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                 const float2 old = old_phi[k];
                 const float d = ff_diff(phi, ff{old.x, old.y});
                 accf_d2 = __fmaf_rn(d, d, accf_d2);
-                accf_p2 = __fmaf_rn(phi.h, phi.h, accf_p2);
+                // norm of the whole iterate (M_LIN: phi(h0) + correction)
+                const float tot = MODE == M_LIN ? __fadd_rn(ref_phi[k].x, phi.h) : phi.h;
+                accf_p2 = __fmaf_rn(tot, tot, accf_p2);
                 phw[4 * (size_t)cell + comp] = make_float2(phi.h, phi.l);
                 xp[g * V + v] = __fadd_rn(phi.h, phi.l);  // phi of (segment g, value v) for phase D
             }
@@ -937,8 +964,9 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                 const int pp = ls + LPC * t;
                 if (pp >= P) continue;
                 const Coef<R> &a = ac[t];
-                PairRhs<R> u = pair_rhs_fixed(qd, ce, sE[cl * P + pp]);
-                if (MODE == M_OCI) {
+                PairRhs<R> u = MODE == M_LIN ? PairRhs<R>{0, 0, 0, 0, 0, 0, 0, 0}
+                                             : pair_rhs_fixed(qd, ce, sE[cl * P + pp]);
+                if (PING) {
                     const r2<R> inP = (refl_l && cell == 0) ? ld2(fMr + pp) : sP[cl * P + pp];
                     const r2<R> inM = (refl_r && cell == J - 1) ? ld2(fPr + (size_t)J * P + pp) : sM[cl * P + pp];
                     u.ukr += mw[t].x * inP.x; u.uhr += mw[t].x * inP.y;
@@ -947,11 +975,15 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                 // +mu: Im(A^{-1}(u + s Phi)); -mu: Re(A^{-1}(u + s conj(Phi)))
                 const R uk_i = u.uki + Fkr, uk_r = u.ukr + Fkl, uh_i = u.uhi + Fhr, uh_r = u.uhr + Fhl;
                 const R vk_r = u.vkr + Fkl, vk_i = u.vki - Fkr, vh_r = u.vhr + Fhl, vh_i = u.vhi - Fhr;
-                const R ok = a.pr * uk_i + a.pi * uk_r + a.rr * uh_i + a.ri * uh_r;
-                const R oh = a.ur * uk_i + a.ui * uk_r + a.vr * uh_i + a.vi * uh_r;
-                const R mk = a.pr * vk_r - a.pi * vk_i + a.rr * vh_r - a.ri * vh_i;
-                const R mh = a.ur * vk_r - a.ui * vk_i + a.vr * vh_r - a.vi * vh_i;
-                if (MODE == M_OCI) {
+                R ok = a.pr * uk_i + a.pi * uk_r + a.rr * uh_i + a.ri * uh_r;
+                R oh = a.ur * uk_i + a.ui * uk_r + a.vr * uh_i + a.vi * uh_r;
+                R mk = a.pr * vk_r - a.pi * vk_i + a.rr * vh_r - a.ri * vh_i;
+                R mh = a.ur * vk_r - a.ui * vk_i + a.vr * vh_r - a.vi * vh_i;
+                if (MODE == M_LIN) {  // d^{l+1} = B d^l + r0
+                    const r4<R> r0v = sE[cl * P + pp];
+                    ok += r0v.x; oh += r0v.y; mk += r0v.z; mh += r0v.w;
+                }
+                if (PING) {
                     st2(fPw + (size_t)(cell + 1) * P + pp, ok, oh);
                     st2(fMw + (size_t)cell * P + pp, mk, mh);
                 } else {
@@ -994,9 +1026,10 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
     bool go = true;
     int frd = 0, fgs = 0;
     const phi_t<R> *phi_psi = nullptr, *phi_pub = nullptr;
-    if (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI) {
+    constexpr bool COMMIT = MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI || MODE == C_COMMIT_LIN;
+    if (COMMIT) {
         go = iter >= 1 && (status == ST_CONVERGED || (status == ST_MAXITER && p.cfg->commit_unconverged));
-        if (MODE == C_COMMIT_OCI) {
+        if (MODE == C_COMMIT_OCI || MODE == C_COMMIT_LIN) {
             frd = (base + iter - 1) & 1;
             fgs = frd ^ 1;
             phi_psi = p.phi[iter & 1];
@@ -1017,8 +1050,8 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
         fgs = st->base_next;
     }
     if (!go) return;
-    const bool refl_l = MODE == C_COMMIT_OCI && p.bc_left == BC_REFLECT;
-    const bool refl_r = MODE == C_COMMIT_OCI && p.bc_right == BC_REFLECT;
+    const bool refl_l = (MODE == C_COMMIT_OCI || MODE == C_COMMIT_LIN) && p.bc_left == BC_REFLECT;
+    const bool refl_r = (MODE == C_COMMIT_OCI || MODE == C_COMMIT_LIN) && p.bc_right == BC_REFLECT;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     R mu[PPL];
@@ -1040,16 +1073,28 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
             qdr[r] = valid ? ldg4(p.cellq + cell) : r4<R>{0, 0, 0, 0};
             F[r][0] = F[r][1] = F[r][2] = F[r][3] = 0;
             if (MODE != C_GUESS && valid) load_phi4<R>(phi_psi, cell, F[r][0], F[r][1], F[r][2], F[r][3]);
+            if (MODE == C_COMMIT_LIN && valid) {
+                R a0, a1, a2, a3;
+                load_phi4<R>(reinterpret_cast<const phi_t<R> *>(p.phi_ref), cell, a0, a1, a2, a3);
+                F[r][0] += a0; F[r][1] += a1; F[r][2] += a2; F[r][3] += a3;
+            }
 #pragma unroll
             for (int i = 0; i < PPL; ++i) {
                 const int pp = ls + LPC * i;
                 const bool ok = valid && pp < P;
                 per[r][i] = ok ? ld4(p.psi_edge + (size_t)cell * P + pp) : r4<R>{0, 0, 0, 0};
                 inPr[r][i] = inMr[r][i] = r2<R>{0, 0};
-                if (ok && (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI)) {
+                if (ok && COMMIT) {
                     inPr[r][i] = (refl_l && cell == 0) ? ld2(p.faceM[frd] + pp) : ld2(p.faceP[frd] + (size_t)cell * P + pp);
                     inMr[r][i] = (refl_r && cell == J - 1) ? ld2(p.faceP[frd] + (size_t)J * P + pp)
                                                           : ld2(p.faceM[frd] + (size_t)(cell + 1) * P + pp);
+                    if (MODE == C_COMMIT_LIN) {  // incident h0 + d
+                        const r2<R> a = (refl_l && cell == 0) ? ld2(p.h0M + pp) : ld2(p.h0P + (size_t)cell * P + pp);
+                        const r2<R> b = (refl_r && cell == J - 1) ? ld2(p.h0P + (size_t)J * P + pp)
+                                                                 : ld2(p.h0M + (size_t)(cell + 1) * P + pp);
+                        inPr[r][i].x += a.x; inPr[r][i].y += a.y;
+                        inMr[r][i].x += b.x; inMr[r][i].y += b.y;
+                    }
                 }
             }
         }
@@ -1104,6 +1149,16 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
                 for (int c = ls; c < 4; c += LPC) {
                     p.phi_out[4 * (size_t)cell + c] = PhiStore<R>::wide(__ldcg(phi_pub + 4 * (size_t)cell + c));
                     p.phi0[4 * (size_t)cell + c] = __ldcg(phi_pub + 4 * (size_t)cell + 2 + (c & 1));
+                }
+            }
+            if constexpr (MODE == C_COMMIT_LIN && sizeof(R) == 4) {
+                for (int c = ls; c < 4; c += LPC) {
+                    const float2 a = __ldcg(phi_pub + 4 * (size_t)cell + c), b = p.phi_ref[4 * (size_t)cell + c];
+                    p.phi_out[4 * (size_t)cell + c] = (double)a.x + (double)a.y + (double)b.x + (double)b.y;
+                    const float2 ah = __ldcg(phi_pub + 4 * (size_t)cell + 2 + (c & 1));
+                    const float2 bh = p.phi_ref[4 * (size_t)cell + 2 + (c & 1)];
+                    const ff t = ff_add(ff{ah.x, ah.y}, ff{bh.x, bh.y});
+                    p.phi0[4 * (size_t)cell + c] = make_float2(t.h, t.l);
                 }
             }
         }
@@ -1175,6 +1230,94 @@ __global__ void __launch_bounds__(256) k_lift(const KParams<R> p, const double *
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 refinement, residual pass: one OCI application G(h0) evaluated in FP64
+// from the saved FP32 halo h0 (same inputs the FP32 iteration uses), giving
+// the high-precision residual r0 = G(h0) - h0 of every outgoing corner and the
+// scalar flux phi(h0).  The correction d then solves d = B d + r0 in FP32,
+// where B is the same OCI map with no source and homogeneous boundary data.
+// ---------------------------------------------------------------------------
+struct RefineArgs {
+    const double *tab64;     // [n_mat][P][8] complex entries of A_{+mu}^{-1}
+    const double *matpar64;  // [n_mat][2] (e, s)
+    const double *muw64;     // [P][2]
+    r4<float> *r0;           // out [J][P]
+    float2 *phi_ref;         // out [J][4] double-float
+};
+
+template <int LPC, int PPL>
+__global__ void __launch_bounds__(256) k_refine_residual(const KParams<float> p, const RefineArgs q)
+{
+    constexpr int SPW = 32 / LPC;
+    const int lane = threadIdx.x & 31;
+    const int seg = lane / LPC, ls = lane % LPC;
+    const int J = p.J, P = p.P;
+    const bool refl_l = p.bc_left == BC_REFLECT, refl_r = p.bc_right == BC_REFLECT;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int c0 = gw * SPW; c0 < J; c0 += nwarps * SPW) {
+        const int cell = c0 + seg;
+        const bool valid = cell < J;
+        const int m = valid ? __ldg(p.mat + cell) : 0;
+        const double e = q.matpar64[2 * m], sc = q.matpar64[2 * m + 1];
+        double qd[4] = {0, 0, 0, 0};
+        if (valid) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(p.cellq + cell));
+            qd[0] = v.x; qd[1] = v.y; qd[2] = v.z; qd[3] = v.w;
+        }
+        double u[PPL][8];
+        double mom[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int t = 0; t < PPL; ++t) {
+            const int pp = ls + LPC * t;
+#pragma unroll
+            for (int z = 0; z < 8; ++z) u[t][z] = 0.0;
+            if (!(valid && pp < P)) continue;
+            const double *a = q.tab64 + ((size_t)m * P + pp) * 8;
+            const double mu = q.muw64[2 * pp], w = q.muw64[2 * pp + 1];
+            const r2<float> inP = (refl_l && cell == 0) ? p.h0M[pp] : p.h0P[(size_t)cell * P + pp];
+            const r2<float> inM = (refl_r && cell == J - 1) ? p.h0P[(size_t)J * P + pp] : p.h0M[(size_t)(cell + 1) * P + pp];
+            const float4 pe = *reinterpret_cast<const float4 *>(p.psi_edge + (size_t)cell * P + pp);
+            double *uu = u[t];
+            uu[0] = qd[0] + e * pe.x + mu * inP.x; uu[1] = qd[1] + e * pe.y; uu[2] = qd[2] + mu * inP.y; uu[3] = qd[3];
+            uu[4] = qd[0] + e * pe.z; uu[5] = -(qd[1] + e * pe.w + mu * inM.x); uu[6] = qd[2]; uu[7] = -(qd[3] + mu * inM.y);
+            const Coef<double> c{a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7]};
+            double ykr, yki, yhr, yhi, zkr, zki, zhr, zhi;
+            ainv(c, uu[0], uu[1], uu[2], uu[3], ykr, yki, yhr, yhi);
+            ainv(c, uu[4], uu[5], uu[6], uu[7], zkr, zki, zhr, zhi);
+            mom[0] += w * (ykr + zkr); mom[1] += w * (yki - zki); mom[2] += w * (yhr + zhr); mom[3] += w * (yhi - zhi);
+        }
+#pragma unroll
+        for (int o = LPC / 2; o >= 1; o >>= 1)
+#pragma unroll
+            for (int z = 0; z < 4; ++z) mom[z] += __shfl_xor_sync(FULL, mom[z], o);
+        const kmat K = p.matK[m];
+        const double phi[4] = {K.k00 * mom[0] + K.k01 * mom[2], K.k00 * mom[1] + K.k01 * mom[3],
+                               K.k10 * mom[0] + K.k11 * mom[2], K.k10 * mom[1] + K.k11 * mom[3]};
+        if (!valid) continue;
+        const double Fkl = sc * phi[0], Fkr = sc * phi[1], Fhl = sc * phi[2], Fhr = sc * phi[3];
+#pragma unroll
+        for (int t = 0; t < PPL; ++t) {
+            const int pp = ls + LPC * t;
+            if (pp >= P) continue;
+            const double *a = q.tab64 + ((size_t)m * P + pp) * 8;
+            const double *uu = u[t];
+            const double uk_i = uu[1] + Fkr, uk_r = uu[0] + Fkl, uh_i = uu[3] + Fhr, uh_r = uu[2] + Fhl;
+            const double vk_r = uu[4] + Fkl, vk_i = uu[5] - Fkr, vh_r = uu[6] + Fhl, vh_i = uu[7] - Fhr;
+            const double ok = a[0] * uk_i + a[1] * uk_r + a[2] * uh_i + a[3] * uh_r;
+            const double oh = a[4] * uk_i + a[5] * uk_r + a[6] * uh_i + a[7] * uh_r;
+            const double mk = a[0] * vk_r - a[1] * vk_i + a[2] * vh_r - a[3] * vh_i;
+            const double mh = a[4] * vk_r - a[5] * vk_i + a[6] * vh_r - a[7] * vh_i;
+            const r2<float> hp = p.h0P[(size_t)(cell + 1) * P + pp], hm = p.h0M[(size_t)cell * P + pp];
+            q.r0[(size_t)cell * P + pp] = r4<float>{(float)(ok - hp.x), (float)(oh - hp.y), (float)(mk - hm.x), (float)(mh - hm.y)};
+        }
+        for (int cc = ls; cc < 4; cc += LPC) {
+            const float h = (float)phi[cc];
+            q.phi_ref[4 * (size_t)cell + cc] = make_float2(h, (float)(phi[cc] - (double)h));
+        }
+    }
+}
+
 // Step prologue: reset the iteration state for a new time step.
 static __global__ void k_step_begin(IterState *st)
 {
@@ -1184,6 +1327,19 @@ static __global__ void k_step_begin(IterState *st)
     st->launches = 0;
     st->base = st->base_next;
     st->resid = 0.0;
+    st->stall = 0;
+    st->best = __longlong_as_double(0x7ff0000000000000LL);
+}
+
+// Resume a stalled step with the correction iteration: the high-precision
+// residual pass counts as one iteration.
+static __global__ void k_refine_setup(IterState *st)
+{
+    st->iter += 1;
+    st->status = ST_RUNNING;
+    st->stall = 0;
+    st->best = __longlong_as_double(0x7ff0000000000000LL);
+    st->arrive = 0u;
 }
 
 // ---------------------------------------------------------------------------

@@ -18,6 +18,9 @@ struct KernelSet {
     const void *cells_oci_tma;  // k_cells_tma<M_OCI> (FP32, even P) or nullptr
     const void *cells_si_tma;   // k_cells_tma<M_SI>
     int tma_stages;             // ring depth of the staged kernels
+    const void *cells_lin_tma;  // k_cells_tma<M_LIN> (FP32 refinement) or nullptr
+    const void *commit_lin;     // k_percell<C_COMMIT_LIN>
+    const void *refine;         // k_refine_residual
     int cells_per_warp;      // cells handled by one warp pass of k_cells (CHUNK * 32 / LPC)
     int cells_per_warp_pc;   // cells per warp of k_percell (32 / LPC)
 };

@@ -21,12 +21,16 @@ static void fill(KernelSet *k)
     k->lift_corr = (const void *)&k_lift<float, LPC, PPL, LIFT_CORR>;
     k->cells_oci_tma = nullptr;
     k->cells_si_tma = nullptr;
+    k->cells_lin_tma = nullptr;
     k->tma_stages = 0;
     if constexpr (LPC >= 2) {
         k->cells_oci_tma = (const void *)&k_cells_tma<LPC, PPL, CHUNK, kStages, M_OCI>;
         k->cells_si_tma = (const void *)&k_cells_tma<LPC, PPL, CHUNK, kStages, M_SI>;
+        k->cells_lin_tma = (const void *)&k_cells_tma<LPC, PPL, CHUNK, kStages, M_LIN>;
         k->tma_stages = kStages;
     }
+    k->commit_lin = (const void *)&k_percell<float, LPC, PPL, C_COMMIT_LIN>;
+    k->refine = (const void *)&k_refine_residual<LPC, PPL>;
     k->cells_per_warp = CHUNK * (32 / LPC);
     k->cells_per_warp_pc = 32 / LPC;
 }
@@ -44,6 +48,7 @@ bool kernel_set_f32(int lpc, int ppl, KernelSet *out)
         if (const char *e = std::getenv("OCI_TMA_STAGES"); e && e[0] == '3') {
             out->cells_oci_tma = (const void *)&k_cells_tma<32, 1, 8, 3, M_OCI>;
             out->cells_si_tma = (const void *)&k_cells_tma<32, 1, 8, 3, M_SI>;
+            out->cells_lin_tma = (const void *)&k_cells_tma<32, 1, 8, 3, M_LIN>;
             out->tma_stages = 3;
         }
         return true;

@@ -17,6 +17,9 @@ static void fill(KernelSet *k)
     k->lift_corr = (const void *)&k_lift<double, LPC, PPL, LIFT_CORR>;
     k->cells_oci_tma = nullptr;
     k->cells_si_tma = nullptr;
+    k->cells_lin_tma = nullptr;
+    k->commit_lin = nullptr;
+    k->refine = nullptr;
     k->tma_stages = 0;
     k->cells_per_warp = CHUNK * (32 / LPC);
     k->cells_per_warp_pc = 32 / LPC;

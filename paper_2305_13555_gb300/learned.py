@@ -25,7 +25,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "data", "cnn_weights.npy")
 
 
-def trajectories(seeds, J=4096, N=16, n_steps=20, precision="fp32", problem=None):
+def trajectories(seeds, J=4096, N=16, n_steps=20, precision="fp64", problem=None):
     """Run the OCI solver on one seeded slab per seed; returns device tensors
     phi [T][n_steps+1][J][4] (float64; index 0 = initial moments), stat
     [T][J][4] and qfeat [T][J] (float32), and the iteration counts."""

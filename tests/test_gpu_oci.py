@@ -244,3 +244,40 @@ def test_fp32_ill_conditioned_capacitance(method):
             rc, st = s.step(method)
             assert rc == pkg.OCI_OK, (rc, st)
             assert _rel(s.fluxes(), ref["phi_steps"][k]) < 5 * FP32_TOL
+
+
+def test_fp32_refinement_forced(monkeypatch):
+    """Force the FP32 refinement (stop as soon as the change is below 1e-3):
+    r0 = G(h0) - h0 in FP64, the correction iterated in FP32; the committed
+    steps match the FP64 path to the FP32 bound."""
+    prob = workloads.hetero(seed=5, J=5000, N=16, n_steps=4, bc_left="reflect", bc_right="incident")
+    prob["psi_bc_right"] = np.full((8, 2), 0.3)
+    ref = []
+    with pkg.Solver(prob, precision="fp64", tol=1e-10) as s:
+        for _ in range(4):
+            assert s.step()[0] == pkg.OCI_OK
+            ref.append(s.fluxes())
+    monkeypatch.setenv("OCI_STALL_FLOOR", "1e-3")
+    monkeypatch.setenv("OCI_STALL_ITERS", "-1")
+    with pkg.Solver(prob, precision="fp32", tol=1e-8) as s:
+        for k in range(4):
+            rc, st = s.step()
+            assert rc == pkg.OCI_OK and st["refined"] == 1, (rc, st)
+            assert _rel(s.fluxes(), ref[k]) < FP32_TOL
+
+
+def test_fp32_stalling_trajectory_converges():
+    """A training slab whose FP32 iteration stalls at the rounding-noise floor
+    (seed 100044: the FP64 path needs ~35 iterations per step) now converges
+    every step, via the refinement when needed, and matches the FP64 path."""
+    prob = workloads.config5_train(100044, J=4096, N=16, n_steps=20)
+    ref = []
+    with pkg.Solver(prob, precision="fp64", tol=1e-8) as s:
+        for _ in range(20):
+            assert s.step()[0] == pkg.OCI_OK
+            ref.append(s.fluxes())
+    with pkg.Solver(prob, precision="fp32", tol=1e-8, max_iter=5000) as s:
+        for k in range(20):
+            rc, st = s.step()
+            assert rc == pkg.OCI_OK, (k, rc, st)
+            assert _rel(s.fluxes(), ref[k]) < FP32_TOL
