@@ -84,6 +84,30 @@ int oci_nn_train_step(float *params, float *adam_m, float *adam_v, int32_t step,
                       const float *tgt, int32_t batch, int32_t n_cells, double *loss, void *workspace,
                       size_t workspace_bytes, void *stream);
 
+/* Largest n_cells accepted by oci_nn_forward_noalloc. */
+#define OCI_NN_NOALLOC_MAX_CELLS 16384
+
+/* Inference without any allocation (the paper has no counterpart): same
+ * network, inputs and outputs as oci_nn_forward for a single sample (batch 1)
+ * of at most OCI_NN_NOALLOC_MAX_CELLS cells, but the scratch memory (BF16
+ * weights and two activation buffers, about 4.2 MB) is a fixed array inside
+ * this library instead of a caller-provided workspace.  For callers that
+ * cannot call cudaMalloc or pass scratch memory: code running where an
+ * allocation would synchronise the device or is forbidden (a real-time step
+ * loop, an inference hook inside another program's time step that owns the
+ * memory plan), or a host that only hands over its input and output buffers.
+ * Every GPU that loads the library holds the array until the process exits.
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make the first call before any stream capture.  All
+ * calls share the one array and it keeps the last call's contents: calls that
+ * can overlap on the GPU (different streams, concurrent host threads) race,
+ * so serialise them.  Nothing in it needs to start at zero.  in [13][n_cells]
+ * and out [4][n_cells] are device pointers, params [oci_nn_param_count()].
+ * Calls no cudaMalloc / cudaFree or allocating library routine.  Returns
+ * 1 (OCI_EINVAL) for NULL pointers, n_cells < 1 or n_cells >
+ * OCI_NN_NOALLOC_MAX_CELLS, 3 (OCI_ECUDA) on a CUDA error. */
+int oci_nn_forward_noalloc(const float *params, const float *in, int32_t n_cells, float *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,7 @@ SIGNATURES = {
                                         ctypes.c_size_t, _VP]),
     "oci_nn_train_step": (ctypes.c_int, [_VP, _VP, _VP, _I32, ctypes.c_float, _VP, _VP, _I32, _I32,
                                          ctypes.POINTER(ctypes.c_double), _VP, ctypes.c_size_t, _VP]),
+    "oci_nn_forward_noalloc": (ctypes.c_int, [_VP, _VP, _I32, _VP, _VP]),
     "oci_last_cuda_error": (ctypes.c_char_p, [_VP]),
 }
 

@@ -13,6 +13,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 #include "../../include/oci_nn.h"
 
@@ -388,6 +389,35 @@ int loss_grad(const float *params, const float *in, const float *tgt, int B, int
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
+// ------------------------------------------------- allocation-free inference
+// Scratch of oci_nn_forward_noalloc: BF16 weights and two activation buffers
+// of 32 channels x OCI_NN_NOALLOC_MAX_CELLS cells, in one file-scope device
+// array that every GPU loading this library keeps until the process exits.
+constexpr size_t kStaticWeightBytes = ((size_t)NPARAM * 2 + 255) & ~(size_t)255;
+constexpr size_t kStaticActFloats = (size_t)MAXC * OCI_NN_NOALLOC_MAX_CELLS;
+static __device__ __align__(256) unsigned char g_nn_scratch[kStaticWeightBytes + 2 * kStaticActFloats * 4];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_nn_scratch on the current device (the host-side symbol
+// is only a stand-in).  Looked up once per device, with that device current.
+int scratch_address(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 3;
+    if (dev < 0 || dev >= kMaxDevices) return 1;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_nn_scratch) != cudaSuccess || !p) return 3;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return 0;
+}
+
 }  // namespace ocinn
 
 using namespace ocinn;
@@ -464,6 +494,28 @@ int oci_nn_train_step(float *params, float *adam_m, float *adam_v, int32_t step,
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     k_adam<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, adam_m, adam_v, w.grad, NPARAM, lr, b1, b2, 1e-8f, c1, c2,
                                                  w.wb);
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int oci_nn_forward_noalloc(const float *params, const float *in, int32_t n_cells, float *out, void *stream)
+{
+    if (!params || !in || !out || n_cells < 1) return 1;
+    if (n_cells > OCI_NN_NOALLOC_MAX_CELLS) return 1;  // beyond the static scratch
+    void *scratch = nullptr;
+    const int rc = scratch_address(&scratch);
+    if (rc) return rc;
+    __nv_bfloat16 *wb = (__nv_bfloat16 *)scratch;
+    float *a = (float *)((char *)scratch + kStaticWeightBytes);
+    float *b = a + kStaticActFloats;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int J = n_cells;
+    const dim3 grid((J + TX - 1) / TX, 1);
+    k_to_bf16<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, NPARAM, wb);
+    k_conv<13, 32, true, false><<<grid, TX, 0, s>>>(in, nullptr, wb + layer_off(0), params + layer_off(0) + layer_w(0), a, J);
+    k_conv<32, 32, true, false><<<grid, TX, 0, s>>>(a, nullptr, wb + layer_off(1), params + layer_off(1) + layer_w(1), b, J);
+    k_conv<32, 32, true, false><<<grid, TX, 0, s>>>(b, nullptr, wb + layer_off(2), params + layer_off(2) + layer_w(2), a, J);
+    k_conv<32, 32, true, false><<<grid, TX, 0, s>>>(a, nullptr, wb + layer_off(3), params + layer_off(3) + layer_w(3), b, J);
+    k_conv<32, 4, false, false><<<grid, TX, 0, s>>>(b, nullptr, wb + layer_off(4), params + layer_off(4) + layer_w(4), out, J);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
