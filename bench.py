@@ -8,7 +8,9 @@ back-substitution, residual -- every iteration, plus the end-of-step commit.
 
 Default workload: the production homogeneous slab (65536 cells, S_64, Sigma = 1,
 c = 0.9, dx = 0.1 mfp, dt = 0.05, v = 1, Q = 1, reflecting left / vacuum right),
-FP32 angular flux with compensated moments and FP64 capacitance / residual.
+FP32 angular flux with compensated moments and double-float capacitance /
+residual difference.  ``compare`` adds SI and FP64 OCI on the same slab, and the
+plain-vs-learned-guess comparison on the thin-cell deployment slab.
 ``value`` = cell-ordinate updates per second (cells x ordinates x iterations /
 device time), summed over replicas.  Prints one JSON line.
 
@@ -211,6 +213,7 @@ def run_ours(args, rank, world):
     compare = {}
     if not args.no_compare and rank == 0:
         compare = run_compare(args, pkg, torch, stream)
+        compare["learned_guess"] = run_learned(args, pkg, torch, stream)
     return {
         "value": value, "units": units, "dev_time": dev_time, "wall": wall, "iters": iters, "launches": launches,
         "roofline": roofline, "e2e": e2e, "clocks": clk, "desc": desc, "J": J, "N": N, "compare": compare,
@@ -242,6 +245,42 @@ def run_compare(args, pkg, torch, stream):
         if ok:
             out[name] = {"updates_per_s": J * N * sum(its) / sum(secs), "s_per_step": sum(secs) / len(secs),
                          "iters_per_step": sum(its) / len(its)}
+    return out
+
+
+def run_learned(args, pkg, torch, stream):
+    """The metric's "plain vs NN+FP32" part on the thin-cell deployment slab
+    (131072 cells, S_64, sigma_t dx ~ U(0.01, 0.1), c ~ U(0.9, 0.999), dt = 0.02):
+    seconds and iterations per converged step of plain FP32 OCI, FP32 OCI with
+    the trained network's initial guess, plain FP64 OCI and FP32 SI, each from
+    the same initial state, after the same warm-up steps."""
+    from paper_2305_13555_gb300 import learned
+    if not os.path.exists(learned.DEFAULT_WEIGHTS):
+        return {"unavailable": "no trained weights"}
+    W = learned.load_weights()
+    prob = workloads.config5_deploy(args.nn_seed, J=131072, N=64, n_steps=16)
+    out = {"workload": f"config-5 deployment slab seed {args.nn_seed}: 131072 cells, S_64, thin cells "
+                       "(sigma_t dx 0.01-0.1), c 0.9-0.999, dt 0.02, vacuum/vacuum, tol 1e-8"}
+    for name, prec, method, nn, n_w, n_t in (("fp32_plain", "fp32", "oci", False, 2, 6),
+                                              ("fp32_nn_guess", "fp32", "oci", True, 2, 6),
+                                              ("fp64_plain", "fp64", "oci", False, 2, 2),
+                                              ("si_fp32", "fp32", "si", False, 2, 2)):
+        s = pkg.Solver(prob, precision=prec, tol=1e-8, stream=stream.cuda_stream, max_iter=50000)
+        if nn:
+            pkg.oci_nn_attach(s.h, W, pkg.OCI_NN_GUESS, 50)
+        its, secs, ok = [], [], True
+        for k in range(n_w + n_t):
+            rc, st = s.step(method)
+            if rc != pkg.OCI_OK:
+                ok = False
+                break
+            if k >= n_w:
+                its.append(st["iters"])
+                secs.append(st["seconds"])
+        s.close()
+        out[name] = ({"s_per_step": sum(secs) / len(secs), "iters_per_step": sum(its) / len(its),
+                      "updates_per_s": 131072 * 64 * sum(its) / sum(secs), "steps_timed": n_t,
+                      "after_steps": n_w} if ok else {"failed_status": rc})
     return out
 
 
@@ -305,6 +344,7 @@ def main():
     ap.add_argument("--c", type=float, default=0.9)
     ap.add_argument("--dx", type=float, default=0.1)
     ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--nn-seed", type=int, default=8)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

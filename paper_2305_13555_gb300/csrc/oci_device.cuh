@@ -858,9 +858,17 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                     const Coef<R> &a = ac[t];
                     const r2<R> inP = (refl_l && cell == 0) ? ld2(fMr + pp) : sP[cl * P + pp];
                     const r2<R> inM = (refl_r && cell == J - 1) ? ld2(fPr + (size_t)J * P + pp) : sM[cl * P + pp];
-                    PairRhs<R> u = MODE == M_LIN ? PairRhs<R>{0, 0, 0, 0, 0, 0, 0, 0}
-                                                 : pair_rhs_fixed(qd, ce, sE[cl * P + pp]);
+                    r4<R> *slot = const_cast<r4<R> *>(sE) + cl * P + pp;  // this lane's own (cell, pair) slot
+                    const r4<R> pe = *slot;                               // psi_{k-1/2} (M_LIN: r0)
+                    PairRhs<R> u = MODE == M_LIN ? PairRhs<R>{0, 0, 0, 0, 0, 0, 0, 0} : pair_rhs_fixed(qd, ce, pe);
+                    r4<R> yo;
                     if (MODE == M_SI) {
+                        // outgoing part of A^{-1} c_fixed; the next sweep's offset adds
+                        // s (A^{-1} phi^{l+1})_out in phase E
+                        yo.x = a.pr * u.uki + a.pi * u.ukr + a.rr * u.uhi + a.ri * u.uhr;
+                        yo.y = a.ur * u.uki + a.ui * u.ukr + a.vr * u.uhi + a.vi * u.uhr;
+                        yo.z = a.pr * u.vkr - a.pi * u.vki + a.rr * u.vhr - a.ri * u.vhi;
+                        yo.w = a.ur * u.vkr - a.ui * u.vki + a.vr * u.vhr - a.vi * u.vhi;
                         u.ukr += fkl; u.uki += fkr; u.uhr += fhl; u.uhi += fhr;
                         u.vkr += fkl; u.vki -= fkr; u.vhr += fhl; u.vhi -= fhr;
                         if (cell == J - 1 && p.bc_right == BC_REFLECT)
@@ -871,6 +879,11 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                     R ykr, yki, yhr, yhi, zkr, zki, zhr, zhi;
                     ainv(a, u.ukr, u.uki, u.uhr, u.uhi, ykr, yki, yhr, yhi);
                     ainv(a, u.vkr, u.vki, u.vhr, u.vhi, zkr, zki, zhr, zhi);
+                    if (MODE != M_SI) {  // outgoing corners of y (M_LIN: plus r0)
+                        yo = r4<R>{yki, yhi, zkr, zhr};
+                        if (MODE == M_LIN) { yo.x += pe.x; yo.y += pe.y; yo.z += pe.z; yo.w += pe.w; }
+                    }
+                    *slot = yo;  // phase E reads it back; no other lane touches this slot
                     m0 += mw[t].y * (ykr + zkr); m1 += mw[t].y * (yki - zki);
                     m2 += mw[t].y * (yhr + zhr); m3 += mw[t].y * (yhi - zhi);
                 }
@@ -949,14 +962,13 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
             }
         }
         __syncwarp();
-        // ---------------- phase D/E: outgoing corners from the staged operands
+        // ---------------- phase D/E: outgoing corners = y_out + s (A^{-1} Phi)_out
 #pragma unroll
         for (int r = 0; r < CHUNK; ++r) {
             const int cl = r * SPW + seg;
             const int cell = chunk * CPC + cl;
             if (cell >= J) continue;
             coefs(sT[cl]);
-            const r4<R> qd = sQ[cl];
             const float4 F = *reinterpret_cast<const float4 *>(xp + seg * V + 4 * r);
             const R Fkl = F.x * cs, Fkr = F.y * cs, Fhl = F.z * cs, Fhr = F.w * cs;
 #pragma unroll
@@ -964,25 +976,12 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                 const int pp = ls + LPC * t;
                 if (pp >= P) continue;
                 const Coef<R> &a = ac[t];
-                PairRhs<R> u = MODE == M_LIN ? PairRhs<R>{0, 0, 0, 0, 0, 0, 0, 0}
-                                             : pair_rhs_fixed(qd, ce, sE[cl * P + pp]);
-                if (PING) {
-                    const r2<R> inP = (refl_l && cell == 0) ? ld2(fMr + pp) : sP[cl * P + pp];
-                    const r2<R> inM = (refl_r && cell == J - 1) ? ld2(fPr + (size_t)J * P + pp) : sM[cl * P + pp];
-                    u.ukr += mw[t].x * inP.x; u.uhr += mw[t].x * inP.y;
-                    u.vki -= mw[t].x * inM.x; u.vhi -= mw[t].x * inM.y;
-                }
-                // +mu: Im(A^{-1}(u + s Phi)); -mu: Re(A^{-1}(u + s conj(Phi)))
-                const R uk_i = u.uki + Fkr, uk_r = u.ukr + Fkl, uh_i = u.uhi + Fhr, uh_r = u.uhr + Fhl;
-                const R vk_r = u.vkr + Fkl, vk_i = u.vki - Fkr, vh_r = u.vhr + Fhl, vh_i = u.vhi - Fhr;
-                R ok = a.pr * uk_i + a.pi * uk_r + a.rr * uh_i + a.ri * uh_r;
-                R oh = a.ur * uk_i + a.ui * uk_r + a.vr * uh_i + a.vi * uh_r;
-                R mk = a.pr * vk_r - a.pi * vk_i + a.rr * vh_r - a.ri * vh_i;
-                R mh = a.ur * vk_r - a.ui * vk_i + a.vr * vh_r - a.vi * vh_i;
-                if (MODE == M_LIN) {  // d^{l+1} = B d^l + r0
-                    const r4<R> r0v = sE[cl * P + pp];
-                    ok += r0v.x; oh += r0v.y; mk += r0v.z; mh += r0v.w;
-                }
+                const r4<R> yo = sE[cl * P + pp];
+                // +mu: Im(A^{-1} s Phi); -mu: Re(A^{-1} s conj(Phi))
+                const R ok = yo.x + (a.pr * Fkr + a.pi * Fkl + a.rr * Fhr + a.ri * Fhl);
+                const R oh = yo.y + (a.ur * Fkr + a.ui * Fkl + a.vr * Fhr + a.vi * Fhl);
+                const R mk = yo.z + (a.pr * Fkl + a.pi * Fkr + a.rr * Fhl + a.ri * Fhr);
+                const R mh = yo.w + (a.ur * Fkl + a.ui * Fkr + a.vr * Fhl + a.vi * Fhr);
                 if (PING) {
                     st2(fPw + (size_t)(cell + 1) * P + pp, ok, oh);
                     st2(fMw + (size_t)cell * P + pp, mk, mh);
@@ -991,6 +990,7 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                 }
             }
         }
+        fence_proxy_async();  // this lane's phase-A stores into the ring before the next copy into it
         __syncwarp();  // stage i and the transpose buffer fully read
     }
     if (!ok_all) {
