@@ -214,6 +214,7 @@ def run_ours(args, rank, world):
     if not args.no_compare and rank == 0:
         compare = run_compare(args, pkg, torch, stream)
         compare["learned_guess"] = run_learned(args, pkg, torch, stream)
+        compare["dense_inverse_s128"] = run_dense(args, pkg, torch, stream)
     return {
         "value": value, "units": units, "dev_time": dev_time, "wall": wall, "iters": iters, "launches": launches,
         "roofline": roofline, "e2e": e2e, "clocks": clk, "desc": desc, "J": J, "N": N, "compare": compare,
@@ -221,15 +222,18 @@ def run_ours(args, rank, world):
 
 
 def run_compare(args, pkg, torch, stream):
-    """SI and FP64 OCI on the same problem (fewer steps), for context."""
+    """SI (the paper's sequential sweep, and the parallel-prefix sweep) and FP64
+    OCI on the same problem (fewer steps), for context."""
     out = {}
     prob, _ = make_problem(args)
     J, N = prob["n_cells"], prob["n_ord"]
-    for name, method, prec in (("si_" + args.precision, "si", args.precision), ("oci_fp64", "oci", "fp64"),
-                               ("si_fp64", "si", "fp64")):
+    for name, method, prec, sweep in (("si_" + args.precision, "si", args.precision, "march"),
+                                      ("si_scan_" + args.precision, "si", args.precision, "scan"),
+                                      ("oci_fp64", "oci", "fp64", "march"), ("si_fp64", "si", "fp64", "march"),
+                                      ("si_scan_fp64", "si", "fp64", "scan")):
         if prec == args.precision and method == "oci":
             continue
-        s = pkg.Solver(prob, precision=prec, tol=prob["tol"], stream=stream.cuda_stream)
+        s = pkg.Solver(prob, precision=prec, tol=prob["tol"], stream=stream.cuda_stream, sweep=sweep)
         n_w, n_t = 2, min(args.steps, 5)
         its, secs = [], []
         ok = True
@@ -281,6 +285,41 @@ def run_learned(args, pkg, torch, stream):
         out[name] = ({"s_per_step": sum(secs) / len(secs), "iters_per_step": sum(its) / len(its),
                       "updates_per_s": 131072 * 64 * sum(its) / sum(secs), "steps_timed": n_t,
                       "after_steps": n_w} if ok else {"failed_status": rc})
+    return out
+
+
+def run_dense(args, pkg, torch, stream):
+    """The dense per-material inverse variant against the Woodbury kernels on
+    the S_128 slab (16384 cells, c = 0.9, dx = 1 mfp; 512 x 512 inverse):
+    device seconds per iteration (CUDA events, 20 iterations) and per converged
+    step, FP64 and FP32.  The dense iteration's GEMM does 2 (4N)^2 flop per
+    cell; its rate is reported in TFLOP/s."""
+    prob = workloads.config3(n_steps=4)
+    J, N = prob["n_cells"], prob["n_ord"]
+    out = {"workload": "slab 16384 cells, S_128, sigma_t=1, c=0.9, dx=1 mfp, dt=0.05, reflect/vacuum, tol 1e-8"}
+    for prec in ("fp64", "fp32"):
+        for solver in ("woodbury", "dense"):
+            s = pkg.Solver(prob, precision=prec, tol=prob["tol"], stream=stream.cuda_stream, solver=solver)
+            rec = {}
+            if prec == "fp64":
+                its, secs = [], []
+                for k in range(3):
+                    rc, st = s.step()
+                    if rc != pkg.OCI_OK:
+                        rec["failed_status"] = rc
+                        break
+                    if k >= 1:
+                        its.append(st["iters"])
+                        secs.append(st["seconds"])
+                if its:
+                    rec.update(s_per_step=sum(secs) / len(secs), iters_per_step=sum(its) / len(its))
+            t = pkg.oci_profile_iterations(s.h, 20)
+            rec["s_per_iteration"] = t
+            rec["updates_per_s"] = J * N / t
+            if solver == "dense":
+                rec["gemm_tflops_incl_rhs_out"] = 2.0 * (4 * N) ** 2 * J / t / 1e12
+            s.close()
+            out[f"{solver}_{prec}"] = rec
     return out
 
 

@@ -122,6 +122,36 @@ int oci_set_iteration(oci_handle *h, double tol, int32_t max_iter, int32_t commi
 /* Change the stream subsequent calls launch on (cudaStream_t, NULL = legacy). */
 int oci_set_stream(oci_handle *h, void *cuda_stream);
 
+/* How oci_step solves each cell's 4N x 4N system (A - S) Psi = c (Sec.
+ * "One-Cell Inversion (OCI)").  OCI_SOLVER_WOODBURY (default): the complex
+ * 2x2 block inverses plus the rank-4 capacitance correction, in one fused
+ * kernel per iteration.  OCI_SOLVER_DENSE: the dense inverse (A - S)^{-1}
+ * (the system the paper's CPU code factorises with LAPACK _gesv) is formed
+ * once per material on the host in FP64 (Gauss-Jordan, partial pivoting) and
+ * every iteration is a right-hand-side kernel, one cuBLAS GEMM per material
+ * (DGEMM in OCI_FP64, SGEMM in OCI_FP32) and an output kernel; the iteration
+ * loop runs on the host (one status read per iteration).  Both give the same
+ * iterates up to rounding.  The dense variant holds n_mat (4N)^2 + 2 J 4N
+ * values (OCI_EINVAL above 4 GiB / 16 GiB), does no FP32 stall refinement and
+ * ignores a learned corrector (the learned guess still applies).  OCI_EINVAL
+ * for an unknown solver or a singular (A - S), OCI_ENOMEM, OCI_ECUDA. */
+enum { OCI_SOLVER_WOODBURY = 0, OCI_SOLVER_DENSE = 1 };
+int oci_set_solver(oci_handle *h, int32_t solver);
+
+/* How si_step sweeps each ordinate (Sec. "Source Iteration (SI)").
+ * OCI_SWEEP_MARCH (default): the paper's sweep, cell by cell in the direction
+ * of travel, parallel over ordinates only (a J-long dependent chain).
+ * OCI_SWEEP_SCAN: the same recurrence -- the outgoing corner pair of a cell is
+ * an affine function of the pair entering it -- evaluated as a parallel prefix
+ * over cells (segment compositions, a pass over the segment maps, a pass that
+ * applies them), so the sweep's depth is O(log J) and all SMs take part.  Not
+ * the paper's method; same fixed point and iterates up to rounding (the
+ * association order differs).  Reflecting boundaries keep the march's order
+ * (mu < 0 first).  Allocates 2 N/2 ceil(J/2048) x 8 values on first use.
+ * OCI_EINVAL for an unknown mode, OCI_ENOMEM, OCI_ECUDA. */
+enum { OCI_SWEEP_MARCH = 0, OCI_SWEEP_SCAN = 1 };
+int oci_set_sweep(oci_handle *h, int32_t sweep);
+
 /* Advance one time step with one-cell inversion (Sec. "One-Cell Inversion"):
  * each iteration every cell solves (A - S) Psi = c for its 4N unknowns with
  * the neighbours' incident fluxes from iterate l, via the block-diagonal plus

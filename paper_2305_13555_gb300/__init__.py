@@ -19,6 +19,10 @@ from . import build as _build
 OCI_OK, OCI_EINVAL, OCI_ENOMEM, OCI_ECUDA, OCI_ENOTCONV, OCI_ENAN, OCI_ETIMEOUT, OCI_ESTATE = range(8)
 OCI_BC_VACUUM, OCI_BC_REFLECT, OCI_BC_INCIDENT = 0, 1, 2
 OCI_FP64, OCI_FP32 = 0, 1
+OCI_SOLVER_WOODBURY, OCI_SOLVER_DENSE = 0, 1
+OCI_SWEEP_MARCH, OCI_SWEEP_SCAN = 0, 1
+_SWEEP = {"march": OCI_SWEEP_MARCH, "scan": OCI_SWEEP_SCAN}
+_SOLVER = {"woodbury": OCI_SOLVER_WOODBURY, "dense": OCI_SOLVER_DENSE}
 _BC = {"vacuum": OCI_BC_VACUUM, "reflect": OCI_BC_REFLECT, "reflecting": OCI_BC_REFLECT,
        "incident": OCI_BC_INCIDENT}
 _PREC = {"fp64": OCI_FP64, "f64": OCI_FP64, "double": OCI_FP64, "fp32": OCI_FP32, "f32": OCI_FP32,
@@ -56,6 +60,8 @@ SIGNATURES = {
     "oci_set_source": (ctypes.c_int, [_VP, _VP]),
     "oci_set_iteration": (ctypes.c_int, [_VP, _D, _I32, _I32]),
     "oci_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "oci_set_solver": (ctypes.c_int, [_VP, _I32]),
+    "oci_set_sweep": (ctypes.c_int, [_VP, _I32]),
     "oci_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
     "si_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
     "oci_fluxes": (ctypes.c_int, [_VP, _VP]),
@@ -184,6 +190,18 @@ def oci_set_stream(h, stream):
     _check(load_library().oci_set_stream(h, stream), "oci_set_stream", h)
 
 
+def oci_set_solver(h, solver):
+    """OCI_SOLVER_WOODBURY (default) or OCI_SOLVER_DENSE (see oci.h); also "woodbury" / "dense"."""
+    solver = _SOLVER.get(solver, solver)
+    _check(load_library().oci_set_solver(h, int(solver)), "oci_set_solver", h)
+
+
+def oci_set_sweep(h, sweep):
+    """OCI_SWEEP_MARCH (default) or OCI_SWEEP_SCAN for si_step (see oci.h); also "march" / "scan"."""
+    sweep = _SWEEP.get(sweep, sweep)
+    _check(load_library().oci_set_sweep(h, int(sweep)), "oci_set_sweep", h)
+
+
 def oci_step(h):
     """One OCI time step; returns (status, stats dict).  Raises only on
     OCI_EINVAL / OCI_ECUDA; convergence failures come back as the status."""
@@ -243,9 +261,18 @@ def oci_set_state(h, psi):
 class Solver:
     """Owns one handle.  ``step()`` / ``si_step()`` advance one time step."""
 
-    def __init__(self, prob, precision="fp64", tol=None, max_iter=100000, stream=None):
+    def __init__(self, prob, precision="fp64", tol=None, max_iter=100000, stream=None, solver="woodbury",
+                 sweep="march"):
         self.prob = prob
         self.h = oci_create(prob, precision, tol, max_iter, stream)
+        try:
+            if solver != "woodbury":
+                oci_set_solver(self.h, solver)
+            if sweep != "march":
+                oci_set_sweep(self.h, sweep)
+        except Exception:
+            self.close()
+            raise
 
     def step(self, method="oci"):
         return (oci_step if method == "oci" else si_step)(self.h)

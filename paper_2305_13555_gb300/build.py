@@ -4,6 +4,7 @@ Produces paper_2305_13555_gb300/_build/liboci_gb300.so (in-tree, git-ignored).
 Translation units compile in parallel with one -gencode; no cmake.
 """
 import os
+import shutil
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -13,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboci_gb300.so")
-SOURCES = ["oci_api.cu", "oci_kernels_f32.cu", "oci_kernels_f64.cu", "nn_kernels.cu"]
-HEADERS = ["oci_device.cuh", "oci_kernels.h"]
+SOURCES = ["oci_api.cu", "oci_kernels_f32.cu", "oci_kernels_f64.cu", "nn_kernels.cu", "oci_dense.cu"]
+HEADERS = ["oci_device.cuh", "oci_kernels.h", "oci_dense.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I" + os.path.join(ROOT, "include")]
@@ -58,7 +59,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
+        cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(shutil.which(nvcc) or nvcc))),
+                                "lib64")
+        run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lcublas",
+             "-Xlinker", "-rpath=" + cuda_lib])
         os.replace(tmp, LIB)
     return LIB
 

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/oci.h"
+#include "oci_dense.h"
 #include "oci_kernels.h"
 
 using ocik::IterConfig;
@@ -135,6 +136,14 @@ struct oci_handle {
     cudaGraph_t graph_lin = nullptr;
     cudaGraphExec_t exec_lin = nullptr;
     int refinements = 0;
+    // dense per-material inverse variant (oci_set_solver)
+    int solver = OCI_SOLVER_WOODBURY;
+    ocik::DenseBuffers dense;
+    int dense_grid = 1;
+    // SI sweep as a parallel prefix (oci_set_sweep)
+    int sweep = OCI_SWEEP_MARCH;
+    void *scan_mem = nullptr;  // segment maps [2P][nseg], entering values [2P][nseg]
+    int scan_nseg = 0;
 };
 
 namespace {
@@ -415,7 +424,25 @@ int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout
     CK(h, cudaGraphAddNode(&n_while, g, &n_prev, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaGraphNode_t b_cells;
-    if (si) {
+    // parallel-prefix sweep operands (used when h->sweep == OCI_SWEEP_SCAN)
+    int nseg = h->scan_nseg;
+    const int nch = 2 * h->P;
+    ocik::Aff<R> *agg = (ocik::Aff<R> *)h->scan_mem;
+    r2<R> *enter = h->scan_mem ? (r2<R> *)((char *)h->scan_mem + (((size_t)nch * nseg * sizeof(ocik::Aff<R>) + 255) &
+                                                                 ~(size_t)255))
+                               : nullptr;
+    void *a_red[] = {&plain, &agg};
+    void *a_seg[] = {&plain, &agg, &enter, &nseg};
+    void *a_app[] = {&plain, &enter};
+    if (si && h->sweep == OCI_SWEEP_SCAN) {
+        cudaGraphNode_t b_red, b_seg, b_app;
+        rc = add_kernel(h, body, &b_red, nullptr, 0, h->ks.scan_reduce, dim3(nseg, nch), dim3(ocik::SCAN_T), a_red);
+        if (!rc) rc = add_kernel(h, body, &b_seg, &b_red, 1, h->ks.scan_segments, dim3(h->P), dim3(32), a_seg);
+        if (!rc) rc = add_kernel(h, body, &b_app, &b_seg, 1, h->ks.scan_apply, dim3(nseg, nch), dim3(ocik::SCAN_T), a_app);
+        if (rc) return rc;
+        rc = add_kernel(h, body, &b_cells, &b_app, 1, h->cells_si, dim3(h->cells_grid), dim3(h->cells_block), a_loop,
+                        h->cells_smem);
+    } else if (si) {
         cudaGraphNode_t b_march;
         const int nm = h->bcl == OCI_BC_REFLECT ? h->P : 2 * h->P;
         rc = add_kernel(h, body, &b_march, nullptr, 0, h->ks.march, dim3(nm), dim3(32), a_march);
@@ -494,6 +521,10 @@ int build_lin_graph(oci_handle *h)
 
 int ensure_graphs(oci_handle *h)
 {
+    if (h->exec_oci && !h->exec_si) {
+        return h->prec == OCI_FP64 ? build_graph<double>(h, true, &h->graph_si, &h->exec_si)
+                                   : build_graph<float>(h, true, &h->graph_si, &h->exec_si);
+    }
     if (h->exec_oci) return OCI_OK;
     int rc;
     if (h->prec == OCI_FP64) {
@@ -623,6 +654,88 @@ int refine_step(oci_handle *h, IterState *s)
                              h->bc_right_host.empty() ? nullptr : h->bc_right_host.data());
 }
 
+// Per-material inverses, cells grouped by material, cuBLAS handle.
+int dense_setup(oci_handle *h)
+{
+    const int J = h->J, P = h->P, nm = (int)h->mats.size(), n = 8 * P;
+    const size_t rs = rsize(h);
+    const size_t inv_bytes = (size_t)nm * n * n * rs, col_bytes = (size_t)J * n * rs;
+    if (inv_bytes > ((size_t)4 << 30) || col_bytes > ((size_t)16 << 30)) return OCI_EINVAL;
+    std::vector<double> mu_p(P), w_p(P), inv, all;
+    for (int p = 0; p < P; ++p) { mu_p[p] = h->mu[P + p]; w_p[p] = h->w[P + p]; }
+    all.reserve((size_t)nm * n * n);
+    for (int m = 0; m < nm; ++m) {
+        const Material &mt = h->mats[m];
+        const double e = std::isinf(h->v) ? 0.0 : mt.dx / (2.0 * h->v * h->dt);
+        if (!ocik::dense_inverse(mu_p.data(), w_p.data(), P, mt.dx, mt.st, mt.ss, e, inv)) return OCI_EINVAL;
+        all.insert(all.end(), inv.begin(), inv.end());
+    }
+    std::vector<int> perm(J), off(nm + 1, 0);
+    for (int j = 0; j < J; ++j) ++off[h->mat[j] + 1];
+    for (int m = 0; m < nm; ++m) off[m + 1] += off[m];
+    {
+        std::vector<int> next(off.begin(), off.end() - 1);
+        for (int j = 0; j < J; ++j) perm[next[h->mat[j]]++] = j;
+    }
+    ocik::DenseBuffers &d = h->dense;
+    const size_t a0 = (inv_bytes + 255) & ~(size_t)255, a1 = (col_bytes + 255) & ~(size_t)255;
+    if (cudaMalloc(&d.mem, a0 + 2 * a1 + (size_t)J * 4) != cudaSuccess) {
+        d.mem = nullptr;
+        return OCI_ENOMEM;
+    }
+    char *b = (char *)d.mem;
+    d.minv = b;
+    d.C = b + a0;
+    d.Psi = b + a0 + a1;
+    d.perm = (int *)(b + a0 + 2 * a1);
+    d.ncols = J;
+    d.col_off = off;
+    int rc = upload_real(h, d.minv, all);
+    if (rc) return rc;
+    CK(h, cudaMemcpy(d.perm, perm.data(), sizeof(int) * J, cudaMemcpyHostToDevice));
+    if (ocik::dense_blas_create(&d.blas)) return cuda_fail(h, cudaErrorUnknown, "cublasCreate");
+    h->dense_grid = std::max(1, std::min((J + 7) / 8, h->grid_cells));
+    return OCI_OK;
+}
+
+void dense_free(oci_handle *h)
+{
+    ocik::dense_blas_destroy(h->dense.blas);
+    if (h->dense.mem) cudaFree(h->dense.mem);
+    h->dense = ocik::DenseBuffers{};
+}
+
+int dense_iterate(oci_handle *h)
+{
+    int rc;
+    if (h->prec == OCI_FP64) rc = ocik::dense_iteration(make_params<double>(h, 0, 0), h->dense, h->dense_grid, h->stream);
+    else rc = ocik::dense_iteration(make_params<float>(h, 0, 0), h->dense, h->dense_grid, h->stream);
+    return rc ? cuda_fail(h, cudaGetLastError(), "dense iteration") : OCI_OK;
+}
+
+// One OCI step with the dense inverse: the loop runs on the host (one status
+// read per iteration), then the shared commit kernel.
+int dense_step(oci_handle *h, IterState *s)
+{
+    IterConfig c = h->cfg;
+    c.stall_floor = 0.0;  // no FP32 refinement on this path
+    c.pause_at = -1;
+    int rc = set_device_cfg(h, c);
+    if (rc) return rc;
+    IterState *st = h->d_st;
+    void *a_st[] = {&st};
+    CK(h, cudaLaunchKernel((const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st, 0, h->stream));
+    for (int it = 0; it < c.max_iter + 2; ++it) {
+        if ((rc = dense_iterate(h)) || (rc = read_state(h, s))) return rc;
+        if (s->status != ocik::ST_RUNNING) break;
+    }
+    KParams<double> pd = make_params<double>(h, 0, 0);
+    KParams<float> pf = make_params<float>(h, 0, 0);
+    void *args[] = {h->prec == OCI_FP64 ? (void *)&pd : (void *)&pf};
+    CK(h, cudaLaunchKernel(h->ks.commit_oci, dim3(h->grid_pc), dim3(kBlock), args, 0, h->stream));
+    return OCI_OK;
+}
+
 int map_status(int s)
 {
     switch (s) {
@@ -654,7 +767,9 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         ++accepts;
     }
     IterState s{};
-    if (nn && h->nn_mode == OCI_NN_GUESS_CORRECT) {
+    if (!si && h->solver == OCI_SOLVER_DENSE) {
+        if ((rc = dense_step(h, &s))) return rc;
+    } else if (nn && h->nn_mode == OCI_NN_GUESS_CORRECT) {
         if (!h->exec_cont) {
             rc = h->prec == OCI_FP64 ? build_cont_graph<double>(h) : build_cont_graph<float>(h);
             if (rc) return rc;
@@ -947,6 +1062,8 @@ void oci_destroy(oci_handle *h)
     if (h->exec_cont) cudaGraphExecDestroy(h->exec_cont);
     if (h->graph_cont) cudaGraphDestroy(h->graph_cont);
     if (h->nn_mem) cudaFree(h->nn_mem);
+    dense_free(h);
+    if (h->scan_mem) cudaFree(h->scan_mem);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->h_st) cudaFreeHost(h->h_st);
@@ -976,6 +1093,47 @@ int oci_set_stream(oci_handle *h, void *cuda_stream)
     if (!h) return OCI_EINVAL;
     CK(h, cudaStreamSynchronize(h->stream));
     h->stream = (cudaStream_t)cuda_stream;
+    return OCI_OK;
+}
+
+int oci_set_solver(oci_handle *h, int32_t solver)
+{
+    if (!h || (solver != OCI_SOLVER_WOODBURY && solver != OCI_SOLVER_DENSE)) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    if (solver == OCI_SOLVER_DENSE && !h->dense.mem) {
+        const int rc = dense_setup(h);
+        if (rc) {
+            dense_free(h);
+            return rc;
+        }
+    }
+    h->solver = solver;
+    return OCI_OK;
+}
+
+int oci_set_sweep(oci_handle *h, int32_t sweep)
+{
+    if (!h || (sweep != OCI_SWEEP_MARCH && sweep != OCI_SWEEP_SCAN)) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    if (sweep == h->sweep) return OCI_OK;
+    if (sweep == OCI_SWEEP_SCAN && !h->scan_mem) {
+        const int nseg = (h->J + ocik::SCAN_SEG - 1) / ocik::SCAN_SEG;
+        if (nseg > 65535) return OCI_EINVAL;
+        const size_t nch = 2 * (size_t)h->P, rs = rsize(h);
+        const size_t a = ((nch * nseg * 6 * rs) + 255) & ~(size_t)255;
+        if (cudaMalloc(&h->scan_mem, a + nch * nseg * 2 * rs) != cudaSuccess) {
+            h->scan_mem = nullptr;
+            return OCI_ENOMEM;
+        }
+        h->scan_nseg = nseg;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    // the SI step graph is rebuilt with the other sweep on the next step
+    if (h->exec_si) cudaGraphExecDestroy(h->exec_si);
+    if (h->graph_si) cudaGraphDestroy(h->graph_si);
+    h->exec_si = nullptr;
+    h->graph_si = nullptr;
+    h->sweep = sweep;
     return OCI_OK;
 }
 
@@ -1058,9 +1216,14 @@ int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_la
     KParams<float> pf = make_params<float>(h, 0, 0);
     void *args[] = {h->prec == OCI_FP64 ? (void *)&pd : (void *)&pf};
     CK(h, cudaEventRecord(h->ev0, h->stream));
-    for (int i = 0; i < n_iter; ++i)
-        CK(h, cudaLaunchKernel(h->cells_oci, dim3(h->cells_grid), dim3(h->cells_block), args, h->cells_smem,
-                               h->stream));
+    for (int i = 0; i < n_iter; ++i) {
+        if (h->solver == OCI_SOLVER_DENSE) {
+            if ((rc = dense_iterate(h))) return rc;
+        } else {
+            CK(h, cudaLaunchKernel(h->cells_oci, dim3(h->cells_grid), dim3(h->cells_block), args, h->cells_smem,
+                                   h->stream));
+        }
+    }
     CK(h, cudaEventRecord(h->ev1, h->stream));
     CK(h, cudaEventSynchronize(h->ev1));
     float ms = 0.f;

@@ -1517,4 +1517,184 @@ __global__ void __launch_bounds__(32) k_si_march(const KParams<R> p, int n_mat)
     }
 }
 
+// ---------------------------------------------------------------------------
+// SI sweep as a parallel prefix over cells (an alternative to the sequential
+// march above; the paper sweeps each ordinate cell by cell).  Along one
+// ordinate's direction of travel the outgoing corner pair of cell j is an
+// affine function of the pair entering it: x_j = G_j x_{j-1} + g_j, G_j the
+// 2x2 response of the material (same as the march), g_j the offset the SI cell
+// kernel stored.  Composition of affine maps is associative, so the chain of J
+// cells is a scan: (1) every block composes a 2048-cell segment (256 threads x
+// 8 cells, then a block scan of the thread maps) into one map per segment;
+// (2) one warp per pair runs the segment maps from the boundary value (mu < 0
+// first, so a reflecting left face takes this sweep's mu < 0 flux) and keeps
+// each segment's entering value; (3) every block recomposes its segment and
+// writes every cell's outgoing pair.  Chain ch = 2 pair + (0: mu < 0, 1: mu > 0).
+// The association order differs from the march, so results agree with it to
+// rounding, not bit for bit.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_T = 256, SCAN_CPT = 8, SCAN_SEG = SCAN_T * SCAN_CPT;
+
+template <typename R>
+struct Aff { R a, b, c, d, e, f; };  // x -> [[a, b], [c, d]] x + (e, f)
+
+template <typename R>
+__device__ __forceinline__ Aff<R> aff_id() { return {1, 0, 0, 1, 0, 0}; }
+
+// the map "first, then second"
+template <typename R>
+__device__ __forceinline__ Aff<R> aff_then(const Aff<R> &f, const Aff<R> &s)
+{
+    return {s.a * f.a + s.b * f.c, s.a * f.b + s.b * f.d, s.c * f.a + s.d * f.c, s.c * f.b + s.d * f.d,
+            s.a * f.e + (s.b * f.f + s.e), s.c * f.e + (s.d * f.f + s.f)};
+}
+
+template <typename R>
+__device__ __forceinline__ Aff<R> aff_shfl_up(const Aff<R> &x, int d)
+{
+    return {__shfl_up_sync(FULL, x.a, d), __shfl_up_sync(FULL, x.b, d), __shfl_up_sync(FULL, x.c, d),
+            __shfl_up_sync(FULL, x.d, d), __shfl_up_sync(FULL, x.e, d), __shfl_up_sync(FULL, x.f, d)};
+}
+
+template <typename R>
+struct ScanShared {
+    r2<R> g[SCAN_SEG];
+    int mat[SCAN_SEG];
+    Aff<R> warp_tot[SCAN_T / 32];
+};
+
+// Stage the segment's offsets and materials, compose each thread's 8 cells
+// and scan the thread maps over the block.  Returns the thread's exclusive
+// prefix (maps of all earlier cells of the segment) and sets *total (block).
+template <typename R>
+__device__ Aff<R> scan_segment(const KParams<R> &p, ScanShared<R> &sh, int ch, int seg, Aff<R> *total)
+{
+    const int J = p.J, P = p.P;
+    const int pp = ch >> 1, dir = (ch & 1) ? 1 : -1;
+    const int s0 = seg * SCAN_SEG;
+    const int n = J - s0 < SCAN_SEG ? J - s0 : SCAN_SEG;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int k = t; k < n; k += SCAN_T) {
+        const int j = dir > 0 ? s0 + k : J - 1 - (s0 + k);
+        sh.g[k] = reinterpret_cast<const r2<R> *>(p.g + (size_t)pp * J + j)[dir > 0 ? 0 : 1];
+        sh.mat[k] = p.mat[j];
+    }
+    __syncthreads();
+    const R mu = ldg2(p.muw + pp).x;
+    int mc = -1;
+    r4<R> G{0, 0, 0, 0};
+    Aff<R> A = aff_id<R>();
+    for (int i = 0; i < SCAN_CPT; ++i) {
+        const int k = t * SCAN_CPT + i;
+        if (k >= n) break;
+        const int m = sh.mat[k];
+        if (m != mc) {
+            mc = m;
+            const Coef<R> c = load_coef(p.tab, m, P, pp);
+            G = r4<R>{mu * c.pi, mu * c.ri, mu * c.ui, mu * c.vi};
+        }
+        A = aff_then(A, Aff<R>{G.x, G.y, G.z, G.w, sh.g[k].x, sh.g[k].y});
+    }
+    // inclusive scan within the warp (earlier lanes' maps apply first)
+    Aff<R> I = A;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const Aff<R> e = aff_shfl_up(I, d);
+        if (lane >= d) I = aff_then(e, I);
+    }
+    if (lane == 31) sh.warp_tot[warp] = I;
+    __syncthreads();
+    Aff<R> W = aff_id<R>();  // maps of the earlier warps
+    for (int w = 0; w < warp; ++w) W = aff_then(W, sh.warp_tot[w]);
+    Aff<R> E = aff_shfl_up(I, 1);  // exclusive within the warp
+    if (lane == 0) E = aff_id<R>();
+    if (total) {
+        Aff<R> T = aff_id<R>();
+        for (int w = 0; w < SCAN_T / 32; ++w) T = aff_then(T, sh.warp_tot[w]);
+        *total = T;
+    }
+    return aff_then(W, E);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const KParams<R> p, Aff<R> *__restrict__ agg)
+{
+    __shared__ ScanShared<R> sh;
+    if (*(volatile int *)&p.st->status != ST_RUNNING) return;
+    const int seg = blockIdx.x, ch = blockIdx.y;
+    Aff<R> T;
+    (void)scan_segment(p, sh, ch, seg, &T);
+    if (threadIdx.x == 0) agg[(size_t)ch * gridDim.x + seg] = T;
+}
+
+// One warp per pair: boundary values, segment entering values (lane 0).
+template <typename R>
+__global__ void __launch_bounds__(32) k_scan_segments(const KParams<R> p, const Aff<R> *__restrict__ agg,
+                                                      r2<R> *__restrict__ enter, int nseg)
+{
+    IterState *st = p.st;
+    if (*(volatile int *)&st->status != ST_RUNNING) return;
+    if (threadIdx.x != 0) return;
+    const int fb = *(volatile int *)&st->base;
+    const int J = p.J, P = p.P, pp = blockIdx.x;
+    // mu < 0 enters through the right face: prescribed / vacuum data or (reflecting)
+    // the previous iterate's mirror flux, copied into the face slot as the march does
+    r2<R> x;
+    if (p.bc_right == BC_REFLECT) {
+        x = ld2(p.refl + pp);
+        st2(p.faceM[fb] + (size_t)J * P + pp, x.x, x.y);
+    } else {
+        x = ld2(p.faceM[fb] + (size_t)J * P + pp);
+    }
+    for (int c = 0; c < 2; ++c) {
+        const int ch = 2 * pp + c;
+        if (c == 1) {
+            if (p.bc_left == BC_REFLECT) st2(p.faceP[fb] + pp, x.x, x.y);  // this sweep's mu < 0 flux at x = 0
+            else x = ld2(p.faceP[fb] + pp);
+        }
+        for (int s = 0; s < nseg; ++s) {
+            enter[(size_t)ch * nseg + s] = x;
+            const Aff<R> A = agg[(size_t)ch * nseg + s];
+            x = r2<R>{A.a * x.x + (A.b * x.y + A.e), A.c * x.x + (A.d * x.y + A.f)};
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(const KParams<R> p, const r2<R> *__restrict__ enter)
+{
+    __shared__ ScanShared<R> sh;
+    IterState *st = p.st;
+    if (*(volatile int *)&st->status != ST_RUNNING) return;
+    const int fb = *(volatile int *)&st->base;
+    const int seg = blockIdx.x, ch = blockIdx.y, nseg = gridDim.x;
+    const int J = p.J, P = p.P;
+    const int pp = ch >> 1, dir = (ch & 1) ? 1 : -1;
+    const Aff<R> E = scan_segment<R>(p, sh, ch, seg, nullptr);
+    const r2<R> x0 = enter[(size_t)ch * nseg + seg];
+    R xk = E.a * x0.x + (E.b * x0.y + E.e), xh = E.c * x0.x + (E.d * x0.y + E.f);
+    const int s0 = seg * SCAN_SEG;
+    const int n = J - s0 < SCAN_SEG ? J - s0 : SCAN_SEG;
+    const R mu = ldg2(p.muw + pp).x;
+    int mc = -1;
+    r4<R> G{0, 0, 0, 0};
+    for (int i = 0; i < SCAN_CPT; ++i) {
+        const int k = threadIdx.x * SCAN_CPT + i;
+        if (k >= n) break;
+        const int m = sh.mat[k];
+        if (m != mc) {
+            mc = m;
+            const Coef<R> c = load_coef(p.tab, m, P, pp);
+            G = r4<R>{mu * c.pi, mu * c.ri, mu * c.ui, mu * c.vi};
+        }
+        const R nk = G.x * xk + (G.y * xh + sh.g[k].x);
+        const R nh = G.z * xk + (G.w * xh + sh.g[k].y);
+        xk = nk;
+        xh = nh;
+        const int j = dir > 0 ? s0 + k : J - 1 - (s0 + k);
+        if (dir > 0) st2(p.faceP[fb] + (size_t)(j + 1) * P + pp, xk, xh);
+        else st2(p.faceM[fb] + (size_t)j * P + pp, xk, xh);
+    }
+}
+
 }  // namespace ocik

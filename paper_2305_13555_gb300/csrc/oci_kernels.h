@@ -13,6 +13,7 @@ struct KernelSet {
     const void *si_prep;     // k_percell<C_SI_PREP>
     const void *guess;       // k_percell<C_GUESS>
     const void *march;       // k_si_march
+    const void *scan_reduce, *scan_segments, *scan_apply;  // parallel-prefix SI sweep
     const void *lift_guess;  // k_lift<LIFT_GUESS>
     const void *lift_corr;   // k_lift<LIFT_CORR>
     const void *cells_oci_tma;  // k_cells_tma<M_OCI> (FP32, even P) or nullptr

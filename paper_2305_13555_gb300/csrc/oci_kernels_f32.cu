@@ -17,6 +17,9 @@ static void fill(KernelSet *k)
     k->si_prep = (const void *)&k_percell<float, LPC, PPL, C_SI_PREP>;
     k->guess = (const void *)&k_percell<float, LPC, PPL, C_GUESS>;
     k->march = (const void *)&k_si_march<float>;
+    k->scan_reduce = (const void *)&k_scan_reduce<float>;
+    k->scan_segments = (const void *)&k_scan_segments<float>;
+    k->scan_apply = (const void *)&k_scan_apply<float>;
     k->lift_guess = (const void *)&k_lift<float, LPC, PPL, LIFT_GUESS>;
     k->lift_corr = (const void *)&k_lift<float, LPC, PPL, LIFT_CORR>;
     k->cells_oci_tma = nullptr;

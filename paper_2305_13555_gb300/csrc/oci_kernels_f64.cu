@@ -13,6 +13,9 @@ static void fill(KernelSet *k)
     k->si_prep = (const void *)&k_percell<double, LPC, PPL, C_SI_PREP>;
     k->guess = (const void *)&k_percell<double, LPC, PPL, C_GUESS>;
     k->march = (const void *)&k_si_march<double>;
+    k->scan_reduce = (const void *)&k_scan_reduce<double>;
+    k->scan_segments = (const void *)&k_scan_segments<double>;
+    k->scan_apply = (const void *)&k_scan_apply<double>;
     k->lift_guess = (const void *)&k_lift<double, LPC, PPL, LIFT_GUESS>;
     k->lift_corr = (const void *)&k_lift<double, LPC, PPL, LIFT_CORR>;
     k->cells_oci_tma = nullptr;
