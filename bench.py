@@ -386,8 +386,19 @@ def main():
     ap.add_argument("--nn-seed", type=int, default=8)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-compare", choices=["solvers", "learned", "dense"],
+                    help="run one comparison block alone and print it (for profiling its kernels)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+
+    if args.only_compare:
+        import torch
+        import paper_2305_13555_gb300 as pkg
+        pkg.load_library()
+        stream = torch.cuda.current_stream()
+        fn = {"solvers": run_compare, "learned": run_learned, "dense": run_dense}[args.only_compare]
+        print(json.dumps({args.only_compare: fn(args, pkg, torch, stream)}))
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

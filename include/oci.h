@@ -194,9 +194,12 @@ int oci_get_state(const oci_handle *h, double *psi_edge);
 int oci_set_state(oci_handle *h, const double *psi_edge);
 
 /* Time the one-cell-inversion iteration kernel alone: run n_iter iterations
- * from the current step's initial iterate as plain stream launches (no graph,
- * no convergence exit), bracketed by CUDA events on the handle's stream, and
- * return the mean device time per launch in *seconds_per_launch.  The
+ * from the current step's initial iterate as stream launches (no graph, no
+ * convergence exit; the staged FP32 kernel as programmatic dependent launches,
+ * as inside a step), after two untimed warm-up launches, bracketed by CUDA
+ * events on the handle's stream, and return the mean device time per launch
+ * in *seconds_per_launch.  With OCI_SOLVER_DENSE one "launch" is a whole
+ * dense iteration (right-hand sides, GEMMs, outputs).  The
  * committed state (psi_{k-1/2}, published phi) is untouched and the next step
  * restarts from it.  Used by the benchmark's roofline figure. */
 int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_launch);

@@ -142,6 +142,7 @@ struct oci_handle {
     int dense_grid = 1;
     // SI sweep as a parallel prefix (oci_set_sweep)
     int sweep = OCI_SWEEP_MARCH;
+    bool pdl_graph = true;           // programmatic edges between iterations (cleared if unsupported)
     void *scan_mem = nullptr;  // segment maps [2P][nseg], entering values [2P][nseg]
     int scan_nseg = 0;
 };
@@ -390,6 +391,34 @@ int add_kernel(oci_handle *h, cudaGraph_t g, cudaGraphNode_t *node, const cudaGr
     return OCI_OK;
 }
 
+// The OCI iteration inside a WHILE body: with the staged kernel, kUnroll
+// launches chained by programmatic edges (each iteration's prologue and
+// iteration-invariant copies overlap the previous one's tail; launches after
+// the step has ended return at once), else one launch.
+constexpr int kUnroll = 4;
+
+int add_iterations(oci_handle *h, cudaGraph_t body, const void *fn, void **args)
+{
+    const int n = (h->staged && h->pdl_graph) ? kUnroll : 1;
+    cudaGraphNode_t prev = nullptr;
+    for (int i = 0; i < n; ++i) {
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeKernel;
+        np.kernel.func = const_cast<void *>(fn);
+        np.kernel.gridDim = dim3(h->cells_grid);
+        np.kernel.blockDim = dim3(h->cells_block);
+        np.kernel.sharedMemBytes = h->cells_smem;
+        np.kernel.kernelParams = args;
+        cudaGraphEdgeData ed{};
+        ed.from_port = cudaGraphKernelNodePortProgrammatic;
+        ed.type = cudaGraphDependencyTypeProgrammatic;
+        cudaGraphNode_t node;
+        CK(h, cudaGraphAddNode(&node, body, i ? &prev : nullptr, i ? &ed : nullptr, i ? 1 : 0, &np));
+        prev = node;
+    }
+    return OCI_OK;
+}
+
 // Step graph: begin -> [si_prep] -> WHILE { [march ->] cells } -> commit.
 template <typename R>
 int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout)
@@ -450,8 +479,7 @@ int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout
         rc = add_kernel(h, body, &b_cells, &b_march, 1, h->cells_si, dim3(h->cells_grid), dim3(h->cells_block),
                         a_loop, h->cells_smem);
     } else {
-        rc = add_kernel(h, body, &b_cells, nullptr, 0, h->cells_oci, dim3(h->cells_grid), dim3(h->cells_block), a_loop,
-                        h->cells_smem);
+        rc = add_iterations(h, body, h->cells_oci, a_loop);
     }
     if (rc) return rc;
     rc = add_kernel(h, g, &n_commit, &n_while, 1, si ? h->ks.commit_si : h->ks.commit_oci, dim3(h->grid_pc),
@@ -479,10 +507,9 @@ int build_cont_graph(oci_handle *h)
     cp.conditional.handle = cond;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    cudaGraphNode_t n_while, n_commit, b_cells;
+    cudaGraphNode_t n_while, n_commit;
     CK(h, cudaGraphAddNode(&n_while, g, nullptr, nullptr, 0, &cp));
-    int rc = add_kernel(h, cp.conditional.phGraph_out[0], &b_cells, nullptr, 0, h->cells_oci, dim3(h->cells_grid),
-                        dim3(h->cells_block), a_loop, h->cells_smem);
+    int rc = add_iterations(h, cp.conditional.phGraph_out[0], h->cells_oci, a_loop);
     if (rc) return rc;
     rc = add_kernel(h, g, &n_commit, &n_while, 1, h->ks.commit_oci, dim3(h->grid_pc), dim3(kBlock), a_plain);
     if (rc) return rc;
@@ -526,14 +553,20 @@ int ensure_graphs(oci_handle *h)
                                    : build_graph<float>(h, true, &h->graph_si, &h->exec_si);
     }
     if (h->exec_oci) return OCI_OK;
-    int rc;
-    if (h->prec == OCI_FP64) {
-        rc = build_graph<double>(h, false, &h->graph_oci, &h->exec_oci);
-        if (!rc) rc = build_graph<double>(h, true, &h->graph_si, &h->exec_si);
-    } else {
-        rc = build_graph<float>(h, false, &h->graph_oci, &h->exec_oci);
-        if (!rc) rc = build_graph<float>(h, true, &h->graph_si, &h->exec_si);
+    int rc = h->prec == OCI_FP64 ? build_graph<double>(h, false, &h->graph_oci, &h->exec_oci)
+                                 : build_graph<float>(h, false, &h->graph_oci, &h->exec_oci);
+    if (rc && h->pdl_graph && h->staged) {
+        // programmatic edges refused inside the loop body: plain single launches
+        (void)cudaGetLastError();
+        if (h->graph_oci) cudaGraphDestroy(h->graph_oci);
+        h->graph_oci = nullptr;
+        h->exec_oci = nullptr;
+        h->pdl_graph = false;
+        rc = h->prec == OCI_FP64 ? build_graph<double>(h, false, &h->graph_oci, &h->exec_oci)
+                                 : build_graph<float>(h, false, &h->graph_oci, &h->exec_oci);
     }
+    if (!rc) rc = h->prec == OCI_FP64 ? build_graph<double>(h, true, &h->graph_si, &h->exec_si)
+                                      : build_graph<float>(h, true, &h->graph_si, &h->exec_si);
     return rc;
 }
 
@@ -1215,10 +1248,22 @@ int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_la
     KParams<double> pd = make_params<double>(h, 0, 0);
     KParams<float> pf = make_params<float>(h, 0, 0);
     void *args[] = {h->prec == OCI_FP64 ? (void *)&pd : (void *)&pf};
-    CK(h, cudaEventRecord(h->ev0, h->stream));
-    for (int i = 0; i < n_iter; ++i) {
+    for (int i = -2; i < n_iter; ++i) {  // two untimed warm-up launches (library setup, caches)
+        if (i == 0) CK(h, cudaEventRecord(h->ev0, h->stream));
         if (h->solver == OCI_SOLVER_DENSE) {
             if ((rc = dense_iterate(h))) return rc;
+        } else if (h->staged) {
+            cudaLaunchConfig_t lc{};
+            lc.gridDim = dim3(h->cells_grid);
+            lc.blockDim = dim3(h->cells_block);
+            lc.dynamicSmemBytes = h->cells_smem;
+            lc.stream = h->stream;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            lc.attrs = at;
+            lc.numAttrs = 1;
+            CK(h, cudaLaunchKernelExC(&lc, h->cells_oci, args));
         } else {
             CK(h, cudaLaunchKernel(h->cells_oci, dim3(h->cells_grid), dim3(h->cells_block), args, h->cells_smem,
                                    h->stream));

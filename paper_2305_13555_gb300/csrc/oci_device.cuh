@@ -420,7 +420,9 @@ __device__ __forceinline__ bool iteration_prologue(const KParams<R> &p, int &ite
     iter = *(volatile int *)&st->iter;
     base = *(volatile int *)&st->base;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const int launches = atomicAdd(&st->launches, 1);
+        // launches while running (a graph body may hold several launches; those
+        // after the step ended return at once and are not counted)
+        const int launches = status == ST_RUNNING ? atomicAdd(&st->launches, 1) : 0;
         if (status == ST_RUNNING && launches >= p.cfg->max_iter + 2) {
             // The loop should have ended: report; this launch's last block
             // ends the loop.
@@ -642,6 +644,13 @@ __global__ void __launch_bounds__(256) k_cells(const KParams<R> p)
 // cp.async.bulk) of the chunk's contiguous rows -- incident faces, time-edge
 // flux, source moments, material ids -- completing on a per-stage mbarrier;
 // the warp computes chunk i while chunks i+1 .. i+STAGES-1 are in flight.
+// Launched as a programmatic dependent of the previous iteration (stream
+// launches with programmatic serialisation, programmatic graph edges): the
+// copies that do not change between iterations (time-edge flux, sources,
+// materials) of the first chunks are issued before griddepcontrol.wait, the
+// state and the incident faces only after it, and the kernel allows its own
+// dependent to launch as soon as it has read the state.  Without a
+// programmatic launch both instructions are no-ops.
 // Every mbarrier wait is bounded: on expiry the kernel records ST_TIMEOUT,
 // drains (again bounded) its own copies and finishes the iteration normally.
 // ---------------------------------------------------------------------------
@@ -671,6 +680,16 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     return ok != 0;
 }
 // Bounded wait; false when the limit expired.
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(a) : "memory");
+}
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
 {
     for (unsigned it = 0; it < kWaitLimit; ++it)
@@ -732,20 +751,8 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
     const int seg = lane / LPC, ls = lane % LPC;
     const int J = p.J, P = p.P;
 
-    int iter, base;
-    if (!iteration_prologue(p, iter, base)) return;
     constexpr bool PING = MODE == M_OCI || MODE == M_LIN;  // iterate in the face buffers
-    const int frd = PING ? ((base + iter) & 1) : base;
-    const int fwr = frd ^ 1;
-    const phi_t<R> *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
-    phi_t<R> *phw = p.phi[(iter + 1) & 1];
-    const r2<R> *fPr = p.faceP[frd], *fMr = p.faceM[frd];
-    r2<R> *fPw = p.faceP[fwr], *fMw = p.faceM[fwr];
-    const bool refl_l = PING && p.bc_left == BC_REFLECT;
-    const bool refl_r = PING && p.bc_right == BC_REFLECT;
-    // M_LIN: the time-edge slot of the ring carries r0 instead of psi_{k-1/2}
     const r4<R> *edge_src = MODE == M_LIN ? p.r0 : p.psi_edge;
-
     // shared memory: [barriers][per-warp transpose buffers][per-warp rings]
     const unsigned oP = 0, oM = round16(CPC * P * 8u), oE = 2 * round16(CPC * P * 8u);
     const unsigned oQ = oE + round16(CPC * P * 16u), oT = oQ + round16(CPC * 16u);
@@ -766,6 +773,49 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
     bool ok_all = true;
     int broke_at = nmine;
 
+    auto issue_static = [&](int i) {  // lane 0: iteration-invariant copies of local chunk i
+        if (i >= nmine) return;
+        const int c0 = (gw + i * tw) * CPC;
+        const int nv = J - c0 < CPC ? J - c0 : CPC;
+        unsigned char *st = ring + (size_t)(i % STAGES) * sbytes;
+        unsigned long long *bar = bars + i % STAGES;
+        const unsigned bE = round16(nv * P * 16u), bQ = nv * 16u, bT = round16(nv * 4u);
+        mbar_expect_tx(bar, bE + bQ + bT);
+        bulk_g2s(st + oE, edge_src + (size_t)c0 * P, bE, bar);
+        bulk_g2s(st + oQ, p.cellq + c0, bQ, bar);
+        bulk_g2s(st + oT, p.mat + c0, bT, bar);
+    };
+    if (lane == 0)
+        for (int i = 0; i < STAGES - 1; ++i) issue_static(i);
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    int iter, base;
+    if (!iteration_prologue(p, iter, base)) {
+        if (lane == 0)
+            for (int i = 0; i < STAGES - 1 && i < nmine; ++i) mbar_arrive(bars + i);
+        for (int i = 0; i < STAGES - 1 && i < nmine; ++i) (void)mbar_wait(bars + i, 0u);
+        return;
+    }
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    const int frd = PING ? ((base + iter) & 1) : base;
+    const int fwr = frd ^ 1;
+    const phi_t<R> *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
+    phi_t<R> *phw = p.phi[(iter + 1) & 1];
+    const r2<R> *fPr = p.faceP[frd], *fMr = p.faceM[frd];
+    r2<R> *fPw = p.faceP[fwr], *fMw = p.faceM[fwr];
+    const bool refl_l = PING && p.bc_left == BC_REFLECT;
+    const bool refl_r = PING && p.bc_right == BC_REFLECT;
+
+    auto issue_faces = [&](int i) {  // lane 0: this iteration's incident faces of local chunk i
+        if (i >= nmine) return;
+        const int c0 = (gw + i * tw) * CPC;
+        const int nv = J - c0 < CPC ? J - c0 : CPC;
+        unsigned char *st = ring + (size_t)(i % STAGES) * sbytes;
+        unsigned long long *bar = bars + i % STAGES;
+        const unsigned bF = round16(nv * P * 8u);
+        mbar_expect_tx_arrive(bar, 2 * bF);
+        bulk_g2s(st + oP, fPr + (size_t)c0 * P, bF, bar);
+        bulk_g2s(st + oM, fMr + (size_t)(c0 + 1) * P, bF, bar);
+    };
     auto issue = [&](int i) {  // lane 0: copies of local chunk i into stage i % STAGES
         if (i >= nmine) return;
         const int c0 = (gw + i * tw) * CPC;
@@ -781,7 +831,7 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
         bulk_g2s(st + oT, p.mat + c0, bT, bar);
     };
     if (lane == 0)
-        for (int i = 0; i < STAGES - 1; ++i) issue(i);
+        for (int i = 0; i < STAGES - 1; ++i) issue_faces(i);
 
     // pair constants and a per-lane cache of the material coefficients
     r2<R> mw[PPL];
