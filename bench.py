@@ -172,7 +172,7 @@ def run_ours(args, rank, world):
         assert rc == pkg.OCI_OK, (rc, st)
         iters.append(st["iters"])
         secs.append(st["seconds"])
-        launches += st["iters"] + 2  # step prologue + iterations + commit
+        launches += st["launches"]  # kernels of the library for the step (as counted by oci_step)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
@@ -256,8 +256,9 @@ def run_learned(args, pkg, torch, stream):
     """The metric's "plain vs NN+FP32" part on the thin-cell deployment slab
     (131072 cells, S_64, sigma_t dx ~ U(0.01, 0.1), c ~ U(0.9, 0.999), dt = 0.02):
     seconds and iterations per converged step of plain FP32 OCI, FP32 OCI with
-    the trained network's initial guess, plain FP64 OCI and FP32 SI, each from
-    the same initial state, after the same warm-up steps."""
+    the trained network's initial guess, plain FP64 OCI, FP32 SI with the
+    paper's march and FP32 SI with the parallel-prefix sweep, each from the same
+    initial state, after the same warm-up steps."""
     from paper_2305_13555_gb300 import learned
     if not os.path.exists(learned.DEFAULT_WEIGHTS):
         return {"unavailable": "no trained weights"}
@@ -265,11 +266,12 @@ def run_learned(args, pkg, torch, stream):
     prob = workloads.config5_deploy(args.nn_seed, J=131072, N=64, n_steps=16)
     out = {"workload": f"config-5 deployment slab seed {args.nn_seed}: 131072 cells, S_64, thin cells "
                        "(sigma_t dx 0.01-0.1), c 0.9-0.999, dt 0.02, vacuum/vacuum, tol 1e-8"}
-    for name, prec, method, nn, n_w, n_t in (("fp32_plain", "fp32", "oci", False, 2, 6),
-                                              ("fp32_nn_guess", "fp32", "oci", True, 2, 6),
-                                              ("fp64_plain", "fp64", "oci", False, 2, 2),
-                                              ("si_fp32", "fp32", "si", False, 2, 2)):
-        s = pkg.Solver(prob, precision=prec, tol=1e-8, stream=stream.cuda_stream, max_iter=50000)
+    for name, prec, method, nn, n_w, n_t, sweep in (("fp32_plain", "fp32", "oci", False, 2, 6, "march"),
+                                                     ("fp32_nn_guess", "fp32", "oci", True, 2, 6, "march"),
+                                                     ("fp64_plain", "fp64", "oci", False, 2, 2, "march"),
+                                                     ("si_fp32", "fp32", "si", False, 2, 2, "march"),
+                                                     ("si_scan_fp32", "fp32", "si", False, 2, 6, "scan")):
+        s = pkg.Solver(prob, precision=prec, tol=1e-8, stream=stream.cuda_stream, max_iter=50000, sweep=sweep)
         if nn:
             pkg.oci_nn_attach(s.h, W, pkg.OCI_NN_GUESS, 50)
         its, secs, ok = [], [], True

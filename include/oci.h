@@ -94,6 +94,8 @@ typedef struct oci_stats {
     int32_t nn_accepts;  /* learned guess / corrections kept (0 without a network) */
     int32_t nn_rejects;  /* learned corrections reverted by the safeguard */
     int32_t refined;     /* 1 if the FP32 path finished the step with its refinement (see oci_step) */
+    int32_t launches;    /* kernels of this library launched for the step (library GEMMs not counted;
+                          * iteration launches that found the step already ended included) */
 } oci_stats;
 
 typedef struct oci_handle oci_handle;
@@ -193,13 +195,13 @@ int oci_get_state(const oci_handle *h, double *psi_edge);
  * starts from it. */
 int oci_set_state(oci_handle *h, const double *psi_edge);
 
-/* Time the one-cell-inversion iteration kernel alone: run n_iter iterations
- * from the current step's initial iterate as stream launches (no graph, no
- * convergence exit; the staged FP32 kernel as programmatic dependent launches,
- * as inside a step), after two untimed warm-up launches, bracketed by CUDA
- * events on the handle's stream, and return the mean device time per launch
- * in *seconds_per_launch.  With OCI_SOLVER_DENSE one "launch" is a whole
- * dense iteration (right-hand sides, GEMMs, outputs).  The
+/* Time the one-cell-inversion iteration alone: run n_iter iterations from the
+ * current step's initial iterate (no graph, no convergence exit), after two
+ * untimed warm-up iterations, bracketed by CUDA events on the handle's stream,
+ * and return the mean device time per iteration in *seconds_per_launch.  The
+ * staged FP32 path runs them as one cooperative launch of its persistent loop
+ * (as inside a step); other paths as one stream launch per iteration.  With
+ * OCI_SOLVER_DENSE an iteration is right-hand sides, GEMMs and outputs.  The
  * committed state (psi_{k-1/2}, published phi) is untouched and the next step
  * restarts from it.  Used by the benchmark's roofline figure. */
 int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_launch);

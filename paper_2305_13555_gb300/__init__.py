@@ -45,7 +45,7 @@ class OciStats(ctypes.Structure):
     _fields_ = [
         ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("residual", ctypes.c_double),
         ("seconds", ctypes.c_double), ("committed", ctypes.c_int32), ("nn_accepts", ctypes.c_int32),
-        ("nn_rejects", ctypes.c_int32), ("refined", ctypes.c_int32),
+        ("nn_rejects", ctypes.c_int32), ("refined", ctypes.c_int32), ("launches", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -143,6 +143,12 @@ struct oci_handle {
     // SI sweep as a parallel prefix (oci_set_sweep)
     int sweep = OCI_SWEEP_MARCH;
     bool pdl_graph = true;           // programmatic edges between iterations (cleared if unsupported)
+    // persistent OCI loop (staged FP32 kernel, cooperative launch): one launch per step
+    const void *cells_loop = nullptr;
+    bool use_loop = false;
+    double *loop_partials = nullptr;
+    unsigned *loop_bar = nullptr;
+    int loop_fixed = 0;
     void *scan_mem = nullptr;  // segment maps [2P][nseg], entering values [2P][nseg]
     int scan_nseg = 0;
 };
@@ -201,6 +207,9 @@ KParams<R> make_params(const oci_handle *h, int use_cond, cudaGraphConditionalHa
     p.partials = h->partials;
     p.st = h->d_st;
     p.cfg = h->d_cfg;
+    p.loop_partials = h->loop_partials;
+    p.loop_bar = h->loop_bar;
+    p.loop_fixed = h->loop_fixed;
     return p;
 }
 
@@ -419,14 +428,36 @@ int add_iterations(oci_handle *h, cudaGraph_t body, const void *fn, void **args)
     return OCI_OK;
 }
 
-// Step graph: begin -> [si_prep] -> WHILE { [march ->] cells } -> commit.
+// The persistent OCI loop in a graph: zero the barrier counter, then one
+// cooperative launch that iterates until the step is decided (or paused).
+int add_loop(oci_handle *h, cudaGraph_t g, const cudaGraphNode_t *dep, cudaGraphNode_t *out, void **args)
+{
+    cudaMemsetParams mp{};
+    mp.dst = h->loop_bar;
+    mp.value = 0;
+    mp.elementSize = sizeof(unsigned);
+    mp.width = 1;
+    mp.height = 1;
+    cudaGraphNode_t n_zero;
+    CK(h, cudaGraphAddMemsetNode(&n_zero, g, dep, dep ? 1 : 0, &mp));
+    int rc = add_kernel(h, g, out, &n_zero, 1, h->cells_loop, dim3(h->cells_grid), dim3(h->cells_block), args,
+                        h->cells_smem);
+    if (rc) return rc;
+    cudaLaunchAttributeValue v{};
+    v.cooperative = 1;
+    CK(h, cudaGraphKernelNodeSetAttribute(*out, cudaLaunchAttributeCooperative, &v));
+    return OCI_OK;
+}
+
+// Step graph: begin -> [si_prep] -> WHILE { [march ->] cells } -> commit
+// (OCI with the persistent loop: begin -> loop -> commit).
 template <typename R>
 int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout)
 {
     cudaGraph_t g;
     CK(h, cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle cond;
-    CK(h, cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphConditionalHandle cond{};
+    if (si || !h->use_loop) CK(h, cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
     KParams<R> plain = make_params<R>(h, 0, 0);
     KParams<R> loop = make_params<R>(h, 1, cond);
     void *a_plain[] = {&plain};
@@ -439,6 +470,15 @@ int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout
     int rc = add_kernel(h, g, &n_begin, nullptr, 0, (const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st);
     if (rc) return rc;
     n_prev = n_begin;
+    if (!si && h->use_loop) {
+        cudaGraphNode_t n_loop;
+        rc = add_loop(h, g, &n_prev, &n_loop, a_plain);
+        if (!rc) rc = add_kernel(h, g, &n_commit, &n_loop, 1, h->ks.commit_oci, dim3(h->grid_pc), dim3(kBlock), a_plain);
+        if (rc) return rc;
+        CK(h, cudaGraphInstantiate(eout, g, 0));
+        *gout = g;
+        return OCI_OK;
+    }
     if (si) {
         cudaGraphNode_t n_prep;
         rc = add_kernel(h, g, &n_prep, &n_prev, 1, h->ks.si_prep, dim3(h->grid_pc), dim3(kBlock), a_plain);
@@ -496,12 +536,21 @@ int build_cont_graph(oci_handle *h)
 {
     cudaGraph_t g;
     CK(h, cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle cond;
-    CK(h, cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphConditionalHandle cond{};
+    if (!h->use_loop) CK(h, cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
     KParams<R> plain = make_params<R>(h, 0, 0);
     KParams<R> loop = make_params<R>(h, 1, cond);
     void *a_plain[] = {&plain};
     void *a_loop[] = {&loop};
+    if (h->use_loop) {
+        cudaGraphNode_t n_loop, n_commit;
+        int rc = add_loop(h, g, nullptr, &n_loop, a_plain);
+        if (!rc) rc = add_kernel(h, g, &n_commit, &n_loop, 1, h->ks.commit_oci, dim3(h->grid_pc), dim3(kBlock), a_plain);
+        if (rc) return rc;
+        CK(h, cudaGraphInstantiate(&h->exec_cont, g, 0));
+        h->graph_cont = g;
+        return OCI_OK;
+    }
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = cond;
@@ -555,6 +604,13 @@ int ensure_graphs(oci_handle *h)
     if (h->exec_oci) return OCI_OK;
     int rc = h->prec == OCI_FP64 ? build_graph<double>(h, false, &h->graph_oci, &h->exec_oci)
                                  : build_graph<float>(h, false, &h->graph_oci, &h->exec_oci);
+    if (rc && h->use_loop) {
+        // a cooperative kernel node was refused: iterate with one launch per iteration
+        (void)cudaGetLastError();
+        h->use_loop = false;
+        rc = h->prec == OCI_FP64 ? build_graph<double>(h, false, &h->graph_oci, &h->exec_oci)
+                                 : build_graph<float>(h, false, &h->graph_oci, &h->exec_oci);
+    }
     if (rc && h->pdl_graph && h->staged) {
         // programmatic edges refused inside the loop body: plain single launches
         (void)cudaGetLastError();
@@ -786,18 +842,24 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
     CK(h, cudaSetDevice(h->device));
     int rc = ensure_graphs(h);
     if (rc) return rc;
+    int launches = 0;  // kernels of this library enqueued for the step
     if (!h->guess_valid) {
         rc = launch_guess(h);
         if (rc) return rc;
+        ++launches;
     }
     const bool nn = !si && h->nn_mode != OCI_NN_OFF;
     int accepts = 0, rejects = 0;
+    const int unroll = (h->staged && h->pdl_graph) ? kUnroll : 1;  // iteration launches per WHILE body
+    auto body_launches = [&](int iters) { return unroll * ((iters + unroll - 1) / unroll); };
+    int corrections = 0, graph_runs = 0;
     CK(h, cudaEventRecord(h->ev0, h->stream));
     if (nn) {
         rc = nn_guess(h);
         if (rc) return rc;
         h->guess_valid = false;
         ++accepts;
+        launches += 10;  // scale, features, weight rounding, 5 layers, predict, lift
     }
     IterState s{};
     if (!si && h->solver == OCI_SOLVER_DENSE) {
@@ -812,6 +874,7 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         h->cfg.pause_at = k;
         if ((rc = upload_cfg(h))) return rc;
         CK(h, cudaGraphLaunch(h->exec_oci, h->stream));
+        ++graph_runs;
         for (;;) {
             if ((rc = read_state(h, &s))) return rc;
             if (s.status != ocik::ST_RUNNING) break;
@@ -819,9 +882,11 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
                 // pause: try a correction toward phat, keep it only if it helped
                 const double before = s.resid;
                 if ((rc = corr_copy(h, s, true)) || (rc = launch_lift(h, h->ks.lift_corr))) return rc;
+                ++corrections;
                 h->cfg.pause_at = s.iter + m_check;
                 if ((rc = upload_cfg(h))) return rc;
                 CK(h, cudaGraphLaunch(h->exec_cont, h->stream));
+                ++graph_runs;
                 IterState s2{};
                 if ((rc = read_state(h, &s2))) return rc;
                 if (s2.status != ocik::ST_RUNNING) { s = s2; ++accepts; break; }
@@ -837,6 +902,7 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
             h->cfg.pause_at = correcting ? s.iter + k : -1;
             if ((rc = upload_cfg(h))) return rc;
             CK(h, cudaGraphLaunch(h->exec_cont, h->stream));
+            ++graph_runs;
         }
         h->cfg.pause_at = -1;
         if ((rc = upload_cfg(h))) return rc;
@@ -845,12 +911,19 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         if (si) c.stall_floor = 0.0;  // SI has no refinement: no stall stop
         if ((rc = set_device_cfg(h, c))) return rc;
         CK(h, cudaGraphLaunch(si ? h->exec_si : h->exec_oci, h->stream));
+        ++graph_runs;
     }
     if ((rc = read_state(h, &s))) return rc;
+    const int main_iters = s.iter;
+    if (!si && h->solver == OCI_SOLVER_DENSE) launches += 2 + 2 * main_iters;  // begin, rhs + out per iteration, commit
+    else if (si) launches += 3 + main_iters * (h->sweep == OCI_SWEEP_SCAN ? 4 : 2);  // begin, prep, sweep + cells, commit
+    else if (h->use_loop) launches += 1 + 2 * graph_runs + corrections;  // begin, (loop, commit) per graph run, lifts
+    else launches += 2 + body_launches(main_iters) + corrections * (unroll + 1);  // begin, bodies, commit, lifts
     int refined = 0;
     if (s.status == ocik::ST_STALL && !si && h->cells_lin && h->ks.refine) {
         if ((rc = refine_step(h, &s))) return rc;
         refined = 1;
+        launches += 2 + (s.iter - main_iters);  // residual pass, setup, correction iterations, commit
     }
     CK(h, cudaEventRecord(h->ev1, h->stream));
     if ((rc = read_state(h, &s))) return rc;
@@ -872,6 +945,7 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         st->nn_accepts = accepts;
         st->nn_rejects = rejects;
         st->refined = refined;
+        st->launches = launches;
     }
     return status;
 }
@@ -999,6 +1073,20 @@ int oci_create(const oci_problem *p, oci_handle **out)
             const int nch = (J + h->ks.cells_per_warp - 1) / h->ks.cells_per_warp;
             const int want = (nch + warps - 1) / warps;
             h->cells_grid = std::min(sms * per_sm, want);
+            // persistent loop over the iterations of a step: needs every block
+            // resident at once (cooperative launch)
+            int coop = 0, per_sm_loop = 0;
+            if (h->ks.cells_oci_loop && std::getenv("OCI_NO_LOOP") == nullptr &&
+                cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device) == cudaSuccess && coop &&
+                cudaFuncSetAttribute(h->ks.cells_oci_loop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)h->cells_smem) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_loop, h->ks.cells_oci_loop, h->cells_block,
+                                                              h->cells_smem) == cudaSuccess &&
+                h->cells_grid <= sms * per_sm_loop) {
+                h->cells_loop = h->ks.cells_oci_loop;
+                h->use_loop = true;
+            }
+            (void)cudaGetLastError();
         }
     }
     // device layout
@@ -1022,7 +1110,9 @@ int oci_create(const oci_problem *p, oci_handle **out)
                       h->prec == OCI_FP32 ? nm * P * 64 : 0, h->prec == OCI_FP32 ? nm * 16 : 0,
                       h->prec == OCI_FP32 ? (size_t)P * 16 : 0, h->prec == OCI_FP32 ? face : 0,
                       h->prec == OCI_FP32 ? face : 0, h->prec == OCI_FP32 ? (size_t)J * P * 16 : 0,
-                      h->prec == OCI_FP32 ? (size_t)J * 32 : 0};
+                      h->prec == OCI_FP32 ? (size_t)J * 32 : 0,
+                      // persistent loop: (d2, p2, fault) per block for two iterations, barrier counter
+                      (size_t)h->cells_grid * 6 * sizeof(double), sizeof(unsigned)};
     const int ns = sizeof(sizes) / sizeof(sizes[0]);
     size_t off[32], total = 0;
     for (int i = 0; i < ns; ++i) {
@@ -1043,6 +1133,8 @@ int oci_create(const oci_problem *p, oci_handle **out)
     h->partials = (double *)(b + off[18]);
     h->d_st = (IterState *)(b + off[19]);
     h->d_cfg = (IterConfig *)(b + off[20]);
+    h->loop_partials = (double *)(b + off[28]);
+    h->loop_bar = (unsigned *)(b + off[29]);
     if (h->prec == OCI_FP32) {
         h->ref_tab = (double *)(b + off[21]);
         h->ref_par = (double *)(b + off[22]);
@@ -1245,6 +1337,34 @@ int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_la
     IterState *st = h->d_st;
     void *a_st[] = {&st};
     CK(h, cudaLaunchKernel((const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st, 0, h->stream));
+    if (h->use_loop && h->solver == OCI_SOLVER_WOODBURY) {
+        // the persistent loop: one cooperative launch runs a fixed number of iterations
+        auto prepare = [&]() -> int {
+            CK(h, cudaLaunchKernel((const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st, 0, h->stream));
+            CK(h, cudaMemsetAsync(h->loop_bar, 0, sizeof(unsigned), h->stream));
+            return OCI_OK;
+        };
+        auto launch = [&](int n) -> int {
+            h->loop_fixed = n;
+            KParams<float> pl = make_params<float>(h, 0, 0);
+            h->loop_fixed = 0;
+            void *la[] = {&pl};
+            CK(h, cudaLaunchCooperativeKernel(h->cells_loop, dim3(h->cells_grid), dim3(h->cells_block), la,
+                                              h->cells_smem, h->stream));
+            return OCI_OK;
+        };
+        if ((rc = prepare()) || (rc = launch(2)) || (rc = prepare())) return rc;  // warm-up
+        CK(h, cudaEventRecord(h->ev0, h->stream));
+        if ((rc = launch(n_iter))) return rc;
+        CK(h, cudaEventRecord(h->ev1, h->stream));
+        CK(h, cudaEventSynchronize(h->ev1));
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        *seconds_per_launch = ms * 1e-3 / n_iter;
+        if ((rc = set_device_cfg(h, h->cfg))) return rc;
+        h->guess_valid = false;
+        return OCI_OK;
+    }
     KParams<double> pd = make_params<double>(h, 0, 0);
     KParams<float> pf = make_params<float>(h, 0, 0);
     void *args[] = {h->prec == OCI_FP64 ? (void *)&pd : (void *)&pf};

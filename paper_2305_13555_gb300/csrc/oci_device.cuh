@@ -249,6 +249,12 @@ struct KParams {
     double *partials;      // [gridDim.x][2]
     IterState *st;
     const IterConfig *cfg;
+    // persistent OCI loop: per-block (d2, p2, fault) of the last two iterations,
+    // the grid barrier's arrival counter (zeroed before each launch), and a fixed
+    // iteration count for timing (0: run to the iteration controls)
+    double *loop_partials;
+    unsigned *loop_bar;
+    int loop_fixed;
 };
 
 // Reduce V values per lane (s with compensation e) over the LPC lanes of a
@@ -655,6 +661,38 @@ __global__ void __launch_bounds__(256) k_cells(const KParams<R> p)
 // drains (again bounded) its own copies and finishes the iteration normally.
 // ---------------------------------------------------------------------------
 constexpr unsigned kWaitLimit = 1u << 22;
+template <bool B> struct BoolTag { static constexpr bool value = B; };
+
+// Grid-wide barrier of the persistent loop (all blocks resident: cooperative
+// launch).  The arrival counter starts at 0 for each launch; the k-th barrier
+// waits until it reaches k * gridDim.x.  Bounded: false after kWaitLimit polls.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *a)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        bool ok = false;
+        for (unsigned it = 0; it < kWaitLimit; ++it) {
+            if (ld_acquire_u32(count) >= target) {
+                ok = true;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
 
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
 {
@@ -736,7 +774,7 @@ __device__ __forceinline__ int xpose_idx(int l, int v)
     return 32 * l + 4 * (((v >> 2) ^ l ^ (l >> 3)) & 7) + (v & 3);
 }
 
-template <int LPC, int PPL, int CHUNK, int STAGES, int MODE>
+template <int LPC, int PPL, int CHUNK, int STAGES, int MODE, bool LOOP = false>
 __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
 {
     using R = float;
@@ -744,6 +782,7 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
     constexpr int CPC = CHUNK * SPW;
     constexpr int V = 4 * CHUNK;           // partial sums per lane
     constexpr int NOWN = (V * SPW) / 32 > 0 ? (V * SPW) / 32 : 1;  // (segment, value) sums owned per lane
+    static_assert(!LOOP || MODE == M_OCI, "the persistent loop runs the OCI iteration only");
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -770,68 +809,60 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
     const int nchunks = (J + CPC - 1) / CPC;
     const int gw = blockIdx.x * wpb + warp, tw = gridDim.x * wpb;
     const int nmine = gw < nchunks ? (nchunks - 1 - gw) / tw + 1 : 0;
-    bool ok_all = true;
-    int broke_at = nmine;
+    // ring position of this iteration's local chunk 0 (the ring runs on across
+    // the iterations of the persistent loop): local chunk i uses stage
+    // (rp + i) % STAGES with phase parity ((rp + i) / STAGES) & 1
+    int rp = 0;
+    auto stage_of = [&](int i) { return (rp + i) % STAGES; };
+    auto parity_of = [&](int i) { return (unsigned)((rp + i) / STAGES) & 1u; };
 
     auto issue_static = [&](int i) {  // lane 0: iteration-invariant copies of local chunk i
         if (i >= nmine) return;
         const int c0 = (gw + i * tw) * CPC;
         const int nv = J - c0 < CPC ? J - c0 : CPC;
-        unsigned char *st = ring + (size_t)(i % STAGES) * sbytes;
-        unsigned long long *bar = bars + i % STAGES;
+        unsigned char *st = ring + (size_t)stage_of(i) * sbytes;
+        unsigned long long *bar = bars + stage_of(i);
         const unsigned bE = round16(nv * P * 16u), bQ = nv * 16u, bT = round16(nv * 4u);
         mbar_expect_tx(bar, bE + bQ + bT);
         bulk_g2s(st + oE, edge_src + (size_t)c0 * P, bE, bar);
         bulk_g2s(st + oQ, p.cellq + c0, bQ, bar);
         bulk_g2s(st + oT, p.mat + c0, bT, bar);
     };
+    // complete the phases of copies issued for chunks that will not run
+    auto drain_static = [&]() {
+        if (lane == 0)
+            for (int i = 0; i < STAGES - 1 && i < nmine; ++i) mbar_arrive(bars + stage_of(i));
+        for (int i = 0; i < STAGES - 1 && i < nmine; ++i) (void)mbar_wait(bars + stage_of(i), parity_of(i));
+    };
     if (lane == 0)
         for (int i = 0; i < STAGES - 1; ++i) issue_static(i);
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
     int iter, base;
-    if (!iteration_prologue(p, iter, base)) {
-        if (lane == 0)
-            for (int i = 0; i < STAGES - 1 && i < nmine; ++i) mbar_arrive(bars + i);
-        for (int i = 0; i < STAGES - 1 && i < nmine; ++i) (void)mbar_wait(bars + i, 0u);
-        return;
+    // persistent loop: the step state is kept by every block (all take the same
+    // decisions from the same per-block partial sums); block 0 publishes it
+    int status = ST_RUNNING, stall = 0, fixed_left = 0;
+    double best = 0.0;
+    if constexpr (LOOP) {
+        const IterState *st0 = p.st;
+        status = *(volatile const int *)&st0->status;
+        iter = *(volatile const int *)&st0->iter;
+        base = *(volatile const int *)&st0->base;
+        stall = *(volatile const int *)&st0->stall;
+        best = *(volatile const double *)&st0->best;
+        fixed_left = p.loop_fixed;
+        if (status != ST_RUNNING) {
+            drain_static();
+            return;
+        }
+    } else {
+        if (!iteration_prologue(p, iter, base)) {
+            drain_static();
+            return;
+        }
     }
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    const int frd = PING ? ((base + iter) & 1) : base;
-    const int fwr = frd ^ 1;
-    const phi_t<R> *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
-    phi_t<R> *phw = p.phi[(iter + 1) & 1];
-    const r2<R> *fPr = p.faceP[frd], *fMr = p.faceM[frd];
-    r2<R> *fPw = p.faceP[fwr], *fMw = p.faceM[fwr];
     const bool refl_l = PING && p.bc_left == BC_REFLECT;
     const bool refl_r = PING && p.bc_right == BC_REFLECT;
-
-    auto issue_faces = [&](int i) {  // lane 0: this iteration's incident faces of local chunk i
-        if (i >= nmine) return;
-        const int c0 = (gw + i * tw) * CPC;
-        const int nv = J - c0 < CPC ? J - c0 : CPC;
-        unsigned char *st = ring + (size_t)(i % STAGES) * sbytes;
-        unsigned long long *bar = bars + i % STAGES;
-        const unsigned bF = round16(nv * P * 8u);
-        mbar_expect_tx_arrive(bar, 2 * bF);
-        bulk_g2s(st + oP, fPr + (size_t)c0 * P, bF, bar);
-        bulk_g2s(st + oM, fMr + (size_t)(c0 + 1) * P, bF, bar);
-    };
-    auto issue = [&](int i) {  // lane 0: copies of local chunk i into stage i % STAGES
-        if (i >= nmine) return;
-        const int c0 = (gw + i * tw) * CPC;
-        const int nv = J - c0 < CPC ? J - c0 : CPC;
-        unsigned char *st = ring + (size_t)(i % STAGES) * sbytes;
-        unsigned long long *bar = bars + i % STAGES;
-        const unsigned bF = round16(nv * P * 8u), bE = round16(nv * P * 16u), bQ = nv * 16u, bT = round16(nv * 4u);
-        mbar_expect_tx_arrive(bar, 2 * bF + bE + bQ + bT);
-        bulk_g2s(st + oP, fPr + (size_t)c0 * P, bF, bar);
-        bulk_g2s(st + oM, fMr + (size_t)(c0 + 1) * P, bF, bar);
-        bulk_g2s(st + oE, edge_src + (size_t)c0 * P, bE, bar);
-        bulk_g2s(st + oQ, p.cellq + c0, bQ, bar);
-        bulk_g2s(st + oT, p.mat + c0, bT, bar);
-    };
-    if (lane == 0)
-        for (int i = 0; i < STAGES - 1; ++i) issue_faces(i);
 
     // pair constants and a per-lane cache of the material coefficients
     r2<R> mw[PPL];
@@ -853,204 +884,333 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
             }
         }
     };
-
-    float accf_d2 = 0.f, accf_p2 = 0.f;  // per-lane partials; block and grid sums in double
     int mK = -1;
     float4 kA = make_float4(0.f, 0.f, 0.f, 0.f), kB = kA;
-    for (int i = 0; i < nmine; ++i) {
+
+    for (int rep = 0;; ++rep) {
+        const int frd = PING ? ((base + iter) & 1) : base;
+        const int fwr = frd ^ 1;
+        const phi_t<R> *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
+        phi_t<R> *phw = p.phi[(iter + 1) & 1];
+        const r2<R> *fPr = p.faceP[frd], *fMr = p.faceM[frd];
+        r2<R> *fPw = p.faceP[fwr], *fMw = p.faceM[fwr];
+
+        auto issue_faces = [&](int i) {  // lane 0: this iteration's incident faces of local chunk i
+            if (i >= nmine) return;
+            const int c0 = (gw + i * tw) * CPC;
+            const int nv = J - c0 < CPC ? J - c0 : CPC;
+            unsigned char *st = ring + (size_t)stage_of(i) * sbytes;
+            unsigned long long *bar = bars + stage_of(i);
+            const unsigned bF = round16(nv * P * 8u);
+            mbar_expect_tx_arrive(bar, 2 * bF);
+            bulk_g2s(st + oP, fPr + (size_t)c0 * P, bF, bar);
+            bulk_g2s(st + oM, fMr + (size_t)(c0 + 1) * P, bF, bar);
+        };
+        auto issue = [&](int i) {  // lane 0: all copies of local chunk i
+            if (i >= nmine) return;
+            const int c0 = (gw + i * tw) * CPC;
+            const int nv = J - c0 < CPC ? J - c0 : CPC;
+            unsigned char *st = ring + (size_t)stage_of(i) * sbytes;
+            unsigned long long *bar = bars + stage_of(i);
+            const unsigned bF = round16(nv * P * 8u), bE = round16(nv * P * 16u), bQ = nv * 16u,
+                           bT = round16(nv * 4u);
+            mbar_expect_tx_arrive(bar, 2 * bF + bE + bQ + bT);
+            bulk_g2s(st + oP, fPr + (size_t)c0 * P, bF, bar);
+            bulk_g2s(st + oM, fMr + (size_t)(c0 + 1) * P, bF, bar);
+            bulk_g2s(st + oE, edge_src + (size_t)c0 * P, bE, bar);
+            bulk_g2s(st + oQ, p.cellq + c0, bQ, bar);
+            bulk_g2s(st + oT, p.mat + c0, bT, bar);
+        };
         if (lane == 0) {
-            fence_proxy_async();
-            issue(i + STAGES - 1);
+            // faces written by other blocks in the previous iteration (generic stores,
+            // ordered by the grid barrier) before this thread's bulk copies read them
+            if (LOOP && rep > 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
+            for (int i = 0; i < STAGES - 1; ++i) issue_faces(i);
         }
-        const int chunk = gw + i * tw;
-        const unsigned char *st = ring + (size_t)(i % STAGES) * sbytes;
-        if (!mbar_wait(bars + i % STAGES, (unsigned)(i / STAGES) & 1u)) {
-            ok_all = false;
-            broke_at = i;
-            break;
-        }
-        const r2<R> *sP = reinterpret_cast<const r2<R> *>(st + oP);
-        const r2<R> *sM = reinterpret_cast<const r2<R> *>(st + oM);
-        const r4<R> *sE = reinterpret_cast<const r4<R> *>(st + oE);
-        const r4<R> *sQ = reinterpret_cast<const r4<R> *>(st + oQ);
-        const int *sT = reinterpret_cast<const int *>(st + oT);
-        // phi^l of the values this lane owns in phase C, fetched now so the
-        // load overlaps phases A and B
-        float2 old_phi[NOWN], ref_phi[NOWN];
-#pragma unroll
-        for (int k = 0; k < NOWN; ++k) {
-            const int f = lane * NOWN + k;
-            const int g = f / V, v = f % V;
-            const int cell = chunk * CPC + (v >> 2) * SPW + g;
-            const bool ok = g < SPW && cell < J;
-            old_phi[k] = ok ? __ldcg(phr + 4 * (size_t)cell + (v & 3)) : make_float2(0.f, 0.f);
-            ref_phi[k] = (MODE == M_LIN && ok) ? __ldg(p.phi_ref + 4 * (size_t)cell + (v & 3)) : make_float2(0.f, 0.f);
-        }
-        // ---------------- phase A: y = A^{-1} c per ordinate pair; lane partials
-        // of the moments w (y+ + conj(y-)) go to the transpose buffer
-#pragma unroll
-        for (int r = 0; r < CHUNK; ++r) {
-            const int cl = r * SPW + seg;
-            const int cell = chunk * CPC + cl;
-            R m0 = 0, m1 = 0, m2 = 0, m3 = 0;
-            if (cell < J) {
-                coefs(sT[cl]);
-                const r4<R> qd = sQ[cl];
-                R fkl = 0, fkr = 0, fhl = 0, fhr = 0;
-                if (MODE == M_SI) {
-                    load_phi4<R>(phr, cell, fkl, fkr, fhl, fhr);
-                    fkl *= cs; fkr *= cs; fhl *= cs; fhr *= cs;
+
+        float accf_d2 = 0.f, accf_p2 = 0.f;  // per-lane partials; block and grid sums in double
+        bool ok_all = true;
+        int broke_at = nmine;
+        for (int i = 0; i < nmine; ++i) {
+            if (lane == 0) {
+                fence_proxy_async();
+                issue(i + STAGES - 1);
+            }
+            const int chunk = gw + i * tw;
+            const unsigned char *st = ring + (size_t)stage_of(i) * sbytes;
+            if (!mbar_wait(bars + stage_of(i), parity_of(i))) {
+                ok_all = false;
+                broke_at = i;
+                break;
+            }
+            const r2<R> *sP = reinterpret_cast<const r2<R> *>(st + oP);
+            const r2<R> *sM = reinterpret_cast<const r2<R> *>(st + oM);
+            const r4<R> *sE = reinterpret_cast<const r4<R> *>(st + oE);
+            const r4<R> *sQ = reinterpret_cast<const r4<R> *>(st + oQ);
+            const int *sT = reinterpret_cast<const int *>(st + oT);
+            // phi^l of the values this lane owns in phase C, fetched now so the
+            // load overlaps phases A and B
+            float2 old_phi[NOWN], ref_phi[NOWN];
+    #pragma unroll
+            for (int k = 0; k < NOWN; ++k) {
+                const int f = lane * NOWN + k;
+                const int g = f / V, v = f % V;
+                const int cell = chunk * CPC + (v >> 2) * SPW + g;
+                const bool ok = g < SPW && cell < J;
+                old_phi[k] = ok ? __ldcg(phr + 4 * (size_t)cell + (v & 3)) : make_float2(0.f, 0.f);
+                ref_phi[k] = (MODE == M_LIN && ok) ? __ldg(p.phi_ref + 4 * (size_t)cell + (v & 3)) : make_float2(0.f, 0.f);
+            }
+            // interior chunk of one material (no boundary cell, all rows present):
+            // the per-row checks and coefficient lookups are hoisted
+            const bool fast = chunk > 0 && (chunk + 1) * CPC < J && __all_sync(FULL, sT[lane % CPC] == sT[0]);
+            if (fast) coefs(sT[0]);
+            // ---------------- phase A: y = A^{-1} c per ordinate pair; lane partials
+            // of the moments w (y+ + conj(y-)) go to the transpose buffer
+            auto phase_a = [&](auto fast_tag) {
+            constexpr bool FAST = decltype(fast_tag)::value;
+    #pragma unroll
+            for (int r = 0; r < CHUNK; ++r) {
+                const int cl = r * SPW + seg;
+                const int cell = chunk * CPC + cl;
+                R m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+                if (FAST || cell < J) {
+                    if (!FAST) coefs(sT[cl]);
+                    const r4<R> qd = sQ[cl];
+                    R fkl = 0, fkr = 0, fhl = 0, fhr = 0;
+                    if (MODE == M_SI) {
+                        load_phi4<R>(phr, cell, fkl, fkr, fhl, fhr);
+                        fkl *= cs; fkr *= cs; fhl *= cs; fhr *= cs;
+                    }
+    #pragma unroll
+                    for (int t = 0; t < PPL; ++t) {
+                        const int pp = ls + LPC * t;
+                        if (pp >= P) continue;
+                        const Coef<R> &a = ac[t];
+                        const r2<R> inP = (!FAST && refl_l && cell == 0) ? ld2(fMr + pp) : sP[cl * P + pp];
+                        const r2<R> inM = (!FAST && refl_r && cell == J - 1) ? ld2(fPr + (size_t)J * P + pp) : sM[cl * P + pp];
+                        r4<R> *slot = const_cast<r4<R> *>(sE) + cl * P + pp;  // this lane's own (cell, pair) slot
+                        const r4<R> pe = *slot;                               // psi_{k-1/2} (M_LIN: r0)
+                        PairRhs<R> u = MODE == M_LIN ? PairRhs<R>{0, 0, 0, 0, 0, 0, 0, 0} : pair_rhs_fixed(qd, ce, pe);
+                        r4<R> yo;
+                        if (MODE == M_SI) {
+                            // outgoing part of A^{-1} c_fixed; the next sweep's offset adds
+                            // s (A^{-1} phi^{l+1})_out in phase E
+                            yo.x = a.pr * u.uki + a.pi * u.ukr + a.rr * u.uhi + a.ri * u.uhr;
+                            yo.y = a.ur * u.uki + a.ui * u.ukr + a.vr * u.uhi + a.vi * u.uhr;
+                            yo.z = a.pr * u.vkr - a.pi * u.vki + a.rr * u.vhr - a.ri * u.vhi;
+                            yo.w = a.ur * u.vkr - a.ui * u.vki + a.vr * u.vhr - a.vi * u.vhi;
+                            u.ukr += fkl; u.uki += fkr; u.uhr += fhl; u.uhi += fhr;
+                            u.vkr += fkl; u.vki -= fkr; u.vhr += fhl; u.vhi -= fhr;
+                            if (!FAST && cell == J - 1 && p.bc_right == BC_REFLECT)
+                                st2(p.refl + pp, ld2(fPr + (size_t)J * P + pp).x, ld2(fPr + (size_t)J * P + pp).y);
+                        }
+                        u.ukr += mw[t].x * inP.x; u.uhr += mw[t].x * inP.y;
+                        u.vki -= mw[t].x * inM.x; u.vhi -= mw[t].x * inM.y;
+                        R ykr, yki, yhr, yhi, zkr, zki, zhr, zhi;
+                        ainv(a, u.ukr, u.uki, u.uhr, u.uhi, ykr, yki, yhr, yhi);
+                        ainv(a, u.vkr, u.vki, u.vhr, u.vhi, zkr, zki, zhr, zhi);
+                        if (MODE != M_SI) {  // outgoing corners of y (M_LIN: plus r0)
+                            yo = r4<R>{yki, yhi, zkr, zhr};
+                            if (MODE == M_LIN) { yo.x += pe.x; yo.y += pe.y; yo.z += pe.z; yo.w += pe.w; }
+                        }
+                        *slot = yo;  // phase E reads it back; no other lane touches this slot
+                        m0 += mw[t].y * (ykr + zkr); m1 += mw[t].y * (yki - zki);
+                        m2 += mw[t].y * (yhr + zhr); m3 += mw[t].y * (yhi - zhi);
+                    }
                 }
-#pragma unroll
+                *reinterpret_cast<float4 *>(xp + xpose_idx(lane, 4 * r)) = make_float4(m0, m1, m2, m3);
+            }
+            };
+            if (fast) phase_a(BoolTag<true>{});
+            else phase_a(BoolTag<false>{});
+            __syncwarp();
+            // ---------------- phase B: each lane sums the LPC lane partials of the
+            // (segment, moment) values it owns, compensated (Kahan)
+            ff own[NOWN];
+    #pragma unroll
+            for (int k = 0; k < NOWN; ++k) {
+                const int f = lane * NOWN + k;
+                const int g = f / V, v = f % V;  // segment and value index (row * 4 + moment)
+                // KC interleaved Kahan sums over the segment's lanes, joined exactly
+                constexpr int KC = LPC >= 4 ? 4 : LPC;
+                float sk[KC], ck[KC];
+    #pragma unroll
+                for (int a = 0; a < KC; ++a) { sk[a] = 0.f; ck[a] = 0.f; }
+                if (g < SPW) {
+    #pragma unroll
+                    for (int q = 0; q < LPC; q += KC) {
+    #pragma unroll
+                        for (int a = 0; a < KC; ++a) {
+                            const float x = xp[xpose_idx(g * LPC + q + a, v)];
+                            const float y = __fsub_rn(x, ck[a]);
+                            const float t = __fadd_rn(sk[a], y);
+                            ck[a] = __fsub_rn(__fsub_rn(t, sk[a]), y);
+                            sk[a] = t;
+                        }
+                    }
+                }
+                ff acc = ff_norm(sk[0], -ck[0]);
+    #pragma unroll
+                for (int a = 1; a < KC; ++a) acc = ff_add(acc, ff_norm(sk[a], -ck[a]));
+                own[k] = acc;
+            }
+            __syncwarp();
+            // ---------------- phase C: capacitance solve + residual, in double
+    #pragma unroll
+            for (int k = 0; k < NOWN; ++k) {
+                const int f = lane * NOWN + k;
+                const int g = f / V, v = f % V;
+                const int row = v >> 2, comp = v & 3;
+                const int cell = chunk * CPC + row * SPW + g;
+                ff phi;
+                if (MODE != M_SI) {
+                    ff r_par;
+                    if constexpr (NOWN >= 4) {
+                        r_par = own[k ^ 2];
+                    } else {
+                        constexpr int o = NOWN == 2 ? 1 : 2;
+                        r_par.h = __shfl_xor_sync(FULL, own[k].h, o);
+                        r_par.l = __shfl_xor_sync(FULL, own[k].l, o);
+                    }
+                    const int m = (g < SPW && cell < J) ? sT[row * SPW + g] : 0;
+                    if (m != mK) {  // capacitance of this value's material (cached per lane)
+                        mK = m;
+                        kA = __ldg(p.matKf + 2 * m);
+                        kB = __ldg(p.matKf + 2 * m + 1);
+                    }
+                    phi = comp < 2 ? ff_add(ff_mul(ff{kA.x, kA.y}, own[k]), ff_mul(ff{kA.z, kA.w}, r_par))
+                                   : ff_add(ff_mul(ff{kB.x, kB.y}, r_par), ff_mul(ff{kB.z, kB.w}, own[k]));
+                } else {
+                    phi = own[k];
+                }
+                if (g < SPW && cell < J) {
+                    const float2 old = old_phi[k];
+                    const float d = ff_diff(phi, ff{old.x, old.y});
+                    accf_d2 = __fmaf_rn(d, d, accf_d2);
+                    // norm of the whole iterate (M_LIN: phi(h0) + correction)
+                    const float tot = MODE == M_LIN ? __fadd_rn(ref_phi[k].x, phi.h) : phi.h;
+                    accf_p2 = __fmaf_rn(tot, tot, accf_p2);
+                    phw[4 * (size_t)cell + comp] = make_float2(phi.h, phi.l);
+                    xp[g * V + v] = __fadd_rn(phi.h, phi.l);  // phi of (segment g, value v) for phase D
+                }
+            }
+            __syncwarp();
+            // ---------------- phase D/E: outgoing corners = y_out + s (A^{-1} Phi)_out
+            auto phase_e = [&](auto fast_tag) {
+            constexpr bool FAST = decltype(fast_tag)::value;
+    #pragma unroll
+            for (int r = 0; r < CHUNK; ++r) {
+                const int cl = r * SPW + seg;
+                const int cell = chunk * CPC + cl;
+                if (!FAST && cell >= J) continue;
+                if (!FAST) coefs(sT[cl]);
+                const float4 F = *reinterpret_cast<const float4 *>(xp + seg * V + 4 * r);
+                const R Fkl = F.x * cs, Fkr = F.y * cs, Fhl = F.z * cs, Fhr = F.w * cs;
+    #pragma unroll
                 for (int t = 0; t < PPL; ++t) {
                     const int pp = ls + LPC * t;
                     if (pp >= P) continue;
                     const Coef<R> &a = ac[t];
-                    const r2<R> inP = (refl_l && cell == 0) ? ld2(fMr + pp) : sP[cl * P + pp];
-                    const r2<R> inM = (refl_r && cell == J - 1) ? ld2(fPr + (size_t)J * P + pp) : sM[cl * P + pp];
-                    r4<R> *slot = const_cast<r4<R> *>(sE) + cl * P + pp;  // this lane's own (cell, pair) slot
-                    const r4<R> pe = *slot;                               // psi_{k-1/2} (M_LIN: r0)
-                    PairRhs<R> u = MODE == M_LIN ? PairRhs<R>{0, 0, 0, 0, 0, 0, 0, 0} : pair_rhs_fixed(qd, ce, pe);
-                    r4<R> yo;
-                    if (MODE == M_SI) {
-                        // outgoing part of A^{-1} c_fixed; the next sweep's offset adds
-                        // s (A^{-1} phi^{l+1})_out in phase E
-                        yo.x = a.pr * u.uki + a.pi * u.ukr + a.rr * u.uhi + a.ri * u.uhr;
-                        yo.y = a.ur * u.uki + a.ui * u.ukr + a.vr * u.uhi + a.vi * u.uhr;
-                        yo.z = a.pr * u.vkr - a.pi * u.vki + a.rr * u.vhr - a.ri * u.vhi;
-                        yo.w = a.ur * u.vkr - a.ui * u.vki + a.vr * u.vhr - a.vi * u.vhi;
-                        u.ukr += fkl; u.uki += fkr; u.uhr += fhl; u.uhi += fhr;
-                        u.vkr += fkl; u.vki -= fkr; u.vhr += fhl; u.vhi -= fhr;
-                        if (cell == J - 1 && p.bc_right == BC_REFLECT)
-                            st2(p.refl + pp, ld2(fPr + (size_t)J * P + pp).x, ld2(fPr + (size_t)J * P + pp).y);
-                    }
-                    u.ukr += mw[t].x * inP.x; u.uhr += mw[t].x * inP.y;
-                    u.vki -= mw[t].x * inM.x; u.vhi -= mw[t].x * inM.y;
-                    R ykr, yki, yhr, yhi, zkr, zki, zhr, zhi;
-                    ainv(a, u.ukr, u.uki, u.uhr, u.uhi, ykr, yki, yhr, yhi);
-                    ainv(a, u.vkr, u.vki, u.vhr, u.vhi, zkr, zki, zhr, zhi);
-                    if (MODE != M_SI) {  // outgoing corners of y (M_LIN: plus r0)
-                        yo = r4<R>{yki, yhi, zkr, zhr};
-                        if (MODE == M_LIN) { yo.x += pe.x; yo.y += pe.y; yo.z += pe.z; yo.w += pe.w; }
-                    }
-                    *slot = yo;  // phase E reads it back; no other lane touches this slot
-                    m0 += mw[t].y * (ykr + zkr); m1 += mw[t].y * (yki - zki);
-                    m2 += mw[t].y * (yhr + zhr); m3 += mw[t].y * (yhi - zhi);
-                }
-            }
-            *reinterpret_cast<float4 *>(xp + xpose_idx(lane, 4 * r)) = make_float4(m0, m1, m2, m3);
-        }
-        __syncwarp();
-        // ---------------- phase B: each lane sums the LPC lane partials of the
-        // (segment, moment) values it owns, compensated (Kahan)
-        ff own[NOWN];
-#pragma unroll
-        for (int k = 0; k < NOWN; ++k) {
-            const int f = lane * NOWN + k;
-            const int g = f / V, v = f % V;  // segment and value index (row * 4 + moment)
-            // KC interleaved Kahan sums over the segment's lanes, joined exactly
-            constexpr int KC = LPC >= 4 ? 4 : LPC;
-            float sk[KC], ck[KC];
-#pragma unroll
-            for (int a = 0; a < KC; ++a) { sk[a] = 0.f; ck[a] = 0.f; }
-            if (g < SPW) {
-#pragma unroll
-                for (int q = 0; q < LPC; q += KC) {
-#pragma unroll
-                    for (int a = 0; a < KC; ++a) {
-                        const float x = xp[xpose_idx(g * LPC + q + a, v)];
-                        const float y = __fsub_rn(x, ck[a]);
-                        const float t = __fadd_rn(sk[a], y);
-                        ck[a] = __fsub_rn(__fsub_rn(t, sk[a]), y);
-                        sk[a] = t;
+                    const r4<R> yo = sE[cl * P + pp];
+                    // +mu: Im(A^{-1} s Phi); -mu: Re(A^{-1} s conj(Phi))
+                    const R ok = yo.x + (a.pr * Fkr + a.pi * Fkl + a.rr * Fhr + a.ri * Fhl);
+                    const R oh = yo.y + (a.ur * Fkr + a.ui * Fkl + a.vr * Fhr + a.vi * Fhl);
+                    const R mk = yo.z + (a.pr * Fkl + a.pi * Fkr + a.rr * Fhl + a.ri * Fhr);
+                    const R mh = yo.w + (a.ur * Fkl + a.ui * Fkr + a.vr * Fhl + a.vi * Fhr);
+                    if (PING) {
+                        st2(fPw + (size_t)(cell + 1) * P + pp, ok, oh);
+                        st2(fMw + (size_t)cell * P + pp, mk, mh);
+                    } else {
+                        st4(p.g + (size_t)pp * J + cell, ok, oh, mk, mh);
                     }
                 }
             }
-            ff acc = ff_norm(sk[0], -ck[0]);
-#pragma unroll
-            for (int a = 1; a < KC; ++a) acc = ff_add(acc, ff_norm(sk[a], -ck[a]));
-            own[k] = acc;
+            };
+            if (fast) phase_e(BoolTag<true>{});
+            else phase_e(BoolTag<false>{});
+            fence_proxy_async();  // this lane's phase-A stores into the ring before the next copy into it
+            __syncwarp();  // stage i and the transpose buffer fully read
         }
-        __syncwarp();
-        // ---------------- phase C: capacitance solve + residual, in double
-#pragma unroll
-        for (int k = 0; k < NOWN; ++k) {
-            const int f = lane * NOWN + k;
-            const int g = f / V, v = f % V;
-            const int row = v >> 2, comp = v & 3;
-            const int cell = chunk * CPC + row * SPW + g;
-            ff phi;
-            if (MODE != M_SI) {
-                ff r_par;
-                if constexpr (NOWN >= 4) {
-                    r_par = own[k ^ 2];
-                } else {
-                    constexpr int o = NOWN == 2 ? 1 : 2;
-                    r_par.h = __shfl_xor_sync(FULL, own[k].h, o);
-                    r_par.l = __shfl_xor_sync(FULL, own[k].l, o);
-                }
-                const int m = (g < SPW && cell < J) ? sT[row * SPW + g] : 0;
-                if (m != mK) {  // capacitance of this value's material (cached per lane)
-                    mK = m;
-                    kA = __ldg(p.matKf + 2 * m);
-                    kB = __ldg(p.matKf + 2 * m + 1);
-                }
-                phi = comp < 2 ? ff_add(ff_mul(ff{kA.x, kA.y}, own[k]), ff_mul(ff{kA.z, kA.w}, r_par))
-                               : ff_add(ff_mul(ff{kB.x, kB.y}, r_par), ff_mul(ff{kB.z, kB.w}, own[k]));
-            } else {
-                phi = own[k];
-            }
-            if (g < SPW && cell < J) {
-                const float2 old = old_phi[k];
-                const float d = ff_diff(phi, ff{old.x, old.y});
-                accf_d2 = __fmaf_rn(d, d, accf_d2);
-                // norm of the whole iterate (M_LIN: phi(h0) + correction)
-                const float tot = MODE == M_LIN ? __fadd_rn(ref_phi[k].x, phi.h) : phi.h;
-                accf_p2 = __fmaf_rn(tot, tot, accf_p2);
-                phw[4 * (size_t)cell + comp] = make_float2(phi.h, phi.l);
-                xp[g * V + v] = __fadd_rn(phi.h, phi.l);  // phi of (segment g, value v) for phase D
-            }
+        if (!ok_all) {
+            // a copy never completed: record it and wait (bounded) for this warp's
+            // outstanding copies before the block's shared memory is released
+            if (lane == 0) atomicExch(&p.st->status, ST_TIMEOUT);
+            const int last = broke_at + STAGES - 1 < nmine ? broke_at + STAGES - 1 : nmine;
+            for (int k = broke_at; k < last; ++k) (void)mbar_wait(bars + stage_of(k), parity_of(k));
         }
-        __syncwarp();
-        // ---------------- phase D/E: outgoing corners = y_out + s (A^{-1} Phi)_out
-#pragma unroll
-        for (int r = 0; r < CHUNK; ++r) {
-            const int cl = r * SPW + seg;
-            const int cell = chunk * CPC + cl;
-            if (cell >= J) continue;
-            coefs(sT[cl]);
-            const float4 F = *reinterpret_cast<const float4 *>(xp + seg * V + 4 * r);
-            const R Fkl = F.x * cs, Fkr = F.y * cs, Fhl = F.z * cs, Fhr = F.w * cs;
-#pragma unroll
-            for (int t = 0; t < PPL; ++t) {
-                const int pp = ls + LPC * t;
-                if (pp >= P) continue;
-                const Coef<R> &a = ac[t];
-                const r4<R> yo = sE[cl * P + pp];
-                // +mu: Im(A^{-1} s Phi); -mu: Re(A^{-1} s conj(Phi))
-                const R ok = yo.x + (a.pr * Fkr + a.pi * Fkl + a.rr * Fhr + a.ri * Fhl);
-                const R oh = yo.y + (a.ur * Fkr + a.ui * Fkl + a.vr * Fhr + a.vi * Fhl);
-                const R mk = yo.z + (a.pr * Fkl + a.pi * Fkr + a.rr * Fhl + a.ri * Fhr);
-                const R mh = yo.w + (a.ur * Fkl + a.ui * Fkr + a.vr * Fhl + a.vi * Fhr);
-                if (PING) {
-                    st2(fPw + (size_t)(cell + 1) * P + pp, ok, oh);
-                    st2(fMw + (size_t)cell * P + pp, mk, mh);
-                } else {
-                    st4(p.g + (size_t)pp * J + cell, ok, oh, mk, mh);
+        if constexpr (!LOOP) {
+            finalize_iteration((double)accf_d2, (double)accf_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond);
+            return;
+        } else {
+            rp += nmine;
+            const bool block_ok = __syncthreads_and(ok_all ? 1 : 0) != 0;
+            // the next iteration's invariant copies go out before the barrier
+            if (lane == 0 && block_ok)
+                for (int i = 0; i < STAGES - 1; ++i) issue_static(i);
+            double d2 = (double)accf_d2, p2 = (double)accf_p2;
+            block_sum2(d2, p2);
+            const int G = gridDim.x;
+            double *lp = p.loop_partials + (size_t)(iter & 1) * 3 * G;
+            if (threadIdx.x == 0) {
+                lp[3 * blockIdx.x] = d2;
+                lp[3 * blockIdx.x + 1] = p2;
+                lp[3 * blockIdx.x + 2] = block_ok ? 0.0 : 1.0;
+            }
+            const bool bar_ok = grid_barrier(p.loop_bar, (unsigned)(rep + 1) * (unsigned)G);
+            // every block sums the partials in the same fixed order
+            double a = 0.0, b = 0.0, f = 0.0;
+            for (int q = threadIdx.x; q < G; q += blockDim.x) {
+                a += __ldcg(lp + 3 * q);
+                b += __ldcg(lp + 3 * q + 1);
+                f += __ldcg(lp + 3 * q + 2);
+            }
+            block_sum2(a, b);
+            const bool fault = __syncthreads_or(f != 0.0 ? 1 : 0) != 0 || !bar_ok;
+            __shared__ double s_ab[2];
+            if (threadIdx.x == 0) { s_ab[0] = a; s_ab[1] = b; }
+            __syncthreads();
+            a = s_ab[0];
+            b = s_ab[1];
+            const int it = iter + 1;
+            double resid;
+            if (b > 0.0) resid = sqrt(a / b);
+            else resid = (a == 0.0) ? 0.0 : __longlong_as_double(0x7ff0000000000000LL);
+            int ns = ST_RUNNING;
+            const IterConfig *cfg = p.cfg;
+            if (fault) ns = ST_TIMEOUT;
+            else if (!(resid == resid) || !(a == a) || !(b == b) || isinf(b)) ns = ST_NAN;
+            else if (fixed_left > 0) ns = it >= fixed_left ? ST_MAXITER : ST_RUNNING;  // timing: a fixed count
+            else if (resid < cfg->tol) ns = ST_CONVERGED;
+            else if (it >= cfg->max_iter) ns = ST_MAXITER;
+            if (ns == ST_RUNNING && fixed_left == 0 && cfg->stall_floor > 0.0) {
+                if (cfg->stall_iters < 0) {
+                    if (resid < cfg->stall_floor) ns = ST_STALL;
+                } else if (resid < 0.9 * best) {
+                    best = resid;
+                    stall = 0;
+                } else if (++stall >= cfg->stall_iters && resid < cfg->stall_floor) {
+                    ns = ST_STALL;
                 }
             }
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                IterState *sw = p.st;
+                sw->iter = it;
+                sw->resid = resid;
+                sw->d2 = a;
+                sw->p2 = b;
+                sw->stall = stall;
+                sw->best = best;
+                sw->launches += 1;
+                if (ns != ST_TIMEOUT || sw->status == ST_RUNNING) sw->status = ns;
+            }
+            iter = it;
+            status = ns;
+            if (status != ST_RUNNING || it == cfg->pause_at) {
+                if (block_ok) drain_static();
+                return;
+            }
         }
-        fence_proxy_async();  // this lane's phase-A stores into the ring before the next copy into it
-        __syncwarp();  // stage i and the transpose buffer fully read
     }
-    if (!ok_all) {
-        // a copy never completed: record it and wait (bounded) for this warp's
-        // outstanding copies before the block's shared memory is released
-        if (lane == 0) atomicExch(&p.st->status, ST_TIMEOUT);
-        const int last = broke_at + STAGES - 1 < nmine ? broke_at + STAGES - 1 : nmine;
-        for (int k = broke_at; k < last; ++k) (void)mbar_wait(bars + k % STAGES, (unsigned)(k / STAGES) & 1u);
-    }
-    finalize_iteration((double)accf_d2, (double)accf_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond);
 }
 
 // ---------------------------------------------------------------------------

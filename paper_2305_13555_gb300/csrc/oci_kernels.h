@@ -17,6 +17,7 @@ struct KernelSet {
     const void *lift_guess;  // k_lift<LIFT_GUESS>
     const void *lift_corr;   // k_lift<LIFT_CORR>
     const void *cells_oci_tma;  // k_cells_tma<M_OCI> (FP32, even P) or nullptr
+    const void *cells_oci_loop; // k_cells_tma<M_OCI, persistent loop> or nullptr
     const void *cells_si_tma;   // k_cells_tma<M_SI>
     int tma_stages;             // ring depth of the staged kernels
     const void *cells_lin_tma;  // k_cells_tma<M_LIN> (FP32 refinement) or nullptr

@@ -23,11 +23,13 @@ static void fill(KernelSet *k)
     k->lift_guess = (const void *)&k_lift<float, LPC, PPL, LIFT_GUESS>;
     k->lift_corr = (const void *)&k_lift<float, LPC, PPL, LIFT_CORR>;
     k->cells_oci_tma = nullptr;
+    k->cells_oci_loop = nullptr;
     k->cells_si_tma = nullptr;
     k->cells_lin_tma = nullptr;
     k->tma_stages = 0;
     if constexpr (LPC >= 2) {
         k->cells_oci_tma = (const void *)&k_cells_tma<LPC, PPL, CHUNK, kStages, M_OCI>;
+        k->cells_oci_loop = (const void *)&k_cells_tma<LPC, PPL, CHUNK, kStages, M_OCI, true>;
         k->cells_si_tma = (const void *)&k_cells_tma<LPC, PPL, CHUNK, kStages, M_SI>;
         k->cells_lin_tma = (const void *)&k_cells_tma<LPC, PPL, CHUNK, kStages, M_LIN>;
         k->tma_stages = kStages;
@@ -50,6 +52,7 @@ bool kernel_set_f32(int lpc, int ppl, KernelSet *out)
         fill<32, 1, 8>(out);
         if (const char *e = std::getenv("OCI_TMA_STAGES"); e && e[0] == '3') {
             out->cells_oci_tma = (const void *)&k_cells_tma<32, 1, 8, 3, M_OCI>;
+            out->cells_oci_loop = (const void *)&k_cells_tma<32, 1, 8, 3, M_OCI, true>;
             out->cells_si_tma = (const void *)&k_cells_tma<32, 1, 8, 3, M_SI>;
             out->cells_lin_tma = (const void *)&k_cells_tma<32, 1, 8, 3, M_LIN>;
             out->tma_stages = 3;

@@ -19,6 +19,7 @@ static void fill(KernelSet *k)
     k->lift_guess = (const void *)&k_lift<double, LPC, PPL, LIFT_GUESS>;
     k->lift_corr = (const void *)&k_lift<double, LPC, PPL, LIFT_CORR>;
     k->cells_oci_tma = nullptr;
+    k->cells_oci_loop = nullptr;
     k->cells_si_tma = nullptr;
     k->cells_lin_tma = nullptr;
     k->commit_lin = nullptr;

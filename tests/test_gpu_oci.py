@@ -281,3 +281,21 @@ def test_fp32_stalling_trajectory_converges():
             rc, st = s.step()
             assert rc == pkg.OCI_OK, (k, rc, st)
             assert _rel(s.fluxes(), ref[k]) < FP32_TOL
+
+
+def test_step_reports_its_kernel_launches():
+    """oci_stats.launches: prologue, commit, the initial-iterate kernel of a
+    first step, and the iteration launches: one per iteration (FP64: plain
+    kernels in a WHILE body), or one persistent launch for all iterations
+    (the staged FP32 path)."""
+    prob = workloads.config2(64, 0.9, 0.1, J=4096, n_steps=2)
+    for prec in ("fp32", "fp64"):
+        with pkg.Solver(prob, precision=prec) as s:
+            for k in range(2):
+                rc, st = s.step()
+                assert rc == pkg.OCI_OK, (rc, st)
+                fixed = 2 + (1 if k == 0 else 0)
+                if prec == "fp64":
+                    assert st["launches"] == fixed + st["iters"], (prec, st)
+                else:
+                    assert st["launches"] in (fixed + 1, *range(fixed + st["iters"], fixed + st["iters"] + 4)), st
