@@ -154,6 +154,17 @@ int oci_set_solver(oci_handle *h, int32_t solver);
 enum { OCI_SWEEP_MARCH = 0, OCI_SWEEP_SCAN = 1 };
 int oci_set_sweep(oci_handle *h, int32_t sweep);
 
+/* Diagnostics of the bounded waits (the paper has no counterpart).  The
+ * persistent FP32 iteration meets the other blocks at a grid barrier once per
+ * iteration; every wait there gives up after poll_limit polls (0: the default,
+ * about a second) and the step then ends with OCI_ETIMEOUT, the state left at
+ * the previous step, the device usable.  barrier_shortfall > 0 makes the
+ * barrier wait for that many arrivals more than the grid has -- a wait that
+ * nothing satisfies -- so tests can drive the timeout path without a fault;
+ * 0 restores normal operation.  Applies from the next step; OCI_EINVAL for a
+ * NULL handle or a negative shortfall. */
+int oci_set_wait_limits(oci_handle *h, uint32_t poll_limit, int32_t barrier_shortfall);
+
 /* Advance one time step with one-cell inversion (Sec. "One-Cell Inversion"):
  * each iteration every cell solves (A - S) Psi = c for its 4N unknowns with
  * the neighbours' incident fluxes from iterate l, via the block-diagonal plus

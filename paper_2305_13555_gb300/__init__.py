@@ -62,6 +62,7 @@ SIGNATURES = {
     "oci_set_stream": (ctypes.c_int, [_VP, _VP]),
     "oci_set_solver": (ctypes.c_int, [_VP, _I32]),
     "oci_set_sweep": (ctypes.c_int, [_VP, _I32]),
+    "oci_set_wait_limits": (ctypes.c_int, [_VP, ctypes.c_uint32, _I32]),
     "oci_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
     "si_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
     "oci_fluxes": (ctypes.c_int, [_VP, _VP]),
@@ -200,6 +201,11 @@ def oci_set_sweep(h, sweep):
     """OCI_SWEEP_MARCH (default) or OCI_SWEEP_SCAN for si_step (see oci.h); also "march" / "scan"."""
     sweep = _SWEEP.get(sweep, sweep)
     _check(load_library().oci_set_sweep(h, int(sweep)), "oci_set_sweep", h)
+
+
+def oci_set_wait_limits(h, poll_limit=0, barrier_shortfall=0):
+    """Bounded-wait diagnostics (see oci.h): grid-barrier poll limit, missing arrivals."""
+    _check(load_library().oci_set_wait_limits(h, int(poll_limit), int(barrier_shortfall)), "oci_set_wait_limits", h)
 
 
 def oci_step(h):

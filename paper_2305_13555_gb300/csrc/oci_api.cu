@@ -128,7 +128,9 @@ struct oci_handle {
     size_t nn_ws_bytes = 0;
     cudaGraph_t graph_cont = nullptr;
     cudaGraphExec_t exec_cont = nullptr;
-    std::vector<double> q_host;      // sources (for the network's inputs)
+    std::vector<double> q_host;      // sources (for the network's inputs; valid while q_host_valid)
+    bool q_host_valid = false;
+    double *q_dev = nullptr, *dx_dev = nullptr;  // FP64 source moments [J][4] and cell widths [J]
     std::vector<double> bc_left_host, bc_right_host;  // prescribed incident data
     // FP32 refinement (stalled steps): FP64 tables, saved halo, residual, phi(h0)
     double *ref_tab = nullptr, *ref_par = nullptr, *ref_muw = nullptr;
@@ -290,21 +292,57 @@ void nn_host_features(const oci_handle *h, std::vector<float> &stat, std::vector
     }
 }
 
+// (dx/4) Q in the storage precision, from the FP64 source moments on the device.
+template <typename R>
+__global__ void k_scale_source(const double *__restrict__ q, const double *__restrict__ dx, int J, r4<R> *cellq)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < J; j += gridDim.x * blockDim.x) {
+        const double f = dx[j] / 4.0;
+        const double *qj = q + 4 * (size_t)j;
+        cellq[j] = r4<R>{(R)(f * qj[0]), (R)(f * qj[1]), (R)(f * qj[2]), (R)(f * qj[3])};
+    }
+}
+
+// The host keeps a copy of Q only while a network is attached (its source input).
+int sync_q_host(oci_handle *h)
+{
+    if (h->q_host_valid) return OCI_OK;
+    h->q_host.resize((size_t)h->J * 4);
+    CK(h, cudaMemcpyAsync(h->q_host.data(), h->q_dev, (size_t)h->J * 32, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->q_host_valid = true;
+    return OCI_OK;
+}
+
+// New source moments: one host-to-device copy of Q and a scaling kernel, no
+// host-side conversion (the copy is enqueued; pageable sources are staged by
+// the driver before the call returns).
 int upload_source(oci_handle *h, const double *q)
 {
-    if (q) h->q_host.assign(q, q + (size_t)h->J * 4);
-    else h->q_host.assign((size_t)h->J * 4, 0.0);
+    const size_t bytes = (size_t)h->J * 32;
+    if (q) CK(h, cudaMemcpyAsync(h->q_dev, q, bytes, cudaMemcpyHostToDevice, h->stream));
+    else CK(h, cudaMemsetAsync(h->q_dev, 0, bytes, h->stream));
+    const int grid = std::min((h->J + 255) / 256, 152 * 8);
+    if (h->prec == OCI_FP64)
+        k_scale_source<double><<<grid, 256, 0, h->stream>>>(h->q_dev, h->dx_dev, h->J, (r4<double> *)h->cellq);
+    else
+        k_scale_source<float><<<grid, 256, 0, h->stream>>>(h->q_dev, h->dx_dev, h->J, (r4<float> *)h->cellq);
+    CK(h, cudaGetLastError());
+    h->q_host_valid = false;
     if (h->nn_mem) {
+        if (q) {
+            h->q_host.assign(q, q + (size_t)h->J * 4);
+            h->q_host_valid = true;
+        } else {
+            h->q_host.assign((size_t)h->J * 4, 0.0);
+            h->q_host_valid = true;
+        }
         std::vector<float> st, qf;
         nn_host_features(h, st, qf);
         CK(h, cudaMemcpyAsync(h->nn_qfeat, qf.data(), sizeof(float) * qf.size(), cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
     }
-    std::vector<double> cq((size_t)h->J * 4, 0.0);
-    if (q)
-        for (int j = 0; j < h->J; ++j)
-            for (int c = 0; c < 4; ++c) cq[(size_t)j * 4 + c] = h->dx[j] / 4.0 * q[(size_t)j * 4 + c];
-    return upload_real(h, h->cellq, cq);
+    return OCI_OK;
 }
 
 // Per-material tables: complex entries of A_{+mu_p}^{-1}, (e, s), and the
@@ -913,7 +951,8 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         CK(h, cudaGraphLaunch(si ? h->exec_si : h->exec_oci, h->stream));
         ++graph_runs;
     }
-    if ((rc = read_state(h, &s))) return rc;
+    CK(h, cudaEventRecord(h->ev1, h->stream));
+    if ((rc = read_state(h, &s))) return rc;  // the step's one synchronisation in the common case
     const int main_iters = s.iter;
     if (!si && h->solver == OCI_SOLVER_DENSE) launches += 2 + 2 * main_iters;  // begin, rhs + out per iteration, commit
     else if (si) launches += 3 + main_iters * (h->sweep == OCI_SWEEP_SCAN ? 4 : 2);  // begin, prep, sweep + cells, commit
@@ -924,9 +963,9 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         if ((rc = refine_step(h, &s))) return rc;
         refined = 1;
         launches += 2 + (s.iter - main_iters);  // residual pass, setup, correction iterations, commit
+        CK(h, cudaEventRecord(h->ev1, h->stream));
+        if ((rc = read_state(h, &s))) return rc;
     }
-    CK(h, cudaEventRecord(h->ev1, h->stream));
-    if ((rc = read_state(h, &s))) return rc;
     float ms = 0.f;
     CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     h->guess_valid = s.committed != 0;
@@ -989,6 +1028,8 @@ int oci_create(const oci_problem *p, oci_handle **out)
     h->cfg.pause_at = -1;
     h->cfg.stall_iters = 8;
     h->cfg.stall_floor = 0.0;  // enabled below for the FP32 path with refinement
+    h->cfg.bar_poll_limit = 0;
+    h->cfg.bar_shortfall = 0;
     gauss_legendre(N, h->mu, h->w);
     h->dx.assign(p->dx, p->dx + J);
     // materials: distinct (dx, sigma_t, sigma_s)
@@ -1112,9 +1153,10 @@ int oci_create(const oci_problem *p, oci_handle **out)
                       h->prec == OCI_FP32 ? face : 0, h->prec == OCI_FP32 ? (size_t)J * P * 16 : 0,
                       h->prec == OCI_FP32 ? (size_t)J * 32 : 0,
                       // persistent loop: (d2, p2, fault) per block for two iterations, barrier counter
-                      (size_t)h->cells_grid * 6 * sizeof(double), sizeof(unsigned)};
+                      (size_t)h->cells_grid * 6 * sizeof(double), sizeof(unsigned),
+                      (size_t)J * 32, (size_t)J * 8};                        // q_dev, dx_dev
     const int ns = sizeof(sizes) / sizeof(sizes[0]);
-    size_t off[32], total = 0;
+    size_t off[40], total = 0;
     for (int i = 0; i < ns; ++i) {
         off[i] = total;
         // 256 B of slack: staged copies round sizes up to 16 B
@@ -1135,6 +1177,8 @@ int oci_create(const oci_problem *p, oci_handle **out)
     h->d_cfg = (IterConfig *)(b + off[20]);
     h->loop_partials = (double *)(b + off[28]);
     h->loop_bar = (unsigned *)(b + off[29]);
+    h->q_dev = (double *)(b + off[30]);
+    h->dx_dev = (double *)(b + off[31]);
     if (h->prec == OCI_FP32) {
         h->ref_tab = (double *)(b + off[21]);
         h->ref_par = (double *)(b + off[22]);
@@ -1162,6 +1206,10 @@ int oci_create(const oci_problem *p, oci_handle **out)
         return OCI_ECUDA;
     }
     rc = build_tables(h);
+    // cell widths for the source scaling (after the allocation was cleared)
+    if (!rc && cudaMemcpyAsync(h->dx_dev, h->dx.data(), sizeof(double) * J, cudaMemcpyHostToDevice, h->stream) !=
+                   cudaSuccess)
+        rc = cuda_fail(h, cudaGetLastError(), "cell widths");
     if (!rc) rc = upload_source(h, p->q);
     if (!rc) rc = upload_boundaries(h, p->psi_bc_left, p->psi_bc_right);
     if (!rc) rc = load_state(h, p->psi0);
@@ -1218,6 +1266,14 @@ int oci_set_stream(oci_handle *h, void *cuda_stream)
     if (!h) return OCI_EINVAL;
     CK(h, cudaStreamSynchronize(h->stream));
     h->stream = (cudaStream_t)cuda_stream;
+    return OCI_OK;
+}
+
+int oci_set_wait_limits(oci_handle *h, uint32_t poll_limit, int32_t barrier_shortfall)
+{
+    if (!h || barrier_shortfall < 0) return OCI_EINVAL;
+    h->cfg.bar_poll_limit = poll_limit;
+    h->cfg.bar_shortfall = barrier_shortfall;
     return OCI_OK;
 }
 
@@ -1435,6 +1491,7 @@ int oci_nn_attach(oci_handle *h, const float *params, int32_t mode, int32_t k_co
         h->nn_ws_bytes = ws;
         h->nn_face_bak = b + off[11];
         std::vector<float> st, qf;
+        if (int rq = sync_q_host(h)) return rq;
         nn_host_features(h, st, qf);
         CK(h, cudaMemcpy(h->nn_stat, st.data(), sizeof(float) * st.size(), cudaMemcpyHostToDevice));
         CK(h, cudaMemcpy(h->nn_qfeat, qf.data(), sizeof(float) * qf.size(), cudaMemcpyHostToDevice));
@@ -1454,6 +1511,7 @@ int oci_nn_static_features(const oci_handle *hc, void *stat, void *qfeat)
     oci_handle *h = const_cast<oci_handle *>(hc);
     if (!h || !stat || !qfeat) return OCI_EINVAL;
     CK(h, cudaSetDevice(h->device));
+    if (int rq = sync_q_host(h)) return rq;
     std::vector<float> st, qf;
     nn_host_features(h, st, qf);
     CK(h, cudaMemcpy(stat, st.data(), sizeof(float) * st.size(), cudaMemcpyHostToDevice));

@@ -71,6 +71,8 @@ struct IterConfig {
     int pause_at;      // iteration count at which the loop stops with the step still running (-1: never)
     int stall_iters;   // stop with ST_STALL after this many iterations without a 10% improvement ...
     double stall_floor;  // ... once the relative change is below this (0 disables)
+    unsigned bar_poll_limit;  // grid-barrier polls before a timeout (0: kWaitLimit)
+    int bar_shortfall;        // arrivals the grid barrier waits for beyond the grid (diagnostic; 0)
 };
 
 
@@ -672,7 +674,7 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *a)
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
     return v;
 }
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target)
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, unsigned limit)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -680,7 +682,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target)
         __threadfence();
         atomicAdd(count, 1u);
         bool ok = false;
-        for (unsigned it = 0; it < kWaitLimit; ++it) {
+        for (unsigned it = 0; it < limit; ++it) {
             if (ld_acquire_u32(count) >= target) {
                 ok = true;
                 break;
@@ -1156,7 +1158,9 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                 lp[3 * blockIdx.x + 1] = p2;
                 lp[3 * blockIdx.x + 2] = block_ok ? 0.0 : 1.0;
             }
-            const bool bar_ok = grid_barrier(p.loop_bar, (unsigned)(rep + 1) * (unsigned)G);
+            const IterConfig *cfg = p.cfg;
+            const bool bar_ok = grid_barrier(p.loop_bar, (unsigned)(rep + 1) * (unsigned)G + (unsigned)cfg->bar_shortfall,
+                                             cfg->bar_poll_limit ? cfg->bar_poll_limit : kWaitLimit);
             // every block sums the partials in the same fixed order
             double a = 0.0, b = 0.0, f = 0.0;
             for (int q = threadIdx.x; q < G; q += blockDim.x) {
@@ -1176,7 +1180,6 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
             if (b > 0.0) resid = sqrt(a / b);
             else resid = (a == 0.0) ? 0.0 : __longlong_as_double(0x7ff0000000000000LL);
             int ns = ST_RUNNING;
-            const IterConfig *cfg = p.cfg;
             if (fault) ns = ST_TIMEOUT;
             else if (!(resid == resid) || !(a == a) || !(b == b) || isinf(b)) ns = ST_NAN;
             else if (fixed_left > 0) ns = it >= fixed_left ? ST_MAXITER : ST_RUNNING;  // timing: a fixed count
@@ -1837,14 +1840,15 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const KParams<R> p, Aff<
     if (threadIdx.x == 0) agg[(size_t)ch * gridDim.x + seg] = T;
 }
 
-// One warp per pair: boundary values, segment entering values (lane 0).
+// One warp per pair: boundary values, then the entering value of every segment
+// as a warp scan over 32 segments at a time (lane s holds segment base + s).
 template <typename R>
 __global__ void __launch_bounds__(32) k_scan_segments(const KParams<R> p, const Aff<R> *__restrict__ agg,
                                                       r2<R> *__restrict__ enter, int nseg)
 {
     IterState *st = p.st;
     if (*(volatile int *)&st->status != ST_RUNNING) return;
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
     const int fb = *(volatile int *)&st->base;
     const int J = p.J, P = p.P, pp = blockIdx.x;
     // mu < 0 enters through the right face: prescribed / vacuum data or (reflecting)
@@ -1852,20 +1856,35 @@ __global__ void __launch_bounds__(32) k_scan_segments(const KParams<R> p, const 
     r2<R> x;
     if (p.bc_right == BC_REFLECT) {
         x = ld2(p.refl + pp);
-        st2(p.faceM[fb] + (size_t)J * P + pp, x.x, x.y);
+        if (lane == 0) st2(p.faceM[fb] + (size_t)J * P + pp, x.x, x.y);
     } else {
         x = ld2(p.faceM[fb] + (size_t)J * P + pp);
     }
     for (int c = 0; c < 2; ++c) {
         const int ch = 2 * pp + c;
         if (c == 1) {
-            if (p.bc_left == BC_REFLECT) st2(p.faceP[fb] + pp, x.x, x.y);  // this sweep's mu < 0 flux at x = 0
-            else x = ld2(p.faceP[fb] + pp);
+            if (p.bc_left == BC_REFLECT) {
+                if (lane == 0) st2(p.faceP[fb] + pp, x.x, x.y);  // this sweep's mu < 0 flux at x = 0
+            } else {
+                x = ld2(p.faceP[fb] + pp);
+            }
         }
-        for (int s = 0; s < nseg; ++s) {
-            enter[(size_t)ch * nseg + s] = x;
-            const Aff<R> A = agg[(size_t)ch * nseg + s];
-            x = r2<R>{A.a * x.x + (A.b * x.y + A.e), A.c * x.x + (A.d * x.y + A.f)};
+        for (int s0 = 0; s0 < nseg; s0 += 32) {
+            const int sg = s0 + lane;
+            Aff<R> I = sg < nseg ? agg[(size_t)ch * nseg + sg] : aff_id<R>();
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const Aff<R> e = aff_shfl_up(I, d);
+                if (lane >= d) I = aff_then(e, I);
+            }
+            Aff<R> E = aff_shfl_up(I, 1);
+            if (lane == 0) E = aff_id<R>();
+            if (sg < nseg)
+                enter[(size_t)ch * nseg + sg] = r2<R>{E.a * x.x + (E.b * x.y + E.e), E.c * x.x + (E.d * x.y + E.f)};
+            // all 32 maps of this pass (identity beyond nseg) applied to the entering value
+            const R a = __shfl_sync(FULL, I.a, 31), b = __shfl_sync(FULL, I.b, 31), cc = __shfl_sync(FULL, I.c, 31);
+            const R d = __shfl_sync(FULL, I.d, 31), e = __shfl_sync(FULL, I.e, 31), f = __shfl_sync(FULL, I.f, 31);
+            x = r2<R>{a * x.x + (b * x.y + e), cc * x.x + (d * x.y + f)};
         }
     }
 }

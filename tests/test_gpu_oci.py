@@ -299,3 +299,22 @@ def test_step_reports_its_kernel_launches():
                     assert st["launches"] == fixed + st["iters"], (prec, st)
                 else:
                     assert st["launches"] in (fixed + 1, *range(fixed + st["iters"], fixed + st["iters"] + 4)), st
+
+
+def test_grid_barrier_wait_runs_out_and_the_device_recovers():
+    """Failure path of the persistent FP32 iteration without a fault: a grid
+    barrier that waits for one arrival more than the grid has (a flag nothing
+    sets) gives up after a short poll limit; the step ends with OCI_ETIMEOUT,
+    nothing is committed, and the next steps run normally and match a solver
+    that never timed out."""
+    prob = workloads.config2(64, 0.9, 0.1, J=65536, n_steps=3)
+    with pkg.Solver(prob, precision="fp32") as s, pkg.Solver(prob, precision="fp32") as ref:
+        pkg.oci_set_wait_limits(s.h, 2000, 1)
+        rc, st = s.step()
+        assert rc == pkg.OCI_ETIMEOUT and st["committed"] == 0, (rc, st)
+        pkg.oci_set_wait_limits(s.h, 0, 0)
+        for _ in range(2):
+            rc, st = s.step()
+            rc2, st2 = ref.step()
+            assert rc == rc2 == pkg.OCI_OK and st["iters"] == st2["iters"], (st, st2)
+            assert np.array_equal(s.fluxes(), ref.fluxes())
