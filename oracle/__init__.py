@@ -57,6 +57,7 @@ def load_library(path):
     lib.oracle_si_iteration.argtypes = [ctypes.POINTER(_Problem), dp, dp, dp, dp, dp]
     lib.oracle_run.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                ctypes.c_int32, ctypes.c_int32, dp, dp, dp, dp, ctypes.c_int32]
+    lib.oracle_be_run.argtypes = lib.oracle_run.argtypes
     lib.oracle_max_threads.restype = ctypes.c_int
     return lib
 
@@ -162,6 +163,27 @@ def run(prob, method=OCI, n_steps=1, tol=1e-10, max_iter=10000, commit_unconverg
     if st not in (0, 4, 5):
         raise RuntimeError(f"oracle_run failed ({st})")
     return {"psi_edge": pe, "phi_steps": phs, "iters": its, "resid": res, "status": st}
+
+
+def run_be(prob, method=OCI, n_steps=1, tol=1e-10, max_iter=10000, commit_unconverged=False,
+           psi=None, n_threads=0, lib=None):
+    """Backward-Euler variant (one time level per step, Sigma_hat = Sigma +
+    1/(v dt), source psi^{n-1}/(v dt); the source at the new time is Q_{k+1/2}).
+    Returns psi [J][N][2] (last committed step), phi_steps [n_steps][J][2],
+    iters, resid, status.  The initial psi is prob's psi0 (or ``psi``)."""
+    p = _as_problem(prob)
+    if isinstance(method, str):
+        method = {"oci": OCI, "si": SI}[method.lower()]
+    ps = (p.psi0 if psi is None else _f64(psi, (p.J, p.N, 2))).copy()
+    phs = np.zeros((n_steps, p.J, 2))
+    its = np.zeros(n_steps, dtype=np.int32)
+    res = np.zeros(n_steps)
+    st = _load(lib).oracle_be_run(ctypes.byref(p.s), int(method), int(n_steps), float(tol), int(max_iter),
+                                  int(bool(commit_unconverged)), _ptr(ps), _ptr(phs),
+                                  its.ctypes.data_as(ctypes.c_void_p), _ptr(res), int(n_threads))
+    if st not in (0, 4, 5):
+        raise RuntimeError(f"oracle_be_run failed ({st})")
+    return {"psi": ps, "phi_steps": phs, "iters": its, "resid": res, "status": st}
 
 
 def max_threads() -> int:

@@ -139,3 +139,89 @@ def run(prob, n_steps, psi_edge=None):
         pe = psi[:, :, 2:4].copy()
         phis.append(phi)
     return pe, np.array(phis)
+
+
+def be_step_system(prob, psi_prev):
+    """Assemble (M, rhs) for one backward-Euler step from psi^{n-1} = psi_prev
+    [J][N][2]: per cell, ordinate and half-cell the SCB balance
+    mu (psi_out_face - psi_in_face) + Sigma_hat dx/2 psi_corner
+        = dx/2 [Sigma_s/2 phi_corner + Q/2 + psi^{n-1}_corner/(v dt)],
+    Sigma_hat = Sigma + 1/(v dt), with the midpoint value (psi_L + psi_R)/2 at
+    x_j and the upstream corner at the cell edges (unlagged), Q = Q_{k+1/2}.
+    Unknown u(j, m, c) = (j*N + m)*2 + c, c in (L, R)."""
+    J, N = int(prob["n_cells"]), int(prob["n_ord"])
+    P = N // 2
+    mu, w = np.polynomial.legendre.leggauss(N)
+    dx = np.asarray(prob["dx"], float)
+    sig = np.asarray(prob["sigma_t"], float)
+    sigs = np.asarray(prob["sigma_s"], float)
+    q = np.zeros((J, 4)) if prob.get("q") is None else np.asarray(prob["q"], float).reshape(J, 4)
+    v, dt = float(prob["v"]), float(prob["dt"])
+    inv_vdt = 0.0 if np.isinf(v) else 1.0 / (v * dt)
+    bcl, bcr = _bc(prob.get("bc_left", 0)), _bc(prob.get("bc_right", 0))
+    psl = None if prob.get("psi_bc_left") is None else np.asarray(prob["psi_bc_left"], float).reshape(P, 2)
+    psr = None if prob.get("psi_bc_right") is None else np.asarray(prob["psi_bc_right"], float).reshape(P, 2)
+    pp = np.asarray(psi_prev, float).reshape(J, N, 2)
+    n = 2 * N * J
+    M = np.zeros((n, n))
+    b = np.zeros(n)
+
+    def u(j, m, c):
+        return (j * N + m) * 2 + c
+
+    def add_face(row, coef, j, m, side):
+        """coef * (flux of ordinate m on the `side` face of cell j, upstream value)."""
+        if side == "left":
+            if mu[m] < 0:
+                M[row, u(j, m, 0)] += coef
+            elif j > 0:
+                M[row, u(j - 1, m, 1)] += coef
+            elif bcl == BC_REFLECT:
+                M[row, u(0, N - 1 - m, 0)] += coef
+            elif bcl == BC_INCIDENT and psl is not None:
+                b[row] -= coef * psl[m - P, 1]
+        else:
+            if mu[m] > 0:
+                M[row, u(j, m, 1)] += coef
+            elif j + 1 < J:
+                M[row, u(j + 1, m, 0)] += coef
+            elif bcr == BC_REFLECT:
+                M[row, u(J - 1, N - 1 - m, 1)] += coef
+            elif bcr == BC_INCIDENT and psr is not None:
+                b[row] -= coef * psr[P - 1 - m, 1]
+
+    for j in range(J):
+        h = dx[j] / 2.0
+        sh = sig[j] + inv_vdt
+        for m in range(N):
+            mm = mu[m]
+            for c, side in ((0, "left"), (1, "right")):
+                r = u(j, m, c)
+                # mu (psi_mid - psi_left_face) or mu (psi_right_face - psi_mid)
+                sgn = 1.0 if c == 0 else -1.0
+                M[r, u(j, m, 0)] += sgn * mm / 2
+                M[r, u(j, m, 1)] += sgn * mm / 2
+                add_face(r, -sgn * mm, j, m, side)
+                M[r, u(j, m, c)] += h * sh
+                for k in range(N):
+                    M[r, u(j, k, c)] -= h / 2 * sigs[j] * w[k]
+                b[r] += h / 2 * q[j, 2 + c] + h * inv_vdt * pp[j, m, c]
+    return M, b
+
+
+def be_solve_step(prob, psi_prev):
+    M, b = be_step_system(prob, psi_prev)
+    J, N = int(prob["n_cells"]), int(prob["n_ord"])
+    return np.linalg.solve(M, b).reshape(J, N, 2)
+
+
+def be_run(prob, n_steps, psi0=None):
+    """Dense BE steps; returns (psi [J][N][2], phi_steps [n][J][2])."""
+    J, N = int(prob["n_cells"]), int(prob["n_ord"])
+    _, w = np.polynomial.legendre.leggauss(N)
+    psi = np.zeros((J, N, 2)) if psi0 is None else np.asarray(psi0, float).reshape(J, N, 2).copy()
+    phis = []
+    for _ in range(n_steps):
+        psi = be_solve_step(prob, psi)
+        phis.append(np.einsum("n,jnc->jc", w, psi))
+    return psi, np.array(phis)

@@ -34,6 +34,15 @@
  *     right face uses iterate l;
  *   - prescribed incident boundary values are given per time moment (k, k+1/2).
  *
+ * Backward-Euler variant (the paper's disabled section "Backward Euler transient
+ * implementation"): one time level per step, the total cross section becomes
+ * Sigma_hat = Sigma + 1/(v dt) and the previous step's angular flux enters as a
+ * source psi^{n-1}/(v dt).  In space it is the same SCB cell: the per-ordinate
+ * 2x2 block is the SCB part of the printed A^+/A^- (their k-rows with the time
+ * terms removed) with Sigma_hat, and S couples the same corner across ordinates.
+ * Reading: the source at the new time is Q_{k+1/2} (components 2, 3 of q).
+ *   be_psi [J][N][2] (L,R) at the new time; be_phi [J][2].
+ *
  * Layouts (row-major, doubles):
  *   ordinates m = 0..N-1 ascending in mu (mu_m < 0 for m < N/2); mirror(m) = N-1-m;
  *   psi      [J][N][4]  components (k,L) (k,R) (k+1/2,L) (k+1/2,R), Eq. for psi_n;
@@ -505,6 +514,210 @@ int oracle_run(const oracle_problem *p, int32_t method, int32_t n_steps, double 
         if (phi_steps) memcpy(phi_steps + (size_t)step * J * 4, fc, sizeof(double) * (size_t)J * 4);
     }
     free(psiA); free(psiB); free(phiA); free(phiB); free(mu); free(w);
+    return status;
+}
+
+/* ------------------------------------------------------ backward Euler (BE) */
+
+/* SCB block of ordinate mu with total cross section sig_hat: the k-rows of the
+ * printed A^+/A^- with 1/(v dt) = 0 (steady state) and Sigma -> Sigma_hat. */
+static void assemble_B_m(double mu, double dx, double sig_hat, double *b)
+{
+    double a[16];
+    assemble_A_m(mu, dx, sig_hat, INFINITY, 1.0, a);
+    b[0] = a[0]; b[1] = a[1];
+    b[2] = a[4]; b[3] = a[5];
+}
+
+static inline size_t ix_be(int j, int m, int c, int N) { return ((size_t)j * N + m) * 2 + c; }
+
+/* Incident flux of ordinate m on cell j from the BE iterate psi [J][N][2]. */
+static double be_incident(const oracle_problem *p, const double *mu, const double *psi, int j, int m)
+{
+    const int J = p->n_cells, N = p->n_ord, P = N / 2;
+    if (mu[m] > 0.0) {
+        if (j > 0) return psi[ix_be(j - 1, m, 1, N)];
+        if (p->bc_left == ORC_BC_REFLECT) return psi[ix_be(0, N - 1 - m, 0, N)];
+        if (p->bc_left == ORC_BC_INCIDENT && p->psi_bc_left) return p->psi_bc_left[(m - P) * 2 + 1];
+        return 0.0;
+    } else {
+        if (j < J - 1) return psi[ix_be(j + 1, m, 0, N)];
+        if (p->bc_right == ORC_BC_REFLECT) return psi[ix_be(J - 1, N - 1 - m, 1, N)];
+        if (p->bc_right == ORC_BC_INCIDENT && p->psi_bc_right) return p->psi_bc_right[(P - 1 - m) * 2 + 1];
+        return 0.0;
+    }
+}
+
+/* Fixed part of the BE right-hand side of ordinate m in cell j plus the
+ * incident term: (dx/4) Q_{k+1/2} + e psi^{n-1} (e = dx/(2 v dt), the
+ * half-cell integral of psi^{n-1}/(v dt)) + |mu| psi_in in the upstream corner. */
+static void be_rhs(const oracle_problem *p, double mu, int j, const double *pprev, double in, double *c2)
+{
+    const double dx = p->dx[j];
+    const double e = dx / (2.0 * p->v * p->dt);
+    const double *Q = p->q + (size_t)j * 4;
+    c2[0] = dx / 4.0 * Q[2] + e * pprev[0];
+    c2[1] = dx / 4.0 * Q[3] + e * pprev[1];
+    if (mu > 0.0) c2[0] += mu * in;
+    else c2[1] -= mu * in;
+}
+
+/* One BE OCI iteration: per cell the dense 2N x 2N system (B - S) psi = c,
+ * LU with partial pivoting per distinct material.  psi_prev [J][N][2] is
+ * psi^{n-1}; psi_in the iterate l; writes psi_out and phi_out [J][2]. */
+int oracle_be_oci_iteration(const oracle_problem *p, const double *psi_prev, const double *psi_in,
+                            double *psi_out, double *phi_out)
+{
+    const int J = p->n_cells, N = p->n_ord, n2 = 2 * N;
+    double *mu = malloc(sizeof(double) * N), *w = malloc(sizeof(double) * N);
+    double *M = malloc(sizeof(double) * (size_t)n2 * n2);
+    int *piv = malloc(sizeof(int) * (size_t)n2);
+    double *c = malloc(sizeof(double) * (size_t)n2);
+    if (!mu || !w || !M || !piv || !c) { free(mu); free(w); free(M); free(piv); free(c); return 2; }
+    oracle_gauss_legendre(N, mu, w);
+    int err = 0;
+    double cdx = NAN, cst = NAN, css = NAN;
+    for (int j = 0; j < J && !err; ++j) {
+        const double dx = p->dx[j], st = p->sigma_t[j], ss = p->sigma_s[j];
+        if (!(dx == cdx && st == cst && ss == css)) { /* factorise once per run of one material */
+            const double sig_hat = st + 1.0 / (p->v * p->dt);
+            memset(M, 0, sizeof(double) * (size_t)n2 * n2);
+            double b[4];
+            for (int m = 0; m < N; ++m) {
+                assemble_B_m(mu[m], dx, sig_hat, b);
+                for (int r = 0; r < 2; ++r)
+                    for (int q = 0; q < 2; ++q) M[(size_t)(2 * m + r) * n2 + 2 * m + q] += b[r * 2 + q];
+            }
+            const double s = dx * ss / 4.0;
+            for (int m = 0; m < N; ++m)
+                for (int n = 0; n < N; ++n)
+                    for (int i = 0; i < 2; ++i) M[(size_t)(2 * m + i) * n2 + 2 * n + i] -= s * w[n];
+            if (lu_factor(n2, M, piv)) { err = 3; break; }
+            cdx = dx; cst = st; css = ss;
+        }
+        for (int m = 0; m < N; ++m)
+            be_rhs(p, mu[m], j, psi_prev + ix_be(j, m, 0, N), be_incident(p, mu, psi_in, j, m), c + 2 * m);
+        lu_solve(n2, M, piv, c);
+        memcpy(psi_out + ix_be(j, 0, 0, N), c, sizeof(double) * (size_t)n2);
+    }
+    if (!err)
+        for (int j = 0; j < J; ++j)
+            for (int i = 0; i < 2; ++i) {
+                double sum = 0.0;
+                for (int n = 0; n < N; ++n) sum += w[n] * psi_out[ix_be(j, n, i, N)];
+                phi_out[(size_t)j * 2 + i] = sum;
+            }
+    free(mu); free(w); free(M); free(piv); free(c);
+    return err;
+}
+
+/* One BE SI iteration: per ordinate a sweep in the direction of travel
+ * (mu < 0 first), each cell's 2x2 SCB block solved with the lagged scalar
+ * flux phi_in [J][2] in the source. */
+int oracle_be_si_iteration(const oracle_problem *p, const double *psi_prev, const double *phi_in,
+                           const double *psi_in, double *psi_out, double *phi_out)
+{
+    const int J = p->n_cells, N = p->n_ord, P = N / 2;
+    double *mu = malloc(sizeof(double) * N), *w = malloc(sizeof(double) * N);
+    if (!mu || !w) { free(mu); free(w); return 2; }
+    oracle_gauss_legendre(N, mu, w);
+    int err = 0;
+    for (int pass = 0; pass < 2 && !err; ++pass) {
+        const int m0 = pass == 0 ? 0 : P, m1 = pass == 0 ? P : N;
+        for (int m = m0; m < m1; ++m) {
+            double in;
+            if (mu[m] < 0.0) {
+                if (p->bc_right == ORC_BC_REFLECT) in = psi_in[ix_be(J - 1, N - 1 - m, 1, N)];  /* lagged */
+                else if (p->bc_right == ORC_BC_INCIDENT && p->psi_bc_right) in = p->psi_bc_right[(P - 1 - m) * 2 + 1];
+                else in = 0.0;
+            } else {
+                if (p->bc_left == ORC_BC_REFLECT) in = psi_out[ix_be(0, N - 1 - m, 0, N)];  /* this sweep */
+                else if (p->bc_left == ORC_BC_INCIDENT && p->psi_bc_left) in = p->psi_bc_left[(m - P) * 2 + 1];
+                else in = 0.0;
+            }
+            for (int t = 0; t < J; ++t) {
+                const int j = mu[m] > 0.0 ? t : J - 1 - t;
+                const double dx = p->dx[j], st = p->sigma_t[j], ss = p->sigma_s[j];
+                double b[4], c2[2];
+                int piv[2];
+                assemble_B_m(mu[m], dx, st + 1.0 / (p->v * p->dt), b);
+                be_rhs(p, mu[m], j, psi_prev + ix_be(j, m, 0, N), in, c2);
+                c2[0] += dx * ss / 4.0 * phi_in[(size_t)j * 2 + 0];
+                c2[1] += dx * ss / 4.0 * phi_in[(size_t)j * 2 + 1];
+                if (lu_factor(2, b, piv)) { err = 3; break; }
+                lu_solve(2, b, piv, c2);
+                psi_out[ix_be(j, m, 0, N)] = c2[0];
+                psi_out[ix_be(j, m, 1, N)] = c2[1];
+                in = mu[m] > 0.0 ? c2[1] : c2[0];  /* outgoing corner */
+            }
+        }
+    }
+    if (!err)
+        for (int j = 0; j < J; ++j)
+            for (int i = 0; i < 2; ++i) {
+                double sum = 0.0;
+                for (int n = 0; n < N; ++n) sum += w[n] * psi_out[ix_be(j, n, i, N)];
+                phi_out[(size_t)j * 2 + i] = sum;
+            }
+    free(mu); free(w);
+    return err;
+}
+
+/* March n_steps BE steps (method 0 OCI, 1 SI).  psi [J][N][2]: on entry
+ * psi^0, on exit the last committed step's flux; phi_steps [n_steps][J][2];
+ * same controls and return codes as oracle_run.  The initial iterate of a
+ * step is psi^{n-1}. */
+int oracle_be_run(const oracle_problem *p, int32_t method, int32_t n_steps, double tol, int32_t max_iter,
+                  int32_t commit_unconverged, double *psi, double *phi_steps, int32_t *iters, double *resid,
+                  int32_t n_threads)
+{
+    const int J = p->n_cells, N = p->n_ord;
+    if (J < 1 || N < 2 || (N & 1) || max_iter < 1) return 1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    const size_t npsi = (size_t)J * N * 2;
+    double *pa = malloc(sizeof(double) * npsi), *pb = malloc(sizeof(double) * npsi);
+    double *fa = malloc(sizeof(double) * (size_t)J * 2), *fb = malloc(sizeof(double) * (size_t)J * 2);
+    double *mu = malloc(sizeof(double) * N), *w = malloc(sizeof(double) * N);
+    if (!pa || !pb || !fa || !fb || !mu || !w) {
+        free(pa); free(pb); free(fa); free(fb); free(mu); free(w);
+        return 2;
+    }
+    oracle_gauss_legendre(N, mu, w);
+    int status = 0;
+    for (int step = 0; step < n_steps && status == 0; ++step) {
+        memcpy(pa, psi, sizeof(double) * npsi);
+        for (int j = 0; j < J; ++j)
+            for (int i = 0; i < 2; ++i) {
+                double sum = 0.0;
+                for (int n = 0; n < N; ++n) sum += w[n] * pa[ix_be(j, n, i, N)];
+                fa[(size_t)j * 2 + i] = sum;
+            }
+        double *pc = pa, *pn = pb, *fc = fa, *fn = fb;
+        int it = 0, conv = 0;
+        double d = INFINITY;
+        while (it < max_iter) {
+            int e = method == ORC_OCI ? oracle_be_oci_iteration(p, psi, pc, pn, fn)
+                                      : oracle_be_si_iteration(p, psi, fc, pc, pn, fn);
+            if (e) { status = e; break; }
+            ++it;
+            d = rel_change(J * 2, fn, fc);
+            double *t = pc; pc = pn; pn = t;
+            t = fc; fc = fn; fn = t;
+            if (!(d == d)) { status = 5; break; }
+            if (d < tol) { conv = 1; break; }
+        }
+        if (iters) iters[step] = it;
+        if (resid) resid[step] = d;
+        if (status) break;
+        if (!conv && !commit_unconverged) { status = 4; break; }
+        memcpy(psi, pc, sizeof(double) * npsi);
+        if (phi_steps) memcpy(phi_steps + (size_t)step * J * 2, fc, sizeof(double) * (size_t)J * 2);
+    }
+    free(pa); free(pb); free(fa); free(fb); free(mu); free(w);
     return status;
 }
 

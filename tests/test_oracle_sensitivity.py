@@ -86,3 +86,46 @@ def test_unmutated_copy_passes(tmp_path):
 def test_mutant_is_caught(tmp_path, name):
     lib = _build_mutant(tmp_path, name)
     assert _pins_fail(lib), f"planted mistake {name} passed every pin"
+
+
+# Planted mistakes in the backward-Euler part, caught by the BE pins (the
+# whole-problem BE solve from the balance equations).
+BE_MUTANTS = {
+    # 1/(v dt) left out of Sigma_hat
+    "be_sigma_hat": ("assemble_B_m(mu[m], dx, sig_hat, b);", "assemble_B_m(mu[m], dx, st, b);"),
+    # previous-step source with the full-cell factor dx/(v dt)
+    "be_edge_factor": ("const double e = dx / (2.0 * p->v * p->dt);\n    const double *Q = p->q + (size_t)j * 4;\n    c2[0]",
+                       "const double e = dx / (p->v * p->dt);\n    const double *Q = p->q + (size_t)j * 4;\n    c2[0]"),
+    # SI: outgoing corner of a mu < 0 cell taken from the wrong side
+    "be_si_outgoing": ("in = mu[m] > 0.0 ? c2[1] : c2[0];  /* outgoing corner */",
+                       "in = mu[m] > 0.0 ? c2[1] : c2[1];  /* outgoing corner */"),
+}
+
+
+def _be_pins_fail(lib):
+    for bcl, bcr in (("reflect", "incident"), ("incident", "reflect")):
+        p = workloads.random_small(seed=78, J=5, N=4, bc_left=bcl, bc_right=bcr)
+        _, ph_b = brute.be_run(p, 2, psi0=np.asarray(p["psi0"]).reshape(5, 4, 2))
+        for method in ("oci", "si"):
+            r = oracle.run_be(p, method, 2, tol=1e-13, max_iter=5000, lib=lib)
+            if r["status"] != 0 or np.abs(r["phi_steps"] - ph_b).max() > 1e-9 * np.abs(ph_b).max():
+                return True
+    return False
+
+
+def test_unmutated_copy_passes_be_pins(tmp_path):
+    path = tmp_path / "same_be.c"
+    path.write_text(open(SRC).read())
+    lib = oracle.load_library(obuild.build(force=True, src=str(path), out=str(tmp_path / "libsame_be.so")))
+    assert not _be_pins_fail(lib)
+
+
+@pytest.mark.parametrize("name", sorted(BE_MUTANTS))
+def test_be_mutant_is_caught(tmp_path, name):
+    old, new = BE_MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    lib = oracle.load_library(obuild.build(force=True, src=str(path), out=str(tmp_path / f"lib{name}.so")))
+    assert _be_pins_fail(lib), f"planted mistake {name} passed every BE pin"
