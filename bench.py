@@ -228,18 +228,22 @@ def run_ours(args, rank, world):
 
 
 def run_compare(args, pkg, torch, stream):
-    """SI (the paper's sequential sweep, and the parallel-prefix sweep) and FP64
-    OCI on the same problem (fewer steps), for context."""
+    """SI (the paper's sequential sweep, and the parallel-prefix sweep), FP64 OCI
+    and the backward-Euler time scheme on the same problem (fewer steps), for
+    context."""
     out = {}
     prob, _ = make_problem(args)
     J, N = prob["n_cells"], prob["n_ord"]
-    for name, method, prec, sweep in (("si_" + args.precision, "si", args.precision, "march"),
-                                      ("si_scan_" + args.precision, "si", args.precision, "scan"),
-                                      ("oci_fp64", "oci", "fp64", "march"), ("si_fp64", "si", "fp64", "march"),
-                                      ("si_scan_fp64", "si", "fp64", "scan")):
-        if prec == args.precision and method == "oci":
+    for name, method, prec, sweep, scheme in (("si_" + args.precision, "si", args.precision, "march", "mb"),
+                                              ("si_scan_" + args.precision, "si", args.precision, "scan", "mb"),
+                                              ("oci_fp64", "oci", "fp64", "march", "mb"),
+                                              ("si_fp64", "si", "fp64", "march", "mb"),
+                                              ("si_scan_fp64", "si", "fp64", "scan", "mb"),
+                                              ("oci_backward_euler_fp32", "oci", "fp32", "march", "be"),
+                                              ("oci_backward_euler_fp64", "oci", "fp64", "march", "be")):
+        if prec == args.precision and method == "oci" and scheme == "mb":
             continue
-        s = pkg.Solver(prob, precision=prec, tol=prob["tol"], stream=stream.cuda_stream, sweep=sweep)
+        s = pkg.Solver(prob, precision=prec, tol=prob["tol"], stream=stream.cuda_stream, sweep=sweep, scheme=scheme)
         n_w, n_t = 2, min(args.steps, 5)
         its, secs = [], []
         ok = True

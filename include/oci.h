@@ -154,6 +154,21 @@ int oci_set_solver(oci_handle *h, int32_t solver);
 enum { OCI_SWEEP_MARCH = 0, OCI_SWEEP_SCAN = 1 };
 int oci_set_sweep(oci_handle *h, int32_t sweep);
 
+/* Time discretisation of oci_step.  OCI_TIME_MB (default): multiple balance,
+ * two time moments per corner (the paper's scheme).  OCI_TIME_BE: backward
+ * Euler (the paper's disabled section "Backward Euler transient
+ * implementation"): one time level per step, total cross section
+ * Sigma + 1/(v dt), the previous step's angular flux as a source
+ * psi^{n-1}/(v dt); the SCB cell is the same, so the cell system is 2N x 2N and
+ * its Woodbury capacitance a scalar.  The source at the new time is Q_{k+1/2}
+ * and prescribed incident data its k+1/2 value; oci_fluxes returns the moments
+ * (L, R) twice; the state (psi at the end of the last step) carries over when
+ * switching.  OCI iteration only (si_step returns OCI_EINVAL under BE); no
+ * learned guess, dense solver or FP32 refinement on this path.  OCI_EINVAL for
+ * an unknown scheme or a singular capacitance, OCI_ENOMEM, OCI_ECUDA. */
+enum { OCI_TIME_MB = 0, OCI_TIME_BE = 1 };
+int oci_set_time_scheme(oci_handle *h, int32_t scheme);
+
 /* Diagnostics of the bounded waits (the paper has no counterpart).  The
  * persistent FP32 iteration meets the other blocks at a grid barrier once per
  * iteration; every wait there gives up after poll_limit polls (0: the default,

@@ -21,6 +21,8 @@ OCI_BC_VACUUM, OCI_BC_REFLECT, OCI_BC_INCIDENT = 0, 1, 2
 OCI_FP64, OCI_FP32 = 0, 1
 OCI_SOLVER_WOODBURY, OCI_SOLVER_DENSE = 0, 1
 OCI_SWEEP_MARCH, OCI_SWEEP_SCAN = 0, 1
+OCI_TIME_MB, OCI_TIME_BE = 0, 1
+_SCHEME = {"mb": OCI_TIME_MB, "be": OCI_TIME_BE}
 _SWEEP = {"march": OCI_SWEEP_MARCH, "scan": OCI_SWEEP_SCAN}
 _SOLVER = {"woodbury": OCI_SOLVER_WOODBURY, "dense": OCI_SOLVER_DENSE}
 _BC = {"vacuum": OCI_BC_VACUUM, "reflect": OCI_BC_REFLECT, "reflecting": OCI_BC_REFLECT,
@@ -62,6 +64,7 @@ SIGNATURES = {
     "oci_set_stream": (ctypes.c_int, [_VP, _VP]),
     "oci_set_solver": (ctypes.c_int, [_VP, _I32]),
     "oci_set_sweep": (ctypes.c_int, [_VP, _I32]),
+    "oci_set_time_scheme": (ctypes.c_int, [_VP, _I32]),
     "oci_set_wait_limits": (ctypes.c_int, [_VP, ctypes.c_uint32, _I32]),
     "oci_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
     "si_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
@@ -208,6 +211,12 @@ def oci_set_wait_limits(h, poll_limit=0, barrier_shortfall=0):
     _check(load_library().oci_set_wait_limits(h, int(poll_limit), int(barrier_shortfall)), "oci_set_wait_limits", h)
 
 
+def oci_set_time_scheme(h, scheme):
+    """OCI_TIME_MB (default) or OCI_TIME_BE (see oci.h); also "mb" / "be"."""
+    scheme = _SCHEME.get(scheme, scheme)
+    _check(load_library().oci_set_time_scheme(h, int(scheme)), "oci_set_time_scheme", h)
+
+
 def oci_step(h):
     """One OCI time step; returns (status, stats dict).  Raises only on
     OCI_EINVAL / OCI_ECUDA; convergence failures come back as the status."""
@@ -268,7 +277,7 @@ class Solver:
     """Owns one handle.  ``step()`` / ``si_step()`` advance one time step."""
 
     def __init__(self, prob, precision="fp64", tol=None, max_iter=100000, stream=None, solver="woodbury",
-                 sweep="march"):
+                 sweep="march", scheme="mb"):
         self.prob = prob
         self.h = oci_create(prob, precision, tol, max_iter, stream)
         try:
@@ -276,6 +285,8 @@ class Solver:
                 oci_set_solver(self.h, solver)
             if sweep != "march":
                 oci_set_sweep(self.h, sweep)
+            if scheme != "mb":
+                oci_set_time_scheme(self.h, scheme)
         except Exception:
             self.close()
             raise

@@ -131,6 +131,13 @@ struct oci_handle {
     std::vector<double> q_host;      // sources (for the network's inputs; valid while q_host_valid)
     bool q_host_valid = false;
     double *q_dev = nullptr, *dx_dev = nullptr;  // FP64 source moments [J][4] and cell widths [J]
+    // backward-Euler time scheme (oci_set_time_scheme)
+    int scheme = OCI_TIME_MB;
+    void *be_mem = nullptr;          // 1/t per material and pair (storage precision), K per material (FP64)
+    void *be_tab = nullptr;
+    double *be_K = nullptr;
+    cudaGraph_t graph_be = nullptr;
+    cudaGraphExec_t exec_be = nullptr;
     std::vector<double> bc_left_host, bc_right_host;  // prescribed incident data
     // FP32 refinement (stalled steps): FP64 tables, saved halo, residual, phi(h0)
     double *ref_tab = nullptr, *ref_par = nullptr, *ref_muw = nullptr;
@@ -863,6 +870,76 @@ int dense_step(oci_handle *h, IterState *s)
     return OCI_OK;
 }
 
+// Backward-Euler tables: 1/t per material and pair, t = a - i mu/2,
+// a = (mu + dx Sigma)/2 + dx/(2 v dt); scalar capacitance K = 1/(1 - s m),
+// m = sum_p 2 w_p Re(1/t).
+int be_setup(oci_handle *h)
+{
+    const int P = h->P, nm = (int)h->mats.size();
+    std::vector<double> tab((size_t)nm * P * 2), K(nm);
+    for (int m = 0; m < nm; ++m) {
+        const Material &mt = h->mats[m];
+        const double e = std::isinf(h->v) ? 0.0 : mt.dx / (2.0 * h->v * h->dt);
+        const double s = mt.dx * mt.ss / 4.0;
+        double msum = 0.0;
+        for (int p = 0; p < P; ++p) {
+            const double mu = h->mu[P + p];
+            const std::complex<double> it = 1.0 / std::complex<double>((mu + mt.dx * mt.st) / 2.0 + e, -mu / 2.0);
+            tab[((size_t)m * P + p) * 2] = it.real();
+            tab[((size_t)m * P + p) * 2 + 1] = it.imag();
+            msum += 2.0 * h->w[P + p] * it.real();
+        }
+        const double den = 1.0 - s * msum;
+        if (!(std::fabs(den) > 0.0) || !std::isfinite(den)) return OCI_EINVAL;
+        K[m] = 1.0 / den;
+    }
+    const size_t rs = rsize(h), tb = ((size_t)nm * P * 2 * rs + 255) & ~(size_t)255;
+    if (cudaMalloc(&h->be_mem, tb + (size_t)nm * 8) != cudaSuccess) {
+        h->be_mem = nullptr;
+        return OCI_ENOMEM;
+    }
+    h->be_tab = h->be_mem;
+    h->be_K = (double *)((char *)h->be_mem + tb);
+    int rc = upload_real(h, h->be_tab, tab);
+    if (rc) return rc;
+    CK(h, cudaMemcpy(h->be_K, K.data(), sizeof(double) * nm, cudaMemcpyHostToDevice));
+    return OCI_OK;
+}
+
+// BE step graph: begin -> WHILE { be_cells } -> be_commit.
+template <typename R>
+int build_be_graph(oci_handle *h)
+{
+    cudaGraph_t g;
+    CK(h, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle cond;
+    CK(h, cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
+    KParams<R> plain = make_params<R>(h, 0, 0);
+    KParams<R> loop = make_params<R>(h, 1, cond);
+    ocik::BeArgs<R> be{(const r2<R> *)h->be_tab, h->be_K};
+    void *a_plain[] = {&plain, &be};
+    void *a_loop[] = {&loop, &be};
+    IterState *st = h->d_st;
+    void *a_st[] = {&st};
+    const int grid = std::max(1, std::min((h->J + 7) / 8, h->grid_cells));
+    cudaGraphNode_t n_begin, n_while, n_commit, b_cells;
+    int rc = add_kernel(h, g, &n_begin, nullptr, 0, (const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st);
+    if (rc) return rc;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CK(h, cudaGraphAddNode(&n_while, g, &n_begin, nullptr, 1, &cp));
+    rc = add_kernel(h, cp.conditional.phGraph_out[0], &b_cells, nullptr, 0, h->ks.be_cells, dim3(grid), dim3(kBlock),
+                    a_loop);
+    if (!rc) rc = add_kernel(h, g, &n_commit, &n_while, 1, h->ks.be_commit, dim3(grid), dim3(kBlock), a_plain);
+    if (rc) return rc;
+    CK(h, cudaGraphInstantiate(&h->exec_be, g, 0));
+    h->graph_be = g;
+    return OCI_OK;
+}
+
 int map_status(int s)
 {
     switch (s) {
@@ -886,7 +963,7 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         if (rc) return rc;
         ++launches;
     }
-    const bool nn = !si && h->nn_mode != OCI_NN_OFF;
+    const bool nn = !si && h->nn_mode != OCI_NN_OFF && h->scheme == OCI_TIME_MB;
     int accepts = 0, rejects = 0;
     const int unroll = (h->staged && h->pdl_graph) ? kUnroll : 1;  // iteration launches per WHILE body
     auto body_launches = [&](int iters) { return unroll * ((iters + unroll - 1) / unroll); };
@@ -900,7 +977,19 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         launches += 10;  // scale, features, weight rounding, 5 layers, predict, lift
     }
     IterState s{};
-    if (!si && h->solver == OCI_SOLVER_DENSE) {
+    if (h->scheme == OCI_TIME_BE) {
+        if (si) return OCI_EINVAL;
+        if (!h->exec_be) {
+            rc = h->prec == OCI_FP64 ? build_be_graph<double>(h) : build_be_graph<float>(h);
+            if (rc) return rc;
+        }
+        IterConfig c = h->cfg;
+        c.stall_floor = 0.0;
+        c.pause_at = -1;
+        if ((rc = set_device_cfg(h, c))) return rc;
+        CK(h, cudaGraphLaunch(h->exec_be, h->stream));
+        ++graph_runs;
+    } else if (!si && h->solver == OCI_SOLVER_DENSE) {
         if ((rc = dense_step(h, &s))) return rc;
     } else if (nn && h->nn_mode == OCI_NN_GUESS_CORRECT) {
         if (!h->exec_cont) {
@@ -954,12 +1043,13 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
     CK(h, cudaEventRecord(h->ev1, h->stream));
     if ((rc = read_state(h, &s))) return rc;  // the step's one synchronisation in the common case
     const int main_iters = s.iter;
-    if (!si && h->solver == OCI_SOLVER_DENSE) launches += 2 + 2 * main_iters;  // begin, rhs + out per iteration, commit
+    if (h->scheme == OCI_TIME_BE) launches += 2 + main_iters;  // begin, iterations, commit
+    else if (!si && h->solver == OCI_SOLVER_DENSE) launches += 2 + 2 * main_iters;  // begin, rhs + out per iteration, commit
     else if (si) launches += 3 + main_iters * (h->sweep == OCI_SWEEP_SCAN ? 4 : 2);  // begin, prep, sweep + cells, commit
     else if (h->use_loop) launches += 1 + 2 * graph_runs + corrections;  // begin, (loop, commit) per graph run, lifts
     else launches += 2 + body_launches(main_iters) + corrections * (unroll + 1);  // begin, bodies, commit, lifts
     int refined = 0;
-    if (s.status == ocik::ST_STALL && !si && h->cells_lin && h->ks.refine) {
+    if (s.status == ocik::ST_STALL && !si && h->scheme == OCI_TIME_MB && h->cells_lin && h->ks.refine) {
         if ((rc = refine_step(h, &s))) return rc;
         refined = 1;
         launches += 2 + (s.iter - main_iters);  // residual pass, setup, correction iterations, commit
@@ -1237,6 +1327,9 @@ void oci_destroy(oci_handle *h)
     if (h->nn_mem) cudaFree(h->nn_mem);
     dense_free(h);
     if (h->scan_mem) cudaFree(h->scan_mem);
+    if (h->exec_be) cudaGraphExecDestroy(h->exec_be);
+    if (h->graph_be) cudaGraphDestroy(h->graph_be);
+    if (h->be_mem) cudaFree(h->be_mem);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->h_st) cudaFreeHost(h->h_st);
@@ -1274,6 +1367,23 @@ int oci_set_wait_limits(oci_handle *h, uint32_t poll_limit, int32_t barrier_shor
     if (!h || barrier_shortfall < 0) return OCI_EINVAL;
     h->cfg.bar_poll_limit = poll_limit;
     h->cfg.bar_shortfall = barrier_shortfall;
+    return OCI_OK;
+}
+
+int oci_set_time_scheme(oci_handle *h, int32_t scheme)
+{
+    if (!h || (scheme != OCI_TIME_MB && scheme != OCI_TIME_BE)) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    if (scheme == OCI_TIME_BE && !h->be_mem) {
+        const int rc = be_setup(h);
+        if (rc) {
+            if (h->be_mem) cudaFree(h->be_mem);
+            h->be_mem = nullptr;
+            return rc;
+        }
+    }
+    if (scheme != h->scheme) h->guess_valid = false;  // faces rebuilt from the committed state
+    h->scheme = scheme;
     return OCI_OK;
 }
 

@@ -2,6 +2,7 @@
 // instantiations for a given (lanes per cell, pairs per lane) layout.
 #pragma once
 #include "oci_device.cuh"
+#include "oci_be.cuh"
 
 namespace ocik {
 
@@ -14,6 +15,7 @@ struct KernelSet {
     const void *guess;       // k_percell<C_GUESS>
     const void *march;       // k_si_march
     const void *scan_reduce, *scan_segments, *scan_apply;  // parallel-prefix SI sweep
+    const void *be_cells, *be_commit;                      // backward-Euler iteration and commit
     const void *lift_guess;  // k_lift<LIFT_GUESS>
     const void *lift_corr;   // k_lift<LIFT_CORR>
     const void *cells_oci_tma;  // k_cells_tma<M_OCI> (FP32, even P) or nullptr

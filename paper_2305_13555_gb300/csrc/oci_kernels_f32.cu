@@ -20,6 +20,8 @@ static void fill(KernelSet *k)
     k->scan_reduce = (const void *)&k_scan_reduce<float>;
     k->scan_segments = (const void *)&k_scan_segments<float>;
     k->scan_apply = (const void *)&k_scan_apply<float>;
+    k->be_cells = (const void *)&k_be_cells<float>;
+    k->be_commit = (const void *)&k_be_commit<float>;
     k->lift_guess = (const void *)&k_lift<float, LPC, PPL, LIFT_GUESS>;
     k->lift_corr = (const void *)&k_lift<float, LPC, PPL, LIFT_CORR>;
     k->cells_oci_tma = nullptr;

@@ -16,6 +16,8 @@ static void fill(KernelSet *k)
     k->scan_reduce = (const void *)&k_scan_reduce<double>;
     k->scan_segments = (const void *)&k_scan_segments<double>;
     k->scan_apply = (const void *)&k_scan_apply<double>;
+    k->be_cells = (const void *)&k_be_cells<double>;
+    k->be_commit = (const void *)&k_be_commit<double>;
     k->lift_guess = (const void *)&k_lift<double, LPC, PPL, LIFT_GUESS>;
     k->lift_corr = (const void *)&k_lift<double, LPC, PPL, LIFT_CORR>;
     k->cells_oci_tma = nullptr;
