@@ -136,6 +136,7 @@ struct oci_handle {
     void *be_mem = nullptr;          // 1/t per material and pair (storage precision), K per material (FP64)
     void *be_tab = nullptr;
     double *be_K = nullptr;
+    float2 *be_Kf = nullptr;
     cudaGraph_t graph_be = nullptr;
     cudaGraphExec_t exec_be = nullptr;
     std::vector<double> bc_left_host, bc_right_host;  // prescribed incident data
@@ -894,15 +895,23 @@ int be_setup(oci_handle *h)
         K[m] = 1.0 / den;
     }
     const size_t rs = rsize(h), tb = ((size_t)nm * P * 2 * rs + 255) & ~(size_t)255;
-    if (cudaMalloc(&h->be_mem, tb + (size_t)nm * 8) != cudaSuccess) {
+    const size_t kb = ((size_t)nm * 8 + 255) & ~(size_t)255;
+    if (cudaMalloc(&h->be_mem, tb + kb + (size_t)nm * 8) != cudaSuccess) {
         h->be_mem = nullptr;
         return OCI_ENOMEM;
     }
     h->be_tab = h->be_mem;
     h->be_K = (double *)((char *)h->be_mem + tb);
+    h->be_Kf = (float2 *)((char *)h->be_mem + tb + kb);
+    std::vector<float> kf((size_t)nm * 2);
+    for (int m = 0; m < nm; ++m) {
+        kf[2 * m] = (float)K[m];
+        kf[2 * m + 1] = (float)(K[m] - (double)kf[2 * m]);
+    }
     int rc = upload_real(h, h->be_tab, tab);
     if (rc) return rc;
     CK(h, cudaMemcpy(h->be_K, K.data(), sizeof(double) * nm, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->be_Kf, kf.data(), sizeof(float) * kf.size(), cudaMemcpyHostToDevice));
     return OCI_OK;
 }
 
@@ -916,7 +925,7 @@ int build_be_graph(oci_handle *h)
     CK(h, cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault));
     KParams<R> plain = make_params<R>(h, 0, 0);
     KParams<R> loop = make_params<R>(h, 1, cond);
-    ocik::BeArgs<R> be{(const r2<R> *)h->be_tab, h->be_K};
+    ocik::BeArgs<R> be{(const r2<R> *)h->be_tab, h->be_K, h->be_Kf};
     void *a_plain[] = {&plain, &be};
     void *a_loop[] = {&loop, &be};
     IterState *st = h->d_st;

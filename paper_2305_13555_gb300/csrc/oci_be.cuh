@@ -20,6 +20,7 @@ template <typename R>
 struct BeArgs {
     const r2<R> *tab;   // [n_mat][P]: 1/t (re, im)
     const double *K;    // [n_mat] scalar capacitance
+    const float2 *Kf;   // [n_mat] the same as a double-float pair (FP32 path)
 };
 
 // One BE OCI iteration; one warp per cell, lanes over ordinate pairs.
@@ -38,11 +39,14 @@ __global__ void __launch_bounds__(256) k_be_cells(const KParams<R> p, const BeAr
     const bool refl_l = p.bc_left == BC_REFLECT, refl_r = p.bc_right == BC_REFLECT;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     double d2 = 0.0, p2 = 0.0;
+    float df2 = 0.f, pf2 = 0.f;  // FP32 path: per-thread partials in float, grid sums in double
     for (int cell = gw; cell < J; cell += nw) {
         const int m = p.mat[cell];
         const r4<R> qd = p.cellq[cell];
         const r2<R> es = p.matpar[m];
-        double rL = 0.0, rR = 0.0;
+        // moment partials: double in FP64 mode; in FP32 mode float pairs summed
+        // error-free across the warp (the FP64 pipe is slow on this GPU)
+        R rLr = 0, rRr = 0;
         for (int pp = lane; pp < P; pp += 32) {
             const r2<R> mw = p.muw[pp];
             const r2<R> it = be.tab[(size_t)m * P + pp];
@@ -54,18 +58,39 @@ __global__ void __launch_bounds__(256) k_be_cells(const KParams<R> p, const BeAr
             const R vr = qd.z + es.x * pe.z, vi = -(qd.w + es.x * pe.w + mw.x * inM);
             const R yr = ur * it.x - ui * it.y, yi = ur * it.y + ui * it.x;
             const R zr = vr * it.x - vi * it.y, zi = vr * it.y + vi * it.x;
-            rL += (double)(mw.y * (yr + zr));
-            rR += (double)(mw.y * (yi - zi));
+            rLr += mw.y * (yr + zr);
+            rRr += mw.y * (yi - zi);
         }
+        // phi = K r (double in FP64 mode, double-float in FP32 mode)
+        double fL = 0.0, fR = 0.0;
+        ff fLf{0.f, 0.f}, fRf{0.f, 0.f};
+        R sL, sR;
+        if constexpr (sizeof(R) == 8) {
+            double rL = rLr, rR = rRr;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            rL += __shfl_xor_sync(FULL, rL, o);
-            rR += __shfl_xor_sync(FULL, rR, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                rL += __shfl_xor_sync(FULL, rL, o);
+                rR += __shfl_xor_sync(FULL, rR, o);
+            }
+            const double K = be.K[m];
+            fL = K * rL;
+            fR = K * rR;
+            sL = (R)(es.y * fL);
+            sR = (R)(es.y * fR);
+        } else {
+            ff aL{(float)rLr, 0.f}, aR{(float)rRr, 0.f};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                aL = ff_add(aL, ff{__shfl_xor_sync(FULL, aL.h, o), __shfl_xor_sync(FULL, aL.l, o)});
+                aR = ff_add(aR, ff{__shfl_xor_sync(FULL, aR.h, o), __shfl_xor_sync(FULL, aR.l, o)});
+            }
+            const float2 K = be.Kf[m];
+            fLf = ff_mul(ff{K.x, K.y}, aL);
+            fRf = ff_mul(ff{K.x, K.y}, aR);
+            sL = (R)(es.y * __fadd_rn(fLf.h, fLf.l));
+            sR = (R)(es.y * __fadd_rn(fRf.h, fRf.l));
         }
-        const double K = be.K[m];
-        const double fL = K * rL, fR = K * rR;
         // outgoing corners: +mu R = Im(y + s phi/t), -mu L = Re(z + s conj(phi)/t)
-        const R sL = (R)(es.y * fL), sR = (R)(es.y * fR);
         for (int pp = lane; pp < P; pp += 32) {
             const r2<R> mw = p.muw[pp];
             const r2<R> it = be.tab[(size_t)m * P + pp];
@@ -81,16 +106,27 @@ __global__ void __launch_bounds__(256) k_be_cells(const KParams<R> p, const BeAr
             fMw[(size_t)cell * P + pp] = r2<R>{outM, outM};
         }
         if (lane < 4) {
-            const double f = (lane & 1) ? fR : fL;
-            if (lane < 2) {
-                const double d = f - PhiStore<R>::wide(phr[4 * (size_t)cell + lane]);
-                d2 += d * d;
-                p2 += f * f;
+            if constexpr (sizeof(R) == 8) {
+                const double f = (lane & 1) ? fR : fL;
+                if (lane < 2) {
+                    const double d = f - PhiStore<R>::wide(phr[4 * (size_t)cell + lane]);
+                    d2 += d * d;
+                    p2 += f * f;
+                }
+                phw[4 * (size_t)cell + lane] = phi_from_double<R>(f);
+            } else {
+                const ff f = (lane & 1) ? fRf : fLf;
+                if (lane < 2) {
+                    const float2 old = phr[4 * (size_t)cell + lane];
+                    const float d = ff_diff(f, ff{old.x, old.y});
+                    df2 = __fmaf_rn(d, d, df2);
+                    pf2 = __fmaf_rn(f.h, f.h, pf2);
+                }
+                phw[4 * (size_t)cell + lane] = make_float2(f.h, f.l);
             }
-            phw[4 * (size_t)cell + lane] = phi_from_double<R>(f);
         }
     }
-    finalize_iteration(d2, p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond);
+    finalize_iteration(d2 + (double)df2, p2 + (double)pf2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond);
 }
 
 // End of a BE step: if accepted, psi^n of every ordinate and corner from the
