@@ -4,6 +4,7 @@
 // the handle; each time step is one CUDA graph launch whose iteration loop is a
 // device-side conditional WHILE node, so the host synchronises once per step.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -960,9 +961,16 @@ int map_status(int s)
     }
 }
 
+// NVTX range around one time step (visible in Nsight timelines; no cost without a tool).
+struct StepRange {
+    explicit StepRange(const char *name) { nvtxRangePushA(name); }
+    ~StepRange() { nvtxRangePop(); }
+};
+
 int run_step(oci_handle *h, bool si, oci_stats *st)
 {
     if (!h) return OCI_EINVAL;
+    const StepRange range(si ? "si_step" : (h->scheme == OCI_TIME_BE ? "oci_step (backward Euler)" : "oci_step"));
     CK(h, cudaSetDevice(h->device));
     int rc = ensure_graphs(h);
     if (rc) return rc;

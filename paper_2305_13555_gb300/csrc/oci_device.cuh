@@ -1774,6 +1774,7 @@ struct ScanShared {
     r2<R> g[SCAN_SEG];
     int mat[SCAN_SEG];
     Aff<R> warp_tot[SCAN_T / 32];
+    Aff<R> block_tot;
 };
 
 // Stage the segment's offsets and materials, compose each thread's 8 cells
@@ -1817,15 +1818,26 @@ __device__ Aff<R> scan_segment(const KParams<R> &p, ScanShared<R> &sh, int ch, i
     }
     if (lane == 31) sh.warp_tot[warp] = I;
     __syncthreads();
-    Aff<R> W = aff_id<R>();  // maps of the earlier warps
-    for (int w = 0; w < warp; ++w) W = aff_then(W, sh.warp_tot[w]);
+    // warp 0 scans the warp totals; slot w then holds the maps of warps 0..w-1
+    constexpr int NW = SCAN_T / 32;
+    if (warp == 0) {
+        Aff<R> T = lane < NW ? sh.warp_tot[lane] : aff_id<R>();
+#pragma unroll
+        for (int d = 1; d < NW; d <<= 1) {
+            const Aff<R> e = aff_shfl_up(T, d);
+            if (lane >= d) T = aff_then(e, T);
+        }
+        Aff<R> X = aff_shfl_up(T, 1);
+        if (lane == 0) X = aff_id<R>();
+        __syncwarp();
+        if (lane < NW) sh.warp_tot[lane] = X;
+        if (lane == NW - 1) sh.block_tot = T;
+    }
+    __syncthreads();
+    const Aff<R> W = sh.warp_tot[warp];  // maps of the earlier warps
     Aff<R> E = aff_shfl_up(I, 1);  // exclusive within the warp
     if (lane == 0) E = aff_id<R>();
-    if (total) {
-        Aff<R> T = aff_id<R>();
-        for (int w = 0; w < SCAN_T / 32; ++w) T = aff_then(T, sh.warp_tot[w]);
-        *total = T;
-    }
+    if (total) *total = sh.block_tot;
     return aff_then(W, E);
 }
 
