@@ -258,10 +258,13 @@ def run_compare(args, pkg, torch, stream):
             if k >= n_w:
                 its.append(st["iters"])
                 secs.append(st["seconds"])
+        t_it = pkg.oci_profile_iterations(s.h, 20) if (ok and method == "oci") else None
         s.close()
         if ok:
             out[name] = {"updates_per_s": J * N * sum(its) / sum(secs), "s_per_step": sum(secs) / len(secs),
                          "iters_per_step": sum(its) / len(its)}
+            if t_it is not None:
+                out[name]["s_per_iteration"] = t_it
     return out
 
 

@@ -227,7 +227,8 @@ int oci_set_state(oci_handle *h, const double *psi_edge);
  * and return the mean device time per iteration in *seconds_per_launch.  The
  * staged FP32 path runs them as one cooperative launch of its persistent loop
  * (as inside a step); other paths as one stream launch per iteration.  With
- * OCI_SOLVER_DENSE an iteration is right-hand sides, GEMMs and outputs.  The
+ * OCI_SOLVER_DENSE an iteration is right-hand sides, GEMMs and outputs; under
+ * OCI_TIME_BE it is the backward-Euler iteration kernel.  The
  * committed state (psi_{k-1/2}, published phi) is untouched and the next step
  * restarts from it.  Used by the benchmark's roofline figure. */
 int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_launch);

@@ -1520,6 +1520,27 @@ int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_la
     IterState *st = h->d_st;
     void *a_st[] = {&st};
     CK(h, cudaLaunchKernel((const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st, 0, h->stream));
+    if (h->scheme == OCI_TIME_BE) {
+        // the backward-Euler iteration kernel as plain launches
+        const int grid = std::max(1, std::min((h->J + 7) / 8, h->grid_cells));
+        KParams<double> bd = make_params<double>(h, 0, 0);
+        KParams<float> bf = make_params<float>(h, 0, 0);
+        ocik::BeArgs<double> ad{(const r2<double> *)h->be_tab, h->be_K, h->be_Kf};
+        ocik::BeArgs<float> af{(const r2<float> *)h->be_tab, h->be_K, h->be_Kf};
+        void *ba[] = {h->prec == OCI_FP64 ? (void *)&bd : (void *)&bf, h->prec == OCI_FP64 ? (void *)&ad : (void *)&af};
+        for (int i = -2; i < n_iter; ++i) {
+            if (i == 0) CK(h, cudaEventRecord(h->ev0, h->stream));
+            CK(h, cudaLaunchKernel(h->ks.be_cells, dim3(grid), dim3(kBlock), ba, 0, h->stream));
+        }
+        CK(h, cudaEventRecord(h->ev1, h->stream));
+        CK(h, cudaEventSynchronize(h->ev1));
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        *seconds_per_launch = ms * 1e-3 / n_iter;
+        if ((rc = set_device_cfg(h, h->cfg))) return rc;
+        h->guess_valid = false;
+        return OCI_OK;
+    }
     if (h->use_loop && h->solver == OCI_SOLVER_WOODBURY) {
         // the persistent loop: one cooperative launch runs a fixed number of iterations
         auto prepare = [&]() -> int {
