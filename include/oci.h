@@ -113,7 +113,11 @@ int oci_create(const oci_problem *p, oci_handle **out);
 void oci_destroy(oci_handle *h);
 
 /* Replace the source moments used from the next step on (Q_k and Q_{k+1/2}
- * of Eqs. scb-mb-a..d): host [J][4].  OCI_EINVAL on NULL. */
+ * of Eqs. scb-mb-a..d): host [J][4].  The copy is enqueued on the handle's
+ * stream: from pageable memory q may be reused when the call returns; from
+ * page-locked (pinned) memory the copy is asynchronous, so keep q unchanged
+ * until the next call that synchronises (oci_step, si_step, oci_fluxes).
+ * OCI_EINVAL on NULL. */
 int oci_set_source(oci_handle *h, const double *q);
 
 /* Iteration controls: tolerance (>= 0; 0 iterates to max_iter), iteration cap

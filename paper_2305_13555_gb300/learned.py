@@ -164,12 +164,21 @@ def main():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed0", type=int, default=100000)
+    ap.add_argument("--family", default="config4", choices=["config4", "thin"],
+                    help="training slabs: the config-4 family (default) or thin, strongly scattering "
+                         "cells like the deployment slabs")
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     a = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
     t0 = time.time()
-    data = trajectories(range(a.seed0, a.seed0 + a.trajectories), J=a.cells, N=a.ordinates, n_steps=a.steps)
+    problem = None
+    if a.family == "thin":
+        import workloads
+        problem = (lambda sd: workloads.hetero(sd, J=a.cells, N=a.ordinates, n_steps=a.steps, dt=0.02,
+                                               tau_range=(0.01, 0.1), c_range=(0.9, 0.999)))
+    data = trajectories(range(a.seed0, a.seed0 + a.trajectories), J=a.cells, N=a.ordinates, n_steps=a.steps,
+                        problem=problem)
     print(f"generated {a.trajectories} trajectories x {a.steps} steps in {time.time() - t0:.1f} s; "
           f"mean OCI iterations per step {data['iters'].mean():.1f}", flush=True)
     params, hist = train(data, epochs=a.epochs, batch=a.batch, lr=a.lr)

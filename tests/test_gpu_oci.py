@@ -318,3 +318,23 @@ def test_grid_barrier_wait_runs_out_and_the_device_recovers():
             rc2, st2 = ref.step()
             assert rc == rc2 == pkg.OCI_OK and st["iters"] == st2["iters"], (st, st2)
             assert np.array_equal(s.fluxes(), ref.fluxes())
+
+
+def test_persistent_loop_matches_one_launch_per_iteration(monkeypatch):
+    """The FP32 persistent cooperative loop and the same kernel launched once per
+    iteration (OCI_NO_LOOP) take the same iterations to the same fluxes."""
+    prob = workloads.hetero(seed=21, J=20000, N=64, n_steps=3)
+    out = {}
+    for mode in ("loop", "per_launch"):
+        if mode == "per_launch":
+            monkeypatch.setenv("OCI_NO_LOOP", "1")
+        with pkg.Solver(prob, precision="fp32", tol=1e-8) as s:
+            its, phis = [], []
+            for _ in range(3):
+                rc, st = s.step()
+                assert rc == pkg.OCI_OK, (mode, rc, st)
+                its.append(st["iters"])
+                phis.append(s.fluxes())
+            out[mode] = (its, np.array(phis))
+    assert out["loop"][0] == out["per_launch"][0]
+    assert _rel(out["loop"][1], out["per_launch"][1]) < 1e-12
