@@ -9,13 +9,17 @@ back-substitution, residual -- every iteration, plus the end-of-step commit.
 Default workload: the production homogeneous slab (65536 cells, S_64, Sigma = 1,
 c = 0.9, dx = 0.1 mfp, dt = 0.05, v = 1, Q = 1, reflecting left / vacuum right),
 FP32 angular flux with compensated moments and double-float capacitance /
-residual difference.  ``compare`` adds SI and FP64 OCI on the same slab, and the
-plain-vs-learned-guess comparison on the thin-cell deployment slab.
-``value`` = cell-ordinate updates per second (cells x ordinates x iterations /
-device time), summed over replicas.  Prints one JSON line.
+residual difference.  ``compare`` adds SI (the paper's march and the parallel
+prefix), FP64 OCI and backward-Euler OCI on the same slab, the plain-vs-learned-
+guess comparison on four thin-cell deployment slabs, and the dense per-material
+inverse against the Woodbury kernel at S_128.  ``value`` = cell-ordinate updates
+per second (cells x ordinates x iterations / device time), summed over replicas;
+``e2e`` = the same through the C ABI with pinned host buffers (source in, fluxes
+out).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload slab|hetero] [--precision fp32|fp64]
+                  [--no-compare] [--no-cpu-baseline] [--only-compare solvers|learned|dense]
 """
 import argparse
 import hashlib

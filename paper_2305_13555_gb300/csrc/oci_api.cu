@@ -1,8 +1,11 @@
 // C ABI of the one-cell-inversion library (declarations and contracts in
 // include/oci.h).  Host-side setup in double precision: Gauss-Legendre set,
 // per-material block inverses and Woodbury capacitance; device memory owned by
-// the handle; each time step is one CUDA graph launch whose iteration loop is a
-// device-side conditional WHILE node, so the host synchronises once per step.
+// the handle; each time step is one CUDA graph launch, so the host
+// synchronises once per step.  Inside the graph the iterations run either in
+// one persistent cooperative launch (the staged FP32 kernel: it loops until the
+// step is decided) or as a device-side conditional WHILE node around one
+// launch per iteration (FP64, SI, backward Euler, the FP32 refinement).
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
