@@ -207,6 +207,20 @@ def run_ours(args, rank, world):
                            if args.precision == "fp32" else "k_cells<double, OCI> (one launch per iteration)"),
                 "iteration_us": round(t_launch * 1e6, 3), "algorithmic_bytes_per_iteration": abytes}
 
+    # the same kernel on the layered 131072-cell S_64 slab, whose ~212 MB working set
+    # does not fit in L2 (every iteration streams from HBM)
+    beyond = None
+    if args.precision == "fp32" and rank == 0:
+        p4 = workloads.config4(seed=args.seed, J=131072, n_steps=2)
+        s4 = pkg.Solver(p4, precision="fp32", tol=p4["tol"], stream=stream.cuda_stream)
+        t4 = pkg.oci_profile_iterations(s4.h, 50)
+        s4.close()
+        b4 = algorithmic_bytes(131072, 64, 4)
+        beyond = {"workload": f"layered slab 131072 cells, S_64 (seed {args.seed})", "iteration_us": round(t4 * 1e6, 3),
+                  "achieved": round(b4 / t4 / 1e9, 1), "frac": round(b4 / t4 / 1e9 / peak, 4),
+                  "algorithmic_bytes_per_iteration": b4}
+    roofline["beyond_l2"] = beyond
+
     # end to end through the C ABI with host buffers: source in, fluxes out, both in
     # pinned host memory (page-locked, so the copies are direct DMA)
     q_pin = torch.empty((J, 4), dtype=torch.float64).pin_memory()
@@ -280,7 +294,9 @@ def run_learned(args, pkg, torch, stream):
     (131072 cells, S_64, sigma_t dx ~ U(0.01, 0.1), c ~ U(0.9, 0.999), dt = 0.02):
     seconds and iterations per converged step of plain FP32 OCI and FP32 OCI with
     the trained network's initial guess on four seeded slabs (2 warm-up and 6
-    timed steps each, from the same initial state), and, on the first slab, plain
+    timed steps each, from the same initial state; the guess always, and the
+    adaptive mode that keeps it only if a plain/guessed trial shows a gain), and,
+    on the first slab, plain
     FP64 OCI and FP32 SI with the paper's march and with the parallel prefix."""
     from paper_2305_13555_gb300 import learned
     if not os.path.exists(learned.DEFAULT_WEIGHTS):
@@ -293,7 +309,7 @@ def run_learned(args, pkg, torch, stream):
     def run(prob, prec, method, nn, n_w, n_t, sweep):
         s = pkg.Solver(prob, precision=prec, tol=1e-8, stream=stream.cuda_stream, max_iter=50000, sweep=sweep)
         if nn:
-            pkg.oci_nn_attach(s.h, W, pkg.OCI_NN_GUESS, 50)
+            pkg.oci_nn_attach(s.h, W, nn, 50)
         its, secs, rc = [], [], pkg.OCI_OK
         for k in range(n_w + n_t):
             rc, st = s.step(method)
@@ -311,18 +327,23 @@ def run_learned(args, pkg, torch, stream):
     per_seed = {}
     for i, seed in enumerate(seeds):
         prob = workloads.config5_deploy(seed, J=131072, N=64, n_steps=16)
-        rec = {"fp32_plain": run(prob, "fp32", "oci", False, 2, 6, "march"),
-               "fp32_nn_guess": run(prob, "fp32", "oci", True, 2, 6, "march")}
+        rec = {"fp32_plain": run(prob, "fp32", "oci", 0, 2, 6, "march"),
+               "fp32_nn_guess": run(prob, "fp32", "oci", pkg.OCI_NN_GUESS, 2, 6, "march"),
+               "fp32_nn_adaptive": run(prob, "fp32", "oci", pkg.OCI_NN_GUESS_ADAPTIVE, 2, 6, "march")}
         if i == 0:
-            rec["fp64_plain"] = run(prob, "fp64", "oci", False, 2, 2, "march")
-            rec["si_fp32"] = run(prob, "fp32", "si", False, 2, 2, "march")
-            rec["si_scan_fp32"] = run(prob, "fp32", "si", False, 2, 6, "scan")
+            rec["fp64_plain"] = run(prob, "fp64", "oci", 0, 2, 2, "march")
+            rec["si_fp32"] = run(prob, "fp32", "si", 0, 2, 2, "march")
+            rec["si_scan_fp32"] = run(prob, "fp32", "si", 0, 2, 6, "scan")
         per_seed[str(seed)] = rec
     out["per_seed"] = per_seed
     ok = [r for r in per_seed.values() if "s_per_step" in r["fp32_plain"] and "s_per_step" in r["fp32_nn_guess"]]
     if ok:
         out["nn_over_plain_time_ratio_mean"] = sum(r["fp32_nn_guess"]["s_per_step"] / r["fp32_plain"]["s_per_step"]
                                                    for r in ok) / len(ok)
+        ad = [r for r in ok if "s_per_step" in r["fp32_nn_adaptive"]]
+        if ad:
+            out["adaptive_over_plain_time_ratio_mean"] = sum(
+                r["fp32_nn_adaptive"]["s_per_step"] / r["fp32_plain"]["s_per_step"] for r in ad) / len(ad)
     return out
 
 

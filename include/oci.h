@@ -238,7 +238,7 @@ int oci_set_state(oci_handle *h, const double *psi_edge);
 int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_launch);
 
 /* ------------------------------------------------- learned guess (oci_nn.h) */
-enum { OCI_NN_OFF = 0, OCI_NN_GUESS = 1, OCI_NN_GUESS_CORRECT = 2 };
+enum { OCI_NN_OFF = 0, OCI_NN_GUESS = 1, OCI_NN_GUESS_CORRECT = 2, OCI_NN_GUESS_ADAPTIVE = 3 };
 
 /* Attach a trained network (parameters: host FP32 array of
  * oci_nn_param_count() elements, layout in oci_nn.h) to the handle, or detach
@@ -250,9 +250,15 @@ enum { OCI_NN_OFF = 0, OCI_NN_GUESS = 1, OCI_NN_GUESS_CORRECT = 2 };
  * every k_corr iterations, applies the same correction to the current
  * iterate, iterates min(k_corr, 8) more times and, if the relative change of
  * phi is then larger than before the correction, restores the saved iterate
- * (plain OCI) and makes no further corrections in that step.  The tolerance
- * is unchanged, so the network changes iteration counts only.  The paper has
- * no counterpart; OCI_EINVAL for a bad mode, k_corr < 1 or NULL params. */
+ * (plain OCI) and makes no further corrections in that step.
+ * OCI_NN_GUESS_ADAPTIVE uses the guess only where it pays: after two plain
+ * steps (a run often starts with a transient), four steps run plain, guessed,
+ * guessed, plain (an order that cancels a linear trend in the iteration
+ * counts), and the guess is kept for the following steps only if the two
+ * guessed steps took at least 3 % fewer iterations than the two plain ones;
+ * the four-step test is repeated every k_corr steps.  The tolerance is unchanged, so the network changes iteration counts
+ * only.  The paper has no counterpart; OCI_EINVAL for a bad mode, k_corr < 1
+ * or NULL params. */
 int oci_nn_attach(oci_handle *h, const float *params, int32_t mode, int32_t k_corr);
 
 /* The handle's static network inputs, as device arrays: stat [J][4] float

@@ -340,7 +340,7 @@ def _stream(stream):
     return _current_stream()
 
 
-OCI_NN_OFF, OCI_NN_GUESS, OCI_NN_GUESS_CORRECT = 0, 1, 2
+OCI_NN_OFF, OCI_NN_GUESS, OCI_NN_GUESS_CORRECT, OCI_NN_GUESS_ADAPTIVE = 0, 1, 2, 3
 
 
 def oci_nn_attach(h, params, mode=OCI_NN_GUESS, k_corr=50):

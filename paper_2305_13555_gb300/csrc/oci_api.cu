@@ -124,6 +124,12 @@ struct oci_handle {
     std::string err;
     // learned guess
     int nn_mode = OCI_NN_OFF, nn_kcorr = 50;
+    // OCI_NN_GUESS_ADAPTIVE: position in the plain/guessed/guessed/plain trial,
+    // iterations of its plain and guessed steps, and the current choice
+    int nn_trial = 0;
+    long nn_trial_plain = 0, nn_trial_nn = 0;
+    bool nn_use = true;
+    int nn_since_trial = 0;
     void *nn_mem = nullptr;          // one allocation for everything below
     float *nn_params = nullptr, *nn_in = nullptr, *nn_out = nullptr, *nn_scale = nullptr, *nn_stat = nullptr,
           *nn_qfeat = nullptr;
@@ -983,7 +989,19 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         if (rc) return rc;
         ++launches;
     }
-    const bool nn = !si && h->nn_mode != OCI_NN_OFF && h->scheme == OCI_TIME_MB;
+    bool nn = !si && h->nn_mode != OCI_NN_OFF && h->scheme == OCI_TIME_MB;
+    int trial_slot = -1;  // adaptive mode: 0 plain / 1 guessed step of a trial, 2 plain lead-in step
+    if (nn && h->nn_mode == OCI_NN_GUESS_ADAPTIVE) {
+        if (h->nn_trial < 0) {
+            trial_slot = 2;
+            nn = false;
+        } else if (h->nn_trial < 4) {
+            trial_slot = (h->nn_trial == 1 || h->nn_trial == 2) ? 1 : 0;
+            nn = trial_slot == 1;
+        } else {
+            nn = h->nn_use;
+        }
+    }
     int accepts = 0, rejects = 0;
     const int unroll = (h->staged && h->pdl_graph) ? kUnroll : 1;  // iteration launches per WHILE body
     auto body_launches = [&](int iters) { return unroll * ((iters + unroll - 1) / unroll); };
@@ -1083,6 +1101,17 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         // history of committed moments for the network: hist[1] <- hist[0] <- phi_out
         std::swap(h->nn_hist[0], h->nn_hist[1]);
         CK(h, cudaMemcpyAsync(h->nn_hist[0], h->phi_out, (size_t)h->J * 32, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    if (trial_slot >= 0 && s.committed) {
+        if (trial_slot < 2) (trial_slot ? h->nn_trial_nn : h->nn_trial_plain) += s.iter;
+        if (++h->nn_trial == 4) {
+            h->nn_use = h->nn_trial_nn < 0.97 * (double)h->nn_trial_plain;
+            h->nn_since_trial = 0;
+        }
+    } else if (!si && h->nn_mode == OCI_NN_GUESS_ADAPTIVE && h->nn_trial >= 4 && s.committed &&
+               ++h->nn_since_trial >= h->nn_kcorr) {
+        h->nn_trial = 0;  // test again
+        h->nn_trial_plain = h->nn_trial_nn = 0;
     }
     const int status = map_status(s.status);
     if (st) {
@@ -1608,7 +1637,7 @@ int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_la
 
 int oci_nn_attach(oci_handle *h, const float *params, int32_t mode, int32_t k_corr)
 {
-    if (!h || mode < OCI_NN_OFF || mode > OCI_NN_GUESS_CORRECT) return OCI_EINVAL;
+    if (!h || mode < OCI_NN_OFF || mode > OCI_NN_GUESS_ADAPTIVE) return OCI_EINVAL;
     if (mode != OCI_NN_OFF && (!params || k_corr < 1)) return OCI_EINVAL;
     CK(h, cudaSetDevice(h->device));
     if (mode == OCI_NN_OFF) {
@@ -1654,6 +1683,10 @@ int oci_nn_attach(oci_handle *h, const float *params, int32_t mode, int32_t k_co
     CK(h, cudaMemcpy(h->nn_params, params, npar * 4, cudaMemcpyHostToDevice));
     h->nn_mode = mode;
     h->nn_kcorr = k_corr;
+    h->nn_trial = -2;  // two plain steps first: the start of a run is often a transient
+    h->nn_trial_plain = h->nn_trial_nn = 0;
+    h->nn_use = true;
+    h->nn_since_trial = 0;
     return OCI_OK;
 }
 

@@ -54,3 +54,29 @@ def test_trained_guess_saves_iterations_on_thin_cells():
     # worse than plain OCI's by more than that order.
     assert np.all(e_plain < 1e-5)
     assert np.all(e_nn < np.maximum(3 * e_plain, 3e-7))
+
+
+def test_adaptive_guess_falls_back_where_the_guess_does_not_pay():
+    """OCI_NN_GUESS_ADAPTIVE: after two plain lead-in steps and its plain /
+    guessed / guessed / plain trial it keeps the guess on the slabs where the
+    guess saves iterations and drops it on those where it costs iterations
+    (seeds 8 and 7, 9, 10 of the deployment family); every step still converges."""
+    W = learned.load_weights()
+    n = 9
+    for seed, keep in ((8, True), (7, False), (9, False), (10, False)):
+        prob = workloads.config5_deploy(seed, J=131072, N=64, n_steps=n)
+        plain_it, _ = _steps(prob, None, n)
+        its = []
+        with pkg.Solver(prob, precision="fp32", tol=1e-8, max_iter=50000) as s:
+            pkg.oci_nn_attach(s.h, W, pkg.OCI_NN_GUESS_ADAPTIVE, 50)
+            for k in range(n):
+                rc, st = s.step()
+                assert rc == pkg.OCI_OK, (rc, st)
+                its.append(st["iters"])
+                guessed = k in (3, 4) or (k >= 6 and keep)
+                assert st["nn_accepts"] == (1 if guessed else 0), (seed, k, st)
+        print("seed", seed, "plain", plain_it.tolist(), "adaptive", its)
+        if keep:
+            assert sum(its[6:]) < 0.85 * sum(plain_it[6:].tolist())
+        else:  # back on the plain path (states equal to within the tolerance)
+            assert all(abs(a - b) <= 5 for a, b in zip(its[6:], plain_it[6:].tolist())), (its, plain_it)
