@@ -45,12 +45,11 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2305_13555_gb300", "csrc", "oci_device.cu
 
 def make_problem(args):
     if args.workload == "slab":
-        p = workloads.config2(N=args.n_ord, c=args.c, dx=args.dx, J=args.cells, n_steps=args.steps + args.warmup)
+        p = workloads.config2(N=args.n_ord, c=args.c, dx=args.dx, J=args.cells, n_steps=50)
         desc = (f"homogeneous slab {p['n_cells']} cells, S_{p['n_ord']}, sigma_t=1, c={args.c}, dx={args.dx} mfp, "
                 f"dt=0.05, v=1, Q=1, reflect/vacuum, tol 1e-8")
     else:
-        p = workloads.config4(seed=args.seed, J=args.cells if args.cells != 65536 else 131072,
-                              n_steps=args.steps + args.warmup)
+        p = workloads.config4(seed=args.seed, J=args.cells if args.cells != 65536 else 131072, n_steps=100)
         desc = (f"seeded layered slab {p['n_cells']} cells, S_64, sigma_t 10^U(-2,2), c U(0,0.999), "
                 f"tau U(0.05,5), dt=0.02, vacuum/vacuum, tol 1e-8 (seed {args.seed})")
     return p, desc
@@ -90,8 +89,8 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
-
+    """nvidia-smi clocks / throttle reasons every 100 ms, each line stamped on
+    arrival; only the lines stamped inside the timed region count."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -99,27 +98,44 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.lines = []
+        self.reader = None
 
     def start(self):
+        """Starts nvidia-smi and returns once its first line has arrived (or after 3 s)."""
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
 
-    def stop(self):
+        def read():
+            for line in self.proc.stdout:
+                self.lines.append((time.perf_counter(), line))
+
+        self.reader = threading.Thread(target=read, daemon=True)
+        self.reader.start()
+        t_end = time.perf_counter() + 3.0
+        while not self.lines and time.perf_counter() < t_end:
+            time.sleep(0.01)
+
+    def stop(self, t0, t1):
         if self.proc is None:
             return None
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+            self.proc.wait()
+        self.reader.join(timeout=5)
+        inside = [ln for t, ln in self.lines if t0 <= t <= t1]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in inside:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -132,9 +148,10 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
-            return None
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": "timed region shorter than the 100 ms sampling period"}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "timed_region_s": round(t1 - t0, 3)}
 
 
 def aggregate(dev_time, units, device="cpu"):
@@ -167,7 +184,23 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     s = pkg.Solver(prob, precision=args.precision, tol=prob["tol"], stream=stream.cuda_stream)
+    # the workload is a trajectory of n_steps time steps from psi0 = 0; longer runs
+    # replay it, restarting from the initial condition through oci_set_state
+    n_traj = prob["n_steps"]
+    psi_init = torch.zeros((J, N, 2), dtype=torch.float64).pin_memory().numpy()
+    counter = {"k": 0, "restarts": 0}
+
+    def restart_if_due():
+        """Returns the library kernels the restart launched (one conversion kernel)."""
+        due = counter["k"] and counter["k"] % n_traj == 0
+        if due:
+            s.set_state(psi_init)
+            counter["restarts"] += 1
+        counter["k"] += 1
+        return 1 if due else 0
+
     for _ in range(args.warmup):
+        restart_if_due()
         rc, st = s.step()
         assert rc == pkg.OCI_OK, (rc, st)
     if world > 1:
@@ -178,6 +211,7 @@ def run_ours(args, rank, world):
     iters, secs, launches = [], [], 0
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
+        launches += restart_if_due()  # host call between steps, outside the steps' device time
         flush.zero_()  # evict the ~100 MB working set from L2 between timed steps
         rc, st = s.step()
         assert rc == pkg.OCI_OK, (rc, st)
@@ -186,7 +220,7 @@ def run_ours(args, rank, world):
         launches += st["launches"]  # kernels of the library for the step (as counted by oci_step)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
-    clk = clocks.stop()
+    clk = clocks.stop(t_wall0, t_wall0 + wall)
     dev_time = float(sum(secs))
     units = float(J) * N * float(sum(iters))
     if world > 1:
@@ -228,16 +262,21 @@ def run_ours(args, rank, world):
     q_host, phi_host = q_pin.numpy(), phi_pin.numpy()
     q_host[:] = np.asarray(prob["q"], dtype=np.float64).reshape(J, 4)
     e2e_iters = 0
+    r0 = counter["restarts"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
+        restart_if_due()
         pkg.oci_set_source(s.h, q_host)
         rc, st = s.step()
         pkg.oci_fluxes(s.h, phi_host)
         e2e_iters += st["iters"]
     e2e_t = time.perf_counter() - t0
-    e2e = {"value": float(J) * N * e2e_iters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(q_host.nbytes),
-           "d2h_bytes_per_step": int(phi_host.nbytes)}
+    state_bytes = (counter["restarts"] - r0) * psi_init.nbytes  # initial conditions of the replayed trajectories
+    e2e = {"value": float(J) * N * e2e_iters / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": int(q_host.nbytes + state_bytes / args.steps),
+           "d2h_bytes_per_step": int(phi_host.nbytes),
+           "h2d": "source Q each step, initial angular flux psi0 at each trajectory restart (pinned host memory)"}
     s.close()
 
     compare = {}
@@ -246,7 +285,7 @@ def run_ours(args, rank, world):
         compare["learned_guess"] = run_learned(args, pkg, torch, stream)
         compare["dense_inverse_s128"] = run_dense(args, pkg, torch, stream)
     return {
-        "value": value, "units": units, "dev_time": dev_time, "wall": wall, "iters": iters, "launches": launches,
+        "n_traj": n_traj, "value": value, "units": units, "dev_time": dev_time, "wall": wall, "iters": iters, "launches": launches,
         "roofline": roofline, "e2e": e2e, "clocks": clk, "desc": desc, "J": J, "N": N, "compare": compare,
     }
 
@@ -401,30 +440,46 @@ def cpu_baseline(args, seconds_target=15.0):
                       f"problem, {t:.1f} s"}
 
 
-def run_reference(args):
-    """The oracle as the reference arm: each step a bounded sample (a few OCI
-    iterations of the workload) timed on the host cores."""
+def run_reference(args, budget_s=150.0):
+    """The oracle as the reference arm: each step a bounded sample of the
+    workload timed on the host cores, sized so that warm-up plus timed steps
+    take about budget_s: two OCI iterations of the whole problem per step when
+    they fit, else one iteration of a slab of the same recipe with fewer cells."""
     import oracle
     prob, desc = make_problem(args)
     J, N = prob["n_cells"], prob["n_ord"]
     P = oracle.Problem(prob)
+    t0 = time.perf_counter()
+    oracle.run(P, "oci", 1, tol=0.0, max_iter=1, commit_unconverged=True)
+    t_iter = time.perf_counter() - t0
+    per_step_budget = budget_s / max(1, args.steps + args.warmup)
+    per_step, Js = 2, J
+    if 2 * t_iter > per_step_budget:
+        per_step = 1
+        if t_iter > per_step_budget:
+            Js = max(1024, int(J * per_step_budget / t_iter) // 256 * 256)
+            sub = argparse.Namespace(**vars(args))
+            sub.cells = Js
+            P = oracle.Problem(make_problem(sub)[0])
     for _ in range(args.warmup):
         oracle.run(P, "oci", 1, tol=0.0, max_iter=1, commit_unconverged=True)
     its, secs = 0, 0.0
-    per_step = 2
     for _ in range(args.steps):
         t0 = time.perf_counter()
         oracle.run(P, "oci", 1, tol=0.0, max_iter=per_step, commit_unconverged=True)
         secs += time.perf_counter() - t0
         its += per_step
-    value = J * N * its / secs
+    value = Js * N * its / secs
+    sample = f"{per_step} OCI iteration(s) per step of the {J}-cell S_{N} problem"
+    if Js != J:
+        sample = f"1 OCI iteration per step of a {Js}-cell slab of the same recipe (the {J}-cell S_{N} problem scaled down)"
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "parallelism": "host threads (OpenMP)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-                         "sample": f"{per_step} OCI iterations per step of the {J}-cell S_{N} problem"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -432,7 +487,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="slab", choices=["slab", "hetero"])
@@ -480,7 +535,9 @@ def main():
             "data": "synthetic",
             "config": {"workload": r["desc"], "cells": r["J"], "ordinates": r["N"],
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "flushed (256 MiB write) between timed steps; iterations within a step reuse L2"},
+                       "l2": "flushed (256 MiB write) between timed steps; iterations within a step reuse L2",
+                       "trajectory": f"{r['n_traj']} time steps from psi0 = 0, replayed from psi0 (oci_set_state) "
+                                     f"when warm-up + timed steps exceed it"},
             "iters_per_step": sum(r["iters"]) / len(r["iters"]),
             "s_per_step": r["dev_time"] / args.steps,
             "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],

@@ -221,8 +221,11 @@ int oci_fluxes_device(const oci_handle *h, void *dptr);
  * [J][N][2]; in OCI_FP32 mode the stored floats are widened. */
 int oci_get_state(const oci_handle *h, double *psi_edge);
 
-/* Resume: replace the time-edge angular flux (host [J][N][2]); the next step
- * starts from it. */
+/* Resume or restart: replace the time-edge angular flux (host [J][N][2]); the
+ * next step starts from it.  One host-to-device copy (direct DMA from
+ * page-locked memory) and a conversion kernel on the handle's stream; returns
+ * with the state in place.  With a network attached, its two previous-step
+ * flux inputs restart from the new state's moments. */
 int oci_set_state(oci_handle *h, const double *psi_edge);
 
 /* Time the one-cell-inversion iteration alone: run n_iter iterations from the

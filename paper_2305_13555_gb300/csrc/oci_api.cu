@@ -248,46 +248,78 @@ int upload_real(oci_handle *h, void *dst, const std::vector<double> &src)
     return OCI_OK;
 }
 
-// psi [J][N][2] (host, ordinates ascending) -> psi_edge [J][P] (+L, +R, -L, -R)
-// and phi0 = (sum w psi_L, sum w psi_R) in both time moments.
+// psi [J][N][2] (device copy, ordinates ascending) -> psi_edge [J][P]
+// (+L, +R, -L, -R) and phi = (sum w psi_L, sum w psi_R) in both time moments:
+// one warp per cell, lanes over ordinate pairs, the moments summed in FP64
+// (w_p is the weight of both +mu_p and -mu_p; Gauss-Legendre is symmetric).
+template <typename R>
+__global__ void k_load_state(const double *__restrict__ psi, const double *__restrict__ wpos, int J, int P,
+                             r4<R> *psi_edge, ocik::phi_t<R> *phi0, double *phi_out)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int j = gw; j < J; j += nw) {
+        const double *pj = psi + (size_t)j * P * 4;
+        double sL = 0.0, sR = 0.0;
+        for (int p = lane; p < P; p += 32) {
+            const double2 a = *(const double2 *)(pj + 2 * (P + p));      // +mu_p
+            const double2 b = *(const double2 *)(pj + 2 * (P - 1 - p));  // -mu_p
+            psi_edge[(size_t)j * P + p] = r4<R>{(R)a.x, (R)a.y, (R)b.x, (R)b.y};
+            sL += wpos[p] * (a.x + b.x);
+            sR += wpos[p] * (a.y + b.y);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sL += __shfl_xor_sync(0xffffffffu, sL, o);
+            sR += __shfl_xor_sync(0xffffffffu, sR, o);
+        }
+        if (lane < 4) {
+            const double f = (lane & 1) ? sR : sL;
+            phi_out[4 * (size_t)j + lane] = f;
+            phi0[4 * (size_t)j + lane] = ocik::phi_from_double<R>(f);
+        }
+    }
+}
+
+// New committed state from host psi [J][N][2] (nullptr: zero): one
+// host-to-device copy into stream-ordered scratch (direct DMA when the caller's
+// buffer is page-locked) and the conversion kernel.  The learned guess's flux
+// history restarts from the new moments.
 int load_state(oci_handle *h, const double *psi)
 {
-    const int J = h->J, N = h->N, P = h->P;
-    std::vector<double> pe((size_t)J * P * 4, 0.0), ph0((size_t)J * 4, 0.0);
-    if (psi) {
-        for (int j = 0; j < J; ++j) {
-            double sL = 0.0, sR = 0.0;
-            for (int m = 0; m < N; ++m) {
-                sL += h->w[m] * psi[((size_t)j * N + m) * 2];
-                sR += h->w[m] * psi[((size_t)j * N + m) * 2 + 1];
-            }
-            for (int p = 0; p < P; ++p) {
-                const int mp = P + p, mm = P - 1 - p;
-                double *o = &pe[((size_t)j * P + p) * 4];
-                o[0] = psi[((size_t)j * N + mp) * 2];
-                o[1] = psi[((size_t)j * N + mp) * 2 + 1];
-                o[2] = psi[((size_t)j * N + mm) * 2];
-                o[3] = psi[((size_t)j * N + mm) * 2 + 1];
-            }
-            ph0[j * 4 + 0] = sL; ph0[j * 4 + 1] = sR; ph0[j * 4 + 2] = sL; ph0[j * 4 + 3] = sR;
-        }
-    }
-    int rc = upload_real(h, h->psi_edge, pe);
-    if (rc) return rc;
-    if (h->prec == OCI_FP32) {
-        // double-float iterate storage: (h, l) with h = fl(x), l = fl(x - h)
-        std::vector<float> f(ph0.size() * 2);
-        for (size_t i = 0; i < ph0.size(); ++i) {
-            f[2 * i] = (float)ph0[i];
-            f[2 * i + 1] = (float)(ph0[i] - (double)f[2 * i]);
-        }
-        CK(h, cudaMemcpyAsync(h->phi0, f.data(), f.size() * 4, cudaMemcpyHostToDevice, h->stream));
-        CK(h, cudaStreamSynchronize(h->stream));
+    const int J = h->J, P = h->P;
+    const size_t rs = h->prec == OCI_FP64 ? 8 : 4;
+    if (!psi) {
+        CK(h, cudaMemsetAsync(h->psi_edge, 0, (size_t)J * P * 4 * rs, h->stream));
+        CK(h, cudaMemsetAsync(h->phi0, 0, (size_t)J * 32, h->stream));  // double or float2 per moment
+        CK(h, cudaMemsetAsync(h->phi_out, 0, (size_t)J * 32, h->stream));
     } else {
-        CK(h, cudaMemcpyAsync(h->phi0, ph0.data(), ph0.size() * 8, cudaMemcpyHostToDevice, h->stream));
+        const size_t n = (size_t)J * P * 4;
+        std::vector<double> wpos(P);
+        for (int p = 0; p < P; ++p) wpos[p] = h->w[P + p];
+        double *scratch = nullptr;
+        CK(h, cudaMallocAsync((void **)&scratch, (n + P) * 8, h->stream));
+        cudaError_t e = cudaMemcpyAsync(scratch, psi, n * 8, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + n, wpos.data(), P * 8, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) {
+            const int grid = std::max(1, std::min((J + 7) / 8, 152 * 8));
+            if (h->prec == OCI_FP64)
+                k_load_state<double><<<grid, 256, 0, h->stream>>>(scratch, scratch + n, J, P, (r4<double> *)h->psi_edge,
+                                                                  (ocik::phi_t<double> *)h->phi0, h->phi_out);
+            else
+                k_load_state<float><<<grid, 256, 0, h->stream>>>(scratch, scratch + n, J, P, (r4<float> *)h->psi_edge,
+                                                                 (ocik::phi_t<float> *)h->phi0, h->phi_out);
+            e = cudaGetLastError();
+        }
+        const cudaError_t ef = cudaFreeAsync(scratch, h->stream);
+        CK(h, e);
+        CK(h, ef);
     }
-    CK(h, cudaMemcpyAsync(h->phi_out, ph0.data(), ph0.size() * 8, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->nn_hist[0]) {
+        CK(h, cudaMemcpyAsync(h->nn_hist[0], h->phi_out, (size_t)J * 32, cudaMemcpyDeviceToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(h->nn_hist[1], h->phi_out, (size_t)J * 32, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));  // wpos is a temporary; the call returns with the state in place
     h->guess_valid = false;
     return OCI_OK;
 }

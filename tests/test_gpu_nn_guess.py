@@ -54,6 +54,27 @@ def test_untrained_network_keeps_the_answer(mode, prec, tol, bound):
         assert all(st["nn_rejects"] == 0 for st in stats)
 
 
+def test_set_state_restarts_the_network_history():
+    """After oci_set_state the network's two previous steps are the new state's
+    moments, so a restart from the initial condition replays the guessed steps."""
+    prob = workloads.hetero(seed=21, J=3000, N=16, n_steps=4, tau_range=(0.01, 0.1), c_range=(0.9, 0.999),
+                            bc_left="reflect", bc_right="vacuum")
+    J, N = prob["n_cells"], prob["n_ord"]
+    params = learned.init_params(seed=3)
+    with pkg.Solver(prob, precision="fp32", tol=1e-8) as s:
+        pkg.oci_nn_attach(s.h, params, pkg.OCI_NN_GUESS, 20)
+        first = []
+        for _ in range(3):
+            rc, st = s.step()
+            assert rc == pkg.OCI_OK and st["nn_accepts"] == 1
+            first.append((st["iters"], s.fluxes()))
+        s.set_state(np.zeros((J, N, 2)))
+        for it, phi in first:
+            rc, st = s.step()
+            assert rc == pkg.OCI_OK and st["iters"] == it, (st, it)
+            assert np.abs(s.fluxes() - phi).max() <= 1e-12 * np.abs(phi).max()
+
+
 def test_attach_validation():
     prob = workloads.config1()
     with pkg.Solver(prob) as s:

@@ -185,6 +185,35 @@ def test_state_roundtrip_and_time_dependent_source():
         assert _rel(s.fluxes(), r2["phi_steps"][0]) < FP64_TOL
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_set_state_restarts_the_trajectory(prec):
+    """oci_set_state converts on the device: get_state returns what was set
+    (exactly in FP64, to float rounding in FP32), and a handle restarted from
+    the initial condition replays its own first steps."""
+    prob = workloads.random_small(seed=17, J=333, N=32, bc_left="reflect", bc_right="incident")
+    J, N = prob["n_cells"], prob["n_ord"]
+    psi0 = np.asarray(prob["psi0"], dtype=np.float64).reshape(J, N, 2)
+    tol = 1e-12 if prec == "fp64" else 1e-8
+    with pkg.Solver(prob, precision=prec, tol=tol) as s:
+        got = s.get_state()
+        if prec == "fp64":
+            assert np.array_equal(got, psi0)
+        else:
+            assert np.array_equal(got, psi0.astype(np.float32).astype(np.float64))
+        first = []
+        for _ in range(3):
+            rc, st = s.step()
+            assert rc == pkg.OCI_OK
+            first.append((st["iters"], s.fluxes()))
+        s.set_state(psi0)
+        for it, phi in first:
+            rc, st = s.step()
+            assert rc == pkg.OCI_OK and st["iters"] == it
+            assert _rel(s.fluxes(), phi) < 1e-13
+        s.set_state(np.zeros((J, N, 2)))
+        assert not s.get_state().any()
+
+
 def test_steady_state_and_single_cell():
     prob = workloads.random_small(seed=9, J=1, N=2, bc_left="incident", bc_right="incident")
     prob["v"] = float("inf")
