@@ -297,16 +297,20 @@ def run_compare(args, pkg, torch, stream):
     out = {}
     prob, _ = make_problem(args)
     J, N = prob["n_cells"], prob["n_ord"]
-    for name, method, prec, sweep, scheme in (("si_" + args.precision, "si", args.precision, "march", "mb"),
-                                              ("si_scan_" + args.precision, "si", args.precision, "scan", "mb"),
-                                              ("oci_fp64", "oci", "fp64", "march", "mb"),
-                                              ("si_fp64", "si", "fp64", "march", "mb"),
-                                              ("si_scan_fp64", "si", "fp64", "scan", "mb"),
-                                              ("oci_backward_euler_fp32", "oci", "fp32", "march", "be"),
-                                              ("oci_backward_euler_fp64", "oci", "fp64", "march", "be")):
-        if prec == args.precision and method == "oci" and scheme == "mb":
+    for name, method, prec, sweep, scheme, halo in (
+            ("si_" + args.precision, "si", args.precision, "march", "mb", "fp32"),
+            ("si_scan_" + args.precision, "si", args.precision, "scan", "mb", "fp32"),
+            ("oci_fp64", "oci", "fp64", "march", "mb", "fp32"),
+            ("si_fp64", "si", "fp64", "march", "mb", "fp32"),
+            ("si_scan_fp64", "si", "fp64", "scan", "mb", "fp32"),
+            ("oci_backward_euler_fp32", "oci", "fp32", "march", "be", "fp32"),
+            ("oci_backward_euler_fp64", "oci", "fp64", "march", "be", "fp32"),
+            ("oci_fp32_same_window", "oci", "fp32", "march", "mb", "fp32"),
+            ("oci_fp32_bf16_halo", "oci", "fp32", "march", "mb", "bf16")):
+        if (halo == "bf16" or name == "oci_fp32_same_window") and args.precision != "fp32":
             continue
-        s = pkg.Solver(prob, precision=prec, tol=prob["tol"], stream=stream.cuda_stream, sweep=sweep, scheme=scheme)
+        s = pkg.Solver(prob, precision=prec, tol=prob["tol"], stream=stream.cuda_stream, sweep=sweep, scheme=scheme,
+                       halo=halo)
         n_w, n_t = 2, min(args.steps, 5)
         its, secs = [], []
         ok = True
@@ -325,6 +329,16 @@ def run_compare(args, pkg, torch, stream):
                          "iters_per_step": sum(its) / len(its)}
             if t_it is not None:
                 out[name]["s_per_iteration"] = t_it
+    if args.precision == "fp32":
+        # the BF16 halo's iteration against the FP32 one on the 131072-cell layered
+        # slab, whose working set does not fit in L2
+        p4 = workloads.config4(seed=args.seed, J=131072, n_steps=2)
+        row = {"workload": f"layered slab 131072 cells, S_64 (seed {args.seed})"}
+        for halo in ("fp32", "bf16"):
+            s = pkg.Solver(p4, precision="fp32", tol=p4["tol"], stream=stream.cuda_stream, halo=halo)
+            row[f"s_per_iteration_{halo}_halo"] = pkg.oci_profile_iterations(s.h, 50)
+            s.close()
+        out["bf16_halo_beyond_l2"] = row
     return out
 
 

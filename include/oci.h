@@ -61,8 +61,10 @@ enum { OCI_BC_VACUUM = 0, OCI_BC_REFLECT = 1, OCI_BC_INCIDENT = 2 };
 /* Arithmetic / storage precision of the angular flux and per-ordinate blocks.
  * OCI_FP64: everything in double.  OCI_FP32: angular flux, per-ordinate 4x4
  * blocks and the scattering-moment sums in float (the sums compensated,
- * TwoSum), the 4x4 capacitance solve and the residual norm in double. */
-enum { OCI_FP64 = 0, OCI_FP32 = 1 };
+ * TwoSum), the 4x4 capacitance solve and the residual norm in double.
+ * OCI_FP32_BF16HALO: OCI_FP32 with oci_set_halo(OCI_HALO_BF16) applied at
+ * creation (OCI_EINVAL where that call would refuse). */
+enum { OCI_FP64 = 0, OCI_FP32 = 1, OCI_FP32_BF16HALO = 2 };
 
 /* ------------------------------------------------------------- problem */
 typedef struct oci_problem {
@@ -172,6 +174,25 @@ int oci_set_sweep(oci_handle *h, int32_t sweep);
  * an unknown scheme or a singular capacitance, OCI_ENOMEM, OCI_ECUDA. */
 enum { OCI_TIME_MB = 0, OCI_TIME_BE = 1 };
 int oci_set_time_scheme(oci_handle *h, int32_t scheme);
+
+/* Storage of the incident-flux halo in the OCI iteration of an OCI_FP32
+ * handle (the face buffers that the iteration reads from the neighbours'
+ * previous iterate, step a3; the paper stores everything in double).
+ * OCI_HALO_FP32 (default): float pairs, 24 bytes per cell-ordinate and
+ * iteration.  OCI_HALO_BF16: each OCI step starts with a BF16 phase whose
+ * iterations read and write the halo as bfloat16 pairs (16 bytes per
+ * cell-ordinate); BF16 rounding (2^-8 relative) stops the relative change of
+ * phi near 1e-3, so the phase ends once the change is below 2e-3, after two
+ * iterations without a 10% fall, or two iterations before max_iter; one
+ * iteration turns the halo back into floats and the FP32 iteration finishes to
+ * the tolerance, so the answer keeps the OCI_FP32 accuracy and the last
+ * iteration of every step reads float faces.  Applies to oci_step with the
+ * Woodbury solver, multiple balance, no corrector and max_iter >= 4 (other
+ * steps run the FP32 halo).  OCI_EINVAL for an OCI_FP64 handle, N/2 not a
+ * multiple of 4, S_N other than S_32, S_64 or S_128, or no persistent
+ * cooperative loop on the device; OCI_ENOMEM; OCI_ECUDA. */
+enum { OCI_HALO_FP32 = 0, OCI_HALO_BF16 = 1 };
+int oci_set_halo(oci_handle *h, int32_t halo);
 
 /* Diagnostics of the bounded waits (the paper has no counterpart).  The
  * persistent FP32 iteration meets the other blocks at a grid barrier once per

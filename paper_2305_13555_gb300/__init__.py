@@ -18,7 +18,8 @@ from . import build as _build
 
 OCI_OK, OCI_EINVAL, OCI_ENOMEM, OCI_ECUDA, OCI_ENOTCONV, OCI_ENAN, OCI_ETIMEOUT, OCI_ESTATE = range(8)
 OCI_BC_VACUUM, OCI_BC_REFLECT, OCI_BC_INCIDENT = 0, 1, 2
-OCI_FP64, OCI_FP32 = 0, 1
+OCI_FP64, OCI_FP32, OCI_FP32_BF16HALO = 0, 1, 2
+OCI_HALO_FP32, OCI_HALO_BF16 = 0, 1
 OCI_SOLVER_WOODBURY, OCI_SOLVER_DENSE = 0, 1
 OCI_SWEEP_MARCH, OCI_SWEEP_SCAN = 0, 1
 OCI_TIME_MB, OCI_TIME_BE = 0, 1
@@ -28,7 +29,8 @@ _SOLVER = {"woodbury": OCI_SOLVER_WOODBURY, "dense": OCI_SOLVER_DENSE}
 _BC = {"vacuum": OCI_BC_VACUUM, "reflect": OCI_BC_REFLECT, "reflecting": OCI_BC_REFLECT,
        "incident": OCI_BC_INCIDENT}
 _PREC = {"fp64": OCI_FP64, "f64": OCI_FP64, "double": OCI_FP64, "fp32": OCI_FP32, "f32": OCI_FP32,
-         "float": OCI_FP32}
+         "float": OCI_FP32, "fp32_bf16halo": OCI_FP32_BF16HALO}
+_HALO = {"fp32": OCI_HALO_FP32, "bf16": OCI_HALO_BF16}
 
 
 class OciProblem(ctypes.Structure):
@@ -65,6 +67,7 @@ SIGNATURES = {
     "oci_set_solver": (ctypes.c_int, [_VP, _I32]),
     "oci_set_sweep": (ctypes.c_int, [_VP, _I32]),
     "oci_set_time_scheme": (ctypes.c_int, [_VP, _I32]),
+    "oci_set_halo": (ctypes.c_int, [_VP, _I32]),
     "oci_set_wait_limits": (ctypes.c_int, [_VP, ctypes.c_uint32, _I32]),
     "oci_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
     "si_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
@@ -217,6 +220,13 @@ def oci_set_time_scheme(h, scheme):
     _check(load_library().oci_set_time_scheme(h, int(scheme)), "oci_set_time_scheme", h)
 
 
+def oci_set_halo(h, halo):
+    """OCI_HALO_FP32 (default) or OCI_HALO_BF16 for the OCI iteration's face buffers (see oci.h);
+    also "fp32" / "bf16"."""
+    halo = _HALO.get(halo, halo)
+    _check(load_library().oci_set_halo(h, int(halo)), "oci_set_halo", h)
+
+
 def oci_step(h):
     """One OCI time step; returns (status, stats dict).  Raises only on
     OCI_EINVAL / OCI_ECUDA; convergence failures come back as the status."""
@@ -277,10 +287,12 @@ class Solver:
     """Owns one handle.  ``step()`` / ``si_step()`` advance one time step."""
 
     def __init__(self, prob, precision="fp64", tol=None, max_iter=100000, stream=None, solver="woodbury",
-                 sweep="march", scheme="mb"):
+                 sweep="march", scheme="mb", halo="fp32"):
         self.prob = prob
         self.h = oci_create(prob, precision, tol, max_iter, stream)
         try:
+            if halo != "fp32":
+                oci_set_halo(self.h, halo)
             if solver != "woodbury":
                 oci_set_solver(self.h, solver)
             if sweep != "march":

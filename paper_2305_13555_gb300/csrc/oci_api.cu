@@ -171,6 +171,14 @@ struct oci_handle {
     int loop_fixed = 0;
     void *scan_mem = nullptr;  // segment maps [2P][nseg], entering values [2P][nseg]
     int scan_nseg = 0;
+    // BF16 halo (oci_set_halo): face buffers as bf16 pairs and the step graph
+    // entry -> BF16 loop -> exit -> FP32 loop -> commit
+    int halo = OCI_HALO_FP32;
+    ocik::HaloKernels hk{};
+    void *hface_mem = nullptr;
+    unsigned *hfP[2] = {nullptr, nullptr}, *hfM[2] = {nullptr, nullptr};
+    cudaGraph_t graph_oci_h = nullptr;
+    cudaGraphExec_t exec_oci_h = nullptr;
 };
 
 namespace {
@@ -230,6 +238,10 @@ KParams<R> make_params(const oci_handle *h, int use_cond, cudaGraphConditionalHa
     p.loop_partials = h->loop_partials;
     p.loop_bar = h->loop_bar;
     p.loop_fixed = h->loop_fixed;
+    for (int b = 0; b < 2; ++b) {
+        p.hfP[b] = h->hfP[b];
+        p.hfM[b] = h->hfM[b];
+    }
     return p;
 }
 
@@ -683,6 +695,84 @@ int build_lin_graph(oci_handle *h)
     return OCI_OK;
 }
 
+// OCI step with the BF16 halo: begin -> entry iteration (float faces in, BF16
+// out) -> BF16 persistent loop (until ST_SWITCH) -> exit iteration (BF16 in,
+// float out) -> FP32 persistent loop -> commit.  The last iteration always
+// reads float faces, so the commit is the plain one.
+int build_halo_graph(oci_handle *h)
+{
+    cudaGraph_t g;
+    CK(h, cudaGraphCreate(&g, 0));
+    KParams<float> plain = make_params<float>(h, 0, 0);
+    void *a_plain[] = {&plain};
+    IterState *st = h->d_st;
+    void *a_st[] = {&st};
+    const dim3 grid(h->cells_grid), block(h->cells_block);
+    cudaGraphNode_t n_begin, n_entry, n_hloop, n_exit, n_loop, n_commit, n_zero;
+    int rc = add_kernel(h, g, &n_begin, nullptr, 0, (const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st);
+    if (!rc) rc = add_kernel(h, g, &n_entry, &n_begin, 1, h->hk.entry, grid, block, a_plain, h->cells_smem);
+    if (rc) return rc;
+    cudaMemsetParams mp{};
+    mp.dst = h->loop_bar;
+    mp.value = 0;
+    mp.elementSize = sizeof(unsigned);
+    mp.width = 1;
+    mp.height = 1;
+    CK(h, cudaGraphAddMemsetNode(&n_zero, g, &n_entry, 1, &mp));
+    rc = add_kernel(h, g, &n_hloop, &n_zero, 1, h->hk.loop, grid, block, a_plain, h->cells_smem);
+    if (rc) return rc;
+    cudaLaunchAttributeValue v{};
+    v.cooperative = 1;
+    CK(h, cudaGraphKernelNodeSetAttribute(n_hloop, cudaLaunchAttributeCooperative, &v));
+    rc = add_kernel(h, g, &n_exit, &n_hloop, 1, h->hk.exit, grid, block, a_plain, h->cells_smem);
+    if (!rc) rc = add_loop(h, g, &n_exit, &n_loop, a_plain);
+    if (!rc) rc = add_kernel(h, g, &n_commit, &n_loop, 1, h->ks.commit_oci, dim3(h->grid_pc), dim3(kBlock), a_plain);
+    if (rc) return rc;
+    CK(h, cudaGraphInstantiate(&h->exec_oci_h, g, 0));
+    h->graph_oci_h = g;
+    return OCI_OK;
+}
+
+// BF16 face buffers: zeroed, with the prescribed boundary data (faceP[.][0],
+// faceM[.][J]) of the float buffers rounded into both.
+__global__ void k_halo_bounds(const r2<float> *fP0, const r2<float> *fMJ, int P, unsigned *hP0, unsigned *hP1,
+                              unsigned *hMJ0, unsigned *hMJ1)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        const unsigned a = ocik::pack_bf16x2(fP0[i].x, fP0[i].y), b = ocik::pack_bf16x2(fMJ[i].x, fMJ[i].y);
+        hP0[i] = a;
+        hP1[i] = a;
+        hMJ0[i] = b;
+        hMJ1[i] = b;
+    }
+}
+
+int halo_setup(oci_handle *h)
+{
+    if (h->prec != OCI_FP32 || !h->use_loop || h->P % 4 != 0 || !ocik::kernel_set_bf16(h->lpc, h->ppl, &h->hk))
+        return OCI_EINVAL;
+    int sms = 0, per_sm = 0;
+    for (const void *fn : {h->hk.entry, h->hk.loop, h->hk.exit})
+        CK(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->cells_smem));
+    CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->hk.loop, h->cells_block, h->cells_smem));
+    if (h->cells_grid > sms * per_sm) return OCI_EINVAL;  // the cooperative loop would not fit
+    const size_t fb = (size_t)(h->J + 1) * h->P * 4, fa = (fb + 255) & ~(size_t)255;
+    if (cudaMalloc(&h->hface_mem, 4 * fa) != cudaSuccess) return OCI_ENOMEM;
+    char *b = (char *)h->hface_mem;
+    h->hfP[0] = (unsigned *)b;
+    h->hfP[1] = (unsigned *)(b + fa);
+    h->hfM[0] = (unsigned *)(b + 2 * fa);
+    h->hfM[1] = (unsigned *)(b + 3 * fa);
+    CK(h, cudaMemsetAsync(h->hface_mem, 0, 4 * fa, h->stream));
+    const size_t JP = (size_t)h->J * h->P;
+    k_halo_bounds<<<1, 256, 0, h->stream>>>((const r2<float> *)h->faceP[0], (const r2<float> *)h->faceM[0] + JP, h->P,
+                                             h->hfP[0], h->hfP[1], h->hfM[0] + JP, h->hfM[1] + JP);
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(h->stream));
+    return build_halo_graph(h);
+}
+
 int ensure_graphs(oci_handle *h)
 {
     if (h->exec_oci && !h->exec_si) {
@@ -1038,6 +1128,7 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
     const int unroll = (h->staged && h->pdl_graph) ? kUnroll : 1;  // iteration launches per WHILE body
     auto body_launches = [&](int iters) { return unroll * ((iters + unroll - 1) / unroll); };
     int corrections = 0, graph_runs = 0;
+    bool halo_graph = false;
     CK(h, cudaEventRecord(h->ev0, h->stream));
     if (nn) {
         rc = nn_guess(h);
@@ -1107,7 +1198,9 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         IterConfig c = h->cfg;
         if (si) c.stall_floor = 0.0;  // SI has no refinement: no stall stop
         if ((rc = set_device_cfg(h, c))) return rc;
-        CK(h, cudaGraphLaunch(si ? h->exec_si : h->exec_oci, h->stream));
+        // BF16 halo: entry, BF16 loop and exit take at least three iterations
+        halo_graph = !si && h->halo == OCI_HALO_BF16 && h->exec_oci_h && h->cfg.max_iter >= 4;
+        CK(h, cudaGraphLaunch(halo_graph ? h->exec_oci_h : (si ? h->exec_si : h->exec_oci), h->stream));
         ++graph_runs;
     }
     CK(h, cudaEventRecord(h->ev1, h->stream));
@@ -1116,6 +1209,7 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
     if (h->scheme == OCI_TIME_BE) launches += 2 + main_iters;  // begin, iterations, commit
     else if (!si && h->solver == OCI_SOLVER_DENSE) launches += 2 + 2 * main_iters;  // begin, rhs + out per iteration, commit
     else if (si) launches += 3 + main_iters * (h->sweep == OCI_SWEEP_SCAN ? 4 : 2);  // begin, prep, sweep + cells, commit
+    else if (halo_graph) launches += 6;  // begin, entry, BF16 loop, exit, loop, commit
     else if (h->use_loop) launches += 1 + 2 * graph_runs + corrections;  // begin, (loop, commit) per graph run, lifts
     else launches += 2 + body_launches(main_iters) + corrections * (unroll + 1);  // begin, bodies, commit, lifts
     int refined = 0;
@@ -1171,7 +1265,7 @@ int oci_create(const oci_problem *p, oci_handle **out)
     if (J < 1 || N < 2 || N > 256 || (N & 1)) return OCI_EINVAL;
     if (!p->dx || !p->sigma_t || !p->sigma_s) return OCI_EINVAL;
     if (!(p->v > 0.0) || !(p->dt > 0.0) || !std::isfinite(p->dt)) return OCI_EINVAL;
-    if (p->precision != OCI_FP64 && p->precision != OCI_FP32) return OCI_EINVAL;
+    if (p->precision != OCI_FP64 && p->precision != OCI_FP32 && p->precision != OCI_FP32_BF16HALO) return OCI_EINVAL;
     if (p->max_iter < 1 || !(p->tol >= 0.0)) return OCI_EINVAL;
     for (int bc : {p->bc_left, p->bc_right})
         if (bc < OCI_BC_VACUUM || bc > OCI_BC_INCIDENT) return OCI_EINVAL;
@@ -1187,7 +1281,7 @@ int oci_create(const oci_problem *p, oci_handle **out)
     h->J = J;
     h->N = N;
     h->P = N / 2;
-    h->prec = p->precision;
+    h->prec = p->precision == OCI_FP64 ? OCI_FP64 : OCI_FP32;
     h->bcl = p->bc_left;
     h->bcr = p->bc_right;
     h->v = p->v;
@@ -1198,6 +1292,8 @@ int oci_create(const oci_problem *p, oci_handle **out)
     h->cfg.commit_unconverged = 0;
     h->cfg.pause_at = -1;
     h->cfg.stall_iters = 8;
+    h->cfg.halo_switch = 2e-3;  // BF16 rounding (2^-8 relative) leaves the change near 1e-3
+    h->cfg.halo_stall = 2;
     h->cfg.stall_floor = 0.0;  // enabled below for the FP32 path with refinement
     h->cfg.bar_poll_limit = 0;
     h->cfg.bar_shortfall = 0;
@@ -1386,6 +1482,10 @@ int oci_create(const oci_problem *p, oci_handle **out)
     if (!rc) rc = load_state(h, p->psi0);
     if (!rc && cudaMemcpy(h->d_cfg, &h->cfg, sizeof(IterConfig), cudaMemcpyHostToDevice) != cudaSuccess) rc = OCI_ECUDA;
     h->cfg_dev = h->cfg;
+    if (!rc && p->precision == OCI_FP32_BF16HALO) {
+        rc = halo_setup(h);
+        if (!rc) h->halo = OCI_HALO_BF16;
+    }
     if (rc) { oci_destroy(h); return rc; }
     *out = h;
     return OCI_OK;
@@ -1405,6 +1505,9 @@ void oci_destroy(oci_handle *h)
     if (h->graph_lin) cudaGraphDestroy(h->graph_lin);
     if (h->exec_cont) cudaGraphExecDestroy(h->exec_cont);
     if (h->graph_cont) cudaGraphDestroy(h->graph_cont);
+    if (h->exec_oci_h) cudaGraphExecDestroy(h->exec_oci_h);
+    if (h->graph_oci_h) cudaGraphDestroy(h->graph_oci_h);
+    if (h->hface_mem) cudaFree(h->hface_mem);
     if (h->nn_mem) cudaFree(h->nn_mem);
     dense_free(h);
     if (h->scan_mem) cudaFree(h->scan_mem);
@@ -1448,6 +1551,18 @@ int oci_set_wait_limits(oci_handle *h, uint32_t poll_limit, int32_t barrier_shor
     if (!h || barrier_shortfall < 0) return OCI_EINVAL;
     h->cfg.bar_poll_limit = poll_limit;
     h->cfg.bar_shortfall = barrier_shortfall;
+    return OCI_OK;
+}
+
+int oci_set_halo(oci_handle *h, int32_t halo)
+{
+    if (!h || (halo != OCI_HALO_FP32 && halo != OCI_HALO_BF16)) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    if (halo == OCI_HALO_BF16 && !h->exec_oci_h) {
+        const int rc = halo_setup(h);
+        if (rc) return rc;
+    }
+    h->halo = halo;
     return OCI_OK;
 }
 
@@ -1621,6 +1736,37 @@ int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_la
                                               h->cells_smem, h->stream));
             return OCI_OK;
         };
+        if (h->halo == OCI_HALO_BF16) {
+            // the BF16 phase's loop, after its entry iteration (which it needs for its faces)
+            auto entry = [&]() -> int {
+                KParams<float> pe = make_params<float>(h, 0, 0);
+                void *ea[] = {&pe};
+                CK(h, cudaLaunchKernel(h->hk.entry, dim3(h->cells_grid), dim3(h->cells_block), ea, h->cells_smem,
+                                       h->stream));
+                CK(h, cudaMemsetAsync(h->loop_bar, 0, sizeof(unsigned), h->stream));
+                return OCI_OK;
+            };
+            auto hlaunch = [&](int n) -> int {
+                h->loop_fixed = n + 1;  // the entry iteration counts
+                KParams<float> pl = make_params<float>(h, 0, 0);
+                h->loop_fixed = 0;
+                void *la[] = {&pl};
+                CK(h, cudaLaunchCooperativeKernel(h->hk.loop, dim3(h->cells_grid), dim3(h->cells_block), la,
+                                                  h->cells_smem, h->stream));
+                return OCI_OK;
+            };
+            if ((rc = prepare()) || (rc = entry()) || (rc = hlaunch(2)) || (rc = prepare()) || (rc = entry())) return rc;
+            CK(h, cudaEventRecord(h->ev0, h->stream));
+            if ((rc = hlaunch(n_iter))) return rc;
+            CK(h, cudaEventRecord(h->ev1, h->stream));
+            CK(h, cudaEventSynchronize(h->ev1));
+            float ms = 0.f;
+            CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+            *seconds_per_launch = ms * 1e-3 / n_iter;
+            if ((rc = set_device_cfg(h, h->cfg))) return rc;
+            h->guess_valid = false;
+            return OCI_OK;
+        }
         if ((rc = prepare()) || (rc = launch(2)) || (rc = prepare())) return rc;  // warm-up
         CK(h, cudaEventRecord(h->ev0, h->stream));
         if ((rc = launch(n_iter))) return rc;

@@ -31,6 +31,7 @@
 // For a symmetric quadrature M is real in the C sense (M = M_r (x) I_2), so the
 // capacitance solve is two 2x2 real systems sharing one inverse K.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,7 +44,8 @@ template <typename R> struct __align__(16) r4 { R x, y, z, w; };
 struct __align__(16) kmat { double k00, k01, k10, k11; };
 
 enum : int { BC_VACUUM = 0, BC_REFLECT = 1, BC_INCIDENT = 2 };
-enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NAN = 3, ST_GUARD = 4, ST_TIMEOUT = 5, ST_STALL = 6 };
+enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NAN = 3, ST_GUARD = 4, ST_TIMEOUT = 5, ST_STALL = 6,
+             ST_SWITCH = 7 };  // ST_SWITCH: the BF16-halo phase of a step ended, FP32 iterations follow
 // k_cells modes (M_LIN: correction equation of the FP32 refinement, staged kernel only)
 enum : int { M_OCI = 0, M_SI = 1, M_LIN = 2 };
 // k_percell modes
@@ -73,6 +75,8 @@ struct IterConfig {
     double stall_floor;  // ... once the relative change is below this (0 disables)
     unsigned bar_poll_limit;  // grid-barrier polls before a timeout (0: kWaitLimit)
     int bar_shortfall;        // arrivals the grid barrier waits for beyond the grid (diagnostic; 0)
+    double halo_switch;       // BF16-halo phase: leave it once the relative change is below this ...
+    int halo_stall;           // ... or after this many iterations without a 10% improvement
 };
 
 
@@ -121,6 +125,19 @@ __device__ __forceinline__ r2<double> ld2(const r2<double> *p)
     return {v.x, v.y};
 }
 template <typename R> __device__ __forceinline__ void st2(r2<R> *p, R x, R y) { *p = r2<R>{x, y}; }
+
+// BF16 storage of a face pair (the (k, k+1/2) values of one ordinate at one
+// face) in one 32-bit word: x in the low half, y in the high half, rounded to
+// nearest even.  Widening is exact (a bf16 is the upper half of a float).
+__device__ __forceinline__ unsigned pack_bf16x2(float x, float y)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(x, y);
+    return *reinterpret_cast<const unsigned *>(&v);
+}
+__device__ __forceinline__ r2<float> unpack_bf16x2(unsigned u)
+{
+    return r2<float>{__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u)};
+}
 template <typename R> __device__ __forceinline__ void st4(r4<R> *p, R x, R y, R z, R w) { *p = r4<R>{x, y, z, w}; }
 
 // Complex entries of A_{+mu}^{-1} for one (material, pair).
@@ -257,6 +274,10 @@ struct KParams {
     double *loop_partials;
     unsigned *loop_bar;
     int loop_fixed;
+    // BF16-halo phase of the FP32 OCI iteration: the face buffers as bf16 pairs
+    // (pack_bf16x2), same layout and ping-pong parity as faceP / faceM
+    unsigned *hfP[2];
+    unsigned *hfM[2];
 };
 
 // Reduce V values per lane (s with compensation e) over the LPC lanes of a
@@ -358,9 +379,12 @@ __device__ __forceinline__ void block_sum2(double &a, double &b)
 // Last-block finalisation of one iteration: sum the per-block partials in a
 // fixed order, form the relative change of phi, update the state and the
 // graph's loop condition.
+// phase 0: the plain iteration; 1: an iteration that leaves its halo in BF16
+// (never final: ends the BF16 phase with ST_SWITCH instead of converging);
+// 3: the iteration back to FP32 after ST_SWITCH (never final either).
 __device__ __forceinline__ void finalize_iteration(double d2, double p2, double *partials, IterState *st,
                                                    const IterConfig *cfg, int iter, int use_cond,
-                                                   cudaGraphConditionalHandle cond)
+                                                   cudaGraphConditionalHandle cond, int phase = 0)
 {
     __shared__ int is_last;
     block_sum2(d2, p2);
@@ -390,7 +414,16 @@ __device__ __forceinline__ void finalize_iteration(double d2, double p2, double 
         st->d2 = a;
         st->p2 = b;
         st->arrive = 0u;
-        if (st->status == ST_RUNNING) {
+        if (phase != 0 && (st->status == ST_RUNNING || (phase == 3 && st->status == ST_SWITCH))) {
+            int ns = ST_RUNNING;
+            if (!(resid == resid) || !(a == a) || !(b == b) || isinf(b)) ns = ST_NAN;
+            else if (phase == 1 && (resid < cfg->halo_switch || it >= cfg->max_iter - 2)) ns = ST_SWITCH;
+            if (phase == 3) {  // the FP32 iterations start their stall tracking afresh
+                st->stall = 0;
+                st->best = __longlong_as_double(0x7ff0000000000000LL);
+            }
+            st->status = ns;
+        } else if (phase == 0 && st->status == ST_RUNNING) {
             int ns = ST_RUNNING;
             if (!(resid == resid) || !(a == a) || !(b == b) || isinf(b)) ns = ST_NAN;
             else if (resid < cfg->tol) ns = ST_CONVERGED;
@@ -421,12 +454,13 @@ __device__ __forceinline__ void finalize_iteration(double d2, double p2, double 
 // the launch guard, stop the loop when the step is already decided.
 // Returns false when the kernel has nothing to do.
 template <typename R>
-__device__ __forceinline__ bool iteration_prologue(const KParams<R> &p, int &iter, int &base)
+__device__ __forceinline__ bool iteration_prologue(const KParams<R> &p, int &iter, int &base, bool after_switch = false)
 {
     IterState *st = p.st;
     const int status = *(volatile int *)&st->status;
     iter = *(volatile int *)&st->iter;
     base = *(volatile int *)&st->base;
+    if (after_switch) return status == ST_SWITCH;  // the one iteration back to FP32 faces
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // launches while running (a graph body may hold several launches; those
         // after the step ended return at once and are not counted)
@@ -776,7 +810,11 @@ __device__ __forceinline__ int xpose_idx(int l, int v)
     return 32 * l + 4 * (((v >> 2) ^ l ^ (l >> 3)) & 7) + (v & 3);
 }
 
-template <int LPC, int PPL, int CHUNK, int STAGES, int MODE, bool LOOP = false>
+// HALO (OCI only) selects the storage of the face buffers the iteration reads
+// and writes: 0 float pairs in and out; 1 float in, BF16 out (first iteration
+// of the BF16 phase); 2 BF16 in and out (the phase's persistent loop); 3 BF16
+// in, float out (the iteration back to FP32 after ST_SWITCH).
+template <int LPC, int PPL, int CHUNK, int STAGES, int MODE, bool LOOP = false, int HALO = 0>
 __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
 {
     using R = float;
@@ -785,6 +823,10 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
     constexpr int V = 4 * CHUNK;           // partial sums per lane
     constexpr int NOWN = (V * SPW) / 32 > 0 ? (V * SPW) / 32 : 1;  // (segment, value) sums owned per lane
     static_assert(!LOOP || MODE == M_OCI, "the persistent loop runs the OCI iteration only");
+    static_assert(HALO == 0 || MODE == M_OCI, "BF16 faces in the OCI iteration only");
+    static_assert(!LOOP || HALO == 0 || HALO == 2, "the persistent loops keep one face storage");
+    constexpr bool IN_BF = HALO == 2 || HALO == 3, OUT_BF = HALO == 1 || HALO == 2;
+    constexpr unsigned FB = IN_BF ? 4u : 8u;  // bytes per face pair read
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -857,7 +899,7 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
             return;
         }
     } else {
-        if (!iteration_prologue(p, iter, base)) {
+        if (!iteration_prologue(p, iter, base, HALO == 3)) {
             drain_static();
             return;
         }
@@ -896,6 +938,19 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
         phi_t<R> *phw = p.phi[(iter + 1) & 1];
         const r2<R> *fPr = p.faceP[frd], *fMr = p.faceM[frd];
         r2<R> *fPw = p.faceP[fwr], *fMw = p.faceM[fwr];
+        const unsigned *hPr = p.hfP[frd], *hMr = p.hfM[frd];
+        unsigned *hPw = p.hfP[fwr], *hMw = p.hfM[fwr];
+        // incident faces at face index f: the staged copy's source, a boundary read
+        auto face_src_P = [&](size_t f) -> const void * { return IN_BF ? (const void *)(hPr + f * P) : (const void *)(fPr + f * P); };
+        auto face_src_M = [&](size_t f) -> const void * { return IN_BF ? (const void *)(hMr + f * P) : (const void *)(fMr + f * P); };
+        auto face_ld_P = [&](size_t i) -> r2<R> {
+            if constexpr (IN_BF) return unpack_bf16x2(hPr[i]);
+            else return ld2(fPr + i);
+        };
+        auto face_ld_M = [&](size_t i) -> r2<R> {
+            if constexpr (IN_BF) return unpack_bf16x2(hMr[i]);
+            else return ld2(fMr + i);
+        };
 
         auto issue_faces = [&](int i) {  // lane 0: this iteration's incident faces of local chunk i
             if (i >= nmine) return;
@@ -903,10 +958,10 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
             const int nv = J - c0 < CPC ? J - c0 : CPC;
             unsigned char *st = ring + (size_t)stage_of(i) * sbytes;
             unsigned long long *bar = bars + stage_of(i);
-            const unsigned bF = round16(nv * P * 8u);
+            const unsigned bF = round16(nv * P * FB);
             mbar_expect_tx_arrive(bar, 2 * bF);
-            bulk_g2s(st + oP, fPr + (size_t)c0 * P, bF, bar);
-            bulk_g2s(st + oM, fMr + (size_t)(c0 + 1) * P, bF, bar);
+            bulk_g2s(st + oP, face_src_P((size_t)c0), bF, bar);
+            bulk_g2s(st + oM, face_src_M((size_t)c0 + 1), bF, bar);
         };
         auto issue = [&](int i) {  // lane 0: all copies of local chunk i
             if (i >= nmine) return;
@@ -914,11 +969,11 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
             const int nv = J - c0 < CPC ? J - c0 : CPC;
             unsigned char *st = ring + (size_t)stage_of(i) * sbytes;
             unsigned long long *bar = bars + stage_of(i);
-            const unsigned bF = round16(nv * P * 8u), bE = round16(nv * P * 16u), bQ = nv * 16u,
+            const unsigned bF = round16(nv * P * FB), bE = round16(nv * P * 16u), bQ = nv * 16u,
                            bT = round16(nv * 4u);
             mbar_expect_tx_arrive(bar, 2 * bF + bE + bQ + bT);
-            bulk_g2s(st + oP, fPr + (size_t)c0 * P, bF, bar);
-            bulk_g2s(st + oM, fMr + (size_t)(c0 + 1) * P, bF, bar);
+            bulk_g2s(st + oP, face_src_P((size_t)c0), bF, bar);
+            bulk_g2s(st + oM, face_src_M((size_t)c0 + 1), bF, bar);
             bulk_g2s(st + oE, edge_src + (size_t)c0 * P, bE, bar);
             bulk_g2s(st + oQ, p.cellq + c0, bQ, bar);
             bulk_g2s(st + oT, p.mat + c0, bT, bar);
@@ -947,6 +1002,8 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
             }
             const r2<R> *sP = reinterpret_cast<const r2<R> *>(st + oP);
             const r2<R> *sM = reinterpret_cast<const r2<R> *>(st + oM);
+            const unsigned *hsP = reinterpret_cast<const unsigned *>(st + oP);
+            const unsigned *hsM = reinterpret_cast<const unsigned *>(st + oM);
             const r4<R> *sE = reinterpret_cast<const r4<R> *>(st + oE);
             const r4<R> *sQ = reinterpret_cast<const r4<R> *>(st + oQ);
             const int *sT = reinterpret_cast<const int *>(st + oT);
@@ -988,8 +1045,12 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                         const int pp = ls + LPC * t;
                         if (pp >= P) continue;
                         const Coef<R> &a = ac[t];
-                        const r2<R> inP = (!FAST && refl_l && cell == 0) ? ld2(fMr + pp) : sP[cl * P + pp];
-                        const r2<R> inM = (!FAST && refl_r && cell == J - 1) ? ld2(fPr + (size_t)J * P + pp) : sM[cl * P + pp];
+                        const r2<R> inP = (!FAST && refl_l && cell == 0)
+                                              ? face_ld_M((size_t)pp)
+                                              : (IN_BF ? unpack_bf16x2(hsP[cl * P + pp]) : sP[cl * P + pp]);
+                        const r2<R> inM = (!FAST && refl_r && cell == J - 1)
+                                              ? face_ld_P((size_t)J * P + pp)
+                                              : (IN_BF ? unpack_bf16x2(hsM[cl * P + pp]) : sM[cl * P + pp]);
                         r4<R> *slot = const_cast<r4<R> *>(sE) + cl * P + pp;  // this lane's own (cell, pair) slot
                         const r4<R> pe = *slot;                               // psi_{k-1/2} (M_LIN: r0)
                         PairRhs<R> u = MODE == M_LIN ? PairRhs<R>{0, 0, 0, 0, 0, 0, 0, 0} : pair_rhs_fixed(qd, ce, pe);
@@ -1119,7 +1180,10 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
                     const R oh = yo.y + (a.ur * Fkr + a.ui * Fkl + a.vr * Fhr + a.vi * Fhl);
                     const R mk = yo.z + (a.pr * Fkl + a.pi * Fkr + a.rr * Fhl + a.ri * Fhr);
                     const R mh = yo.w + (a.ur * Fkl + a.ui * Fkr + a.vr * Fhl + a.vi * Fhr);
-                    if (PING) {
+                    if (OUT_BF) {
+                        hPw[(size_t)(cell + 1) * P + pp] = pack_bf16x2(ok, oh);
+                        hMw[(size_t)cell * P + pp] = pack_bf16x2(mk, mh);
+                    } else if (PING) {
                         st2(fPw + (size_t)(cell + 1) * P + pp, ok, oh);
                         st2(fMw + (size_t)cell * P + pp, mk, mh);
                     } else {
@@ -1141,7 +1205,8 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
             for (int k = broke_at; k < last; ++k) (void)mbar_wait(bars + stage_of(k), parity_of(k));
         }
         if constexpr (!LOOP) {
-            finalize_iteration((double)accf_d2, (double)accf_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond);
+            finalize_iteration((double)accf_d2, (double)accf_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond,
+                               HALO == 1 ? 1 : (HALO == 3 ? 3 : 0));
             return;
         } else {
             rp += nmine;
@@ -1183,9 +1248,20 @@ __global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
             if (fault) ns = ST_TIMEOUT;
             else if (!(resid == resid) || !(a == a) || !(b == b) || isinf(b)) ns = ST_NAN;
             else if (fixed_left > 0) ns = it >= fixed_left ? ST_MAXITER : ST_RUNNING;  // timing: a fixed count
+            else if (HALO == 2) {
+                // BF16 phase: never final; ends at the switch threshold, near the
+                // iteration limit, or once BF16 rounding stops the change falling
+                if (resid < cfg->halo_switch || it >= cfg->max_iter - 2) ns = ST_SWITCH;
+                else if (resid < 0.9 * best) {
+                    best = resid;
+                    stall = 0;
+                } else if (++stall >= cfg->halo_stall) {
+                    ns = ST_SWITCH;
+                }
+            }
             else if (resid < cfg->tol) ns = ST_CONVERGED;
             else if (it >= cfg->max_iter) ns = ST_MAXITER;
-            if (ns == ST_RUNNING && fixed_left == 0 && cfg->stall_floor > 0.0) {
+            if (HALO == 0 && ns == ST_RUNNING && fixed_left == 0 && cfg->stall_floor > 0.0) {
                 if (cfg->stall_iters < 0) {
                     if (resid < cfg->stall_floor) ns = ST_STALL;
                 } else if (resid < 0.9 * best) {

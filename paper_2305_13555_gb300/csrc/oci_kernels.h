@@ -29,8 +29,16 @@ struct KernelSet {
     int cells_per_warp_pc;   // cells per warp of k_percell (32 / LPC)
 };
 
+// The staged FP32 OCI iteration with BF16 face storage (k_cells_tma HALO 1-3).
+struct HaloKernels {
+    const void *entry;  // one iteration, float faces in, BF16 out
+    const void *loop;   // persistent loop, BF16 in and out, until ST_SWITCH
+    const void *exit;   // one iteration, BF16 in, float out
+};
+
 // Returns false if (lpc, ppl) has no instantiation.
 bool kernel_set_f32(int lpc, int ppl, KernelSet *out);
+bool kernel_set_bf16(int lpc, int ppl, HaloKernels *out);
 // Shared-memory bytes per stage of the staged FP32 kernels for P pairs.
 unsigned tma_stage_bytes(int lpc, int ppl, int P);
 bool kernel_set_f64(int lpc, int ppl, KernelSet *out);

@@ -101,4 +101,5 @@ def test_null_handle_calls(lib):
     assert lib.si_step(None, None) == pkg.OCI_EINVAL
     assert lib.oci_fluxes(None, None) == pkg.OCI_EINVAL
     assert lib.oci_set_iteration(None, 1e-8, 10, 0) == pkg.OCI_EINVAL
+    assert lib.oci_set_halo(None, pkg.OCI_HALO_BF16) == pkg.OCI_EINVAL
     lib.oci_destroy(None)
