@@ -81,6 +81,9 @@ def read_traffic(key):
     return None
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is the roofline's peak)
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -237,6 +240,7 @@ def run_ours(args, rank, world):
     traffic = read_traffic(f"{args.workload}_{args.precision}_S{N}_J{J}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+                "nominal_peak_gbs": NOMINAL_HBM_GBS, "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                 "kernel": ("k_cells_tma<OCI> persistent loop (figures per iteration; 50 iterations per launch)"
                            if args.precision == "fp32" else "k_cells<double, OCI> (one launch per iteration)"),
                 "iteration_us": round(t_launch * 1e6, 3), "algorithmic_bytes_per_iteration": abytes}

@@ -749,7 +749,9 @@ __global__ void k_halo_bounds(const r2<float> *fP0, const r2<float> *fMJ, int P,
 
 int halo_setup(oci_handle *h)
 {
-    if (h->prec != OCI_FP32 || !h->use_loop || h->P % 4 != 0 || !ocik::kernel_set_bf16(h->lpc, h->ppl, &h->hk))
+    // the BF16 kernels are instantiated for 8-row chunks and a 2-stage ring only
+    if (h->prec != OCI_FP32 || !h->use_loop || h->P % 4 != 0 || h->ks.tma_chunk != 8 || h->ks.tma_stages != 2 ||
+        !ocik::kernel_set_bf16(h->lpc, h->ppl, &h->hk))
         return OCI_EINVAL;
     int sms = 0, per_sm = 0;
     for (const void *fn : {h->hk.entry, h->hk.loop, h->hk.exit})
@@ -1348,10 +1350,10 @@ int oci_create(const oci_problem *p, oci_handle **out)
             delete h;
             return OCI_ECUDA;
         }
-        const unsigned sb = ocik::tma_stage_bytes(h->lpc, h->ppl, P);
+        const unsigned sb = ocik::tma_stage_bytes(h->lpc, h->ks.tma_chunk, P);
         const unsigned per_warp = (unsigned)h->ks.tma_stages * (sb + 8u) + ocik::kXposeBytes;
         int warps = (int)((unsigned)(smem_optin - 2048) / per_warp);
-        if (warps > 12) warps = 12;
+        if (warps > h->ks.tma_max_warps) warps = h->ks.tma_max_warps;
         if (warps >= 1) {
             h->staged = true;
             h->cells_oci = h->ks.cells_oci_tma;

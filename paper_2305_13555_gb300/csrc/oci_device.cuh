@@ -814,8 +814,14 @@ __device__ __forceinline__ int xpose_idx(int l, int v)
 // and writes: 0 float pairs in and out; 1 float in, BF16 out (first iteration
 // of the BF16 phase); 2 BF16 in and out (the phase's persistent loop); 3 BF16
 // in, float out (the iteration back to FP32 after ST_SWITCH).
+// Threads per block of the staged kernel: the rings of 8-row chunks fit 11
+// warps in shared memory, those of 4-row chunks of one pair per lane 18 (at
+// S_64 that layout measured 27 % slower per iteration than 8-row chunks with
+// 11 warps: the warps' own instruction-level parallelism matters more).
+__host__ __device__ constexpr int tma_max_threads(int chunk, int ppl) { return (chunk >= 8 || ppl > 1) ? 384 : 576; }
+
 template <int LPC, int PPL, int CHUNK, int STAGES, int MODE, bool LOOP = false, int HALO = 0>
-__global__ void __launch_bounds__(384, 1) k_cells_tma(const KParams<float> p)
+__global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(const KParams<float> p)
 {
     using R = float;
     constexpr int SPW = 32 / LPC;

@@ -22,6 +22,8 @@ struct KernelSet {
     const void *cells_oci_loop; // k_cells_tma<M_OCI, persistent loop> or nullptr
     const void *cells_si_tma;   // k_cells_tma<M_SI>
     int tma_stages;             // ring depth of the staged kernels
+    int tma_chunk;              // cell rows per chunk of the staged kernels
+    int tma_max_warps;          // their launch bound, in warps
     const void *cells_lin_tma;  // k_cells_tma<M_LIN> (FP32 refinement) or nullptr
     const void *commit_lin;     // k_percell<C_COMMIT_LIN>
     const void *refine;         // k_refine_residual
@@ -39,8 +41,9 @@ struct HaloKernels {
 // Returns false if (lpc, ppl) has no instantiation.
 bool kernel_set_f32(int lpc, int ppl, KernelSet *out);
 bool kernel_set_bf16(int lpc, int ppl, HaloKernels *out);
-// Shared-memory bytes per stage of the staged FP32 kernels for P pairs.
-unsigned tma_stage_bytes(int lpc, int ppl, int P);
+// Shared-memory bytes per stage of the staged FP32 kernels for P pairs and
+// chunks of `chunk` cell rows.
+unsigned tma_stage_bytes(int lpc, int chunk, int P);
 bool kernel_set_f64(int lpc, int ppl, KernelSet *out);
 
 }  // namespace ocik

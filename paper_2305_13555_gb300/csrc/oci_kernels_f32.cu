@@ -35,6 +35,8 @@ static void fill(KernelSet *k)
         k->cells_si_tma = (const void *)&k_cells_tma<LPC, PPL, CHUNK, kStages, M_SI>;
         k->cells_lin_tma = (const void *)&k_cells_tma<LPC, PPL, CHUNK, kStages, M_LIN>;
         k->tma_stages = kStages;
+        k->tma_chunk = CHUNK;
+        k->tma_max_warps = tma_max_threads(CHUNK, PPL) / 32;
     }
     k->commit_lin = (const void *)&k_percell<float, LPC, PPL, C_COMMIT_LIN>;
     k->refine = (const void *)&k_refine_residual<LPC, PPL>;
@@ -66,9 +68,8 @@ bool kernel_set_f32(int lpc, int ppl, KernelSet *out)
     }
 }
 
-unsigned tma_stage_bytes(int lpc, int ppl, int P)
+unsigned tma_stage_bytes(int lpc, int chunk, int P)
 {
-    const int chunk = ppl >= 4 ? 4 : 8;
     const unsigned cpc = (unsigned)(chunk * (32 / lpc));
     return round16(cpc * P * 8u) * 2u + round16(cpc * P * 16u) + round16(cpc * 16u) + round16(cpc * 4u);
 }
