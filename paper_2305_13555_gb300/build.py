@@ -14,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboci_gb300.so")
-SOURCES = ["oci_api.cu", "oci_kernels_f32.cu", "oci_kernels_bf16.cu", "oci_kernels_f64.cu", "nn_kernels.cu",
-           "oci_dense.cu"]
+SOURCES = ["oci_api.cu", "oci_kernels_f32.cu", "oci_kernels_bf16.cu", "oci_kernels_async.cu", "oci_kernels_f64.cu",
+           "nn_kernels.cu", "oci_dense.cu"]
 HEADERS = ["oci_device.cuh", "oci_be.cuh", "oci_kernels.h", "oci_dense.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -98,7 +98,7 @@ struct oci_handle {
     // device memory (one allocation)
     void *d_base = nullptr;
     size_t d_bytes = 0;
-    void *faceP[2] = {nullptr, nullptr}, *faceM[2] = {nullptr, nullptr};
+    void *faceP[3] = {nullptr, nullptr, nullptr}, *faceM[3] = {nullptr, nullptr, nullptr};  // [2]: barrier-free loop
     void *psi_edge = nullptr, *g = nullptr, *cellq = nullptr, *tab = nullptr, *matpar = nullptr, *muw = nullptr,
          *refl = nullptr;
     int *d_mat = nullptr;
@@ -179,6 +179,18 @@ struct oci_handle {
     unsigned *hfP[2] = {nullptr, nullptr}, *hfM[2] = {nullptr, nullptr};
     cudaGraph_t graph_oci_h = nullptr;
     cudaGraphExec_t exec_oci_h = nullptr;
+    // barrier-free persistent OCI loop (staged FP32, S_32 / S_64 / S_128): its
+    // kernel, third face buffer pair, sync block + per-warp counts (zeroed per
+    // launch) and per-warp partials; the barrier loop's graph kept for the corrector
+    bool use_async = false;
+    const void *cells_async = nullptr;
+    void *async_mem = nullptr;
+    ocik::AsyncSync *as = nullptr;
+    unsigned *as_done = nullptr;
+    double *as_part = nullptr;
+    size_t as_zero_bytes = 0;
+    cudaGraph_t graph_oci_bar = nullptr;
+    cudaGraphExec_t exec_oci_bar = nullptr;
 };
 
 namespace {
@@ -222,6 +234,11 @@ KParams<R> make_params(const oci_handle *h, int use_cond, cudaGraphConditionalHa
         p.faceM[b] = (r2<R> *)h->faceM[b];
         p.phi[b] = (ocik::phi_t<R> *)h->phi[b];
     }
+    p.faceP[2] = (r2<R> *)h->faceP[2];
+    p.faceM[2] = (r2<R> *)h->faceM[2];
+    p.as = h->as;
+    p.as_done = h->as_done;
+    p.as_part = h->as_part;
     p.psi_edge = (r4<R> *)h->psi_edge;
     p.g = (r4<R> *)h->g;
     p.refl = (r2<R> *)h->refl;
@@ -476,7 +493,7 @@ int upload_boundaries(oci_handle *h, const double *bl, const double *br)
     std::vector<double> l((size_t)P * 2, 0.0), r((size_t)P * 2, 0.0);
     if (h->bcl == OCI_BC_INCIDENT && bl) std::memcpy(l.data(), bl, sizeof(double) * P * 2);
     if (h->bcr == OCI_BC_INCIDENT && br) std::memcpy(r.data(), br, sizeof(double) * P * 2);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < (h->faceP[2] ? 3 : 2); ++b) {
         int rc = upload_real(h, h->faceP[b], l);  // face 0 = first P pairs
         if (rc) return rc;
         rc = upload_real(h, (char *)h->faceM[b] + (size_t)J * P * 2 * rs, r);  // face J
@@ -552,7 +569,7 @@ int add_loop(oci_handle *h, cudaGraph_t g, const cudaGraphNode_t *dep, cudaGraph
 // Step graph: begin -> [si_prep] -> WHILE { [march ->] cells } -> commit
 // (OCI with the persistent loop: begin -> loop -> commit).
 template <typename R>
-int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout)
+int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout, bool bar_loop = false)
 {
     cudaGraph_t g;
     CK(h, cudaGraphCreate(&g, 0));
@@ -570,6 +587,27 @@ int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout
     int rc = add_kernel(h, g, &n_begin, nullptr, 0, (const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st);
     if (rc) return rc;
     n_prev = n_begin;
+    if (!si && h->use_loop && h->use_async && !bar_loop) {
+        // barrier-free loop: zero its sync block, one cooperative launch that
+        // iterates and ends the step
+        cudaMemsetParams mp{};
+        mp.dst = h->as;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = h->as_zero_bytes / 4;
+        mp.height = 1;
+        cudaGraphNode_t n_zero, n_loop;
+        CK(h, cudaGraphAddMemsetNode(&n_zero, g, &n_prev, 1, &mp));
+        rc = add_kernel(h, g, &n_loop, &n_zero, 1, h->cells_async, dim3(h->cells_grid), dim3(h->cells_block), a_plain,
+                        h->cells_smem);
+        if (rc) return rc;
+        cudaLaunchAttributeValue v{};
+        v.cooperative = 1;
+        CK(h, cudaGraphKernelNodeSetAttribute(n_loop, cudaLaunchAttributeCooperative, &v));
+        CK(h, cudaGraphInstantiate(eout, g, 0));
+        *gout = g;
+        return OCI_OK;
+    }
     if (!si && h->use_loop) {
         cudaGraphNode_t n_loop;
         rc = add_loop(h, g, &n_prev, &n_loop, a_plain);
@@ -896,7 +934,8 @@ int refine_step(oci_handle *h, IterState *s)
         int rc = build_lin_graph(h);
         if (rc) return rc;
     }
-    const int fb = (s->base + s->iter) & 1;
+    // the latest iterate: rotated through three buffers by the barrier-free loop
+    const int fb = s->rot3 ? s->cur_face : (s->base + s->iter) & 1;
     const size_t fbytes = face_bytes(h);
     CK(h, cudaMemcpyAsync(h->ref_h0P, h->faceP[fb], fbytes, cudaMemcpyDeviceToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->ref_h0M, h->faceM[fb], fbytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -1130,7 +1169,7 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
     const int unroll = (h->staged && h->pdl_graph) ? kUnroll : 1;  // iteration launches per WHILE body
     auto body_launches = [&](int iters) { return unroll * ((iters + unroll - 1) / unroll); };
     int corrections = 0, graph_runs = 0;
-    bool halo_graph = false;
+    bool halo_graph = false, async_run = false;
     CK(h, cudaEventRecord(h->ev0, h->stream));
     if (nn) {
         rc = nn_guess(h);
@@ -1163,7 +1202,12 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         bool correcting = true;
         h->cfg.pause_at = k;
         if ((rc = upload_cfg(h))) return rc;
-        CK(h, cudaGraphLaunch(h->exec_oci, h->stream));
+        // pauses need the barrier loop (its iterate stays in the two-buffer order)
+        if (h->use_async && !h->exec_oci_bar) {
+            rc = build_graph<float>(h, false, &h->graph_oci_bar, &h->exec_oci_bar, true);
+            if (rc) return rc;
+        }
+        CK(h, cudaGraphLaunch(h->use_async ? h->exec_oci_bar : h->exec_oci, h->stream));
         ++graph_runs;
         for (;;) {
             if ((rc = read_state(h, &s))) return rc;
@@ -1202,6 +1246,7 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         if ((rc = set_device_cfg(h, c))) return rc;
         // BF16 halo: entry, BF16 loop and exit take at least three iterations
         halo_graph = !si && h->halo == OCI_HALO_BF16 && h->exec_oci_h && h->cfg.max_iter >= 4;
+        async_run = !si && !halo_graph && h->use_async;
         CK(h, cudaGraphLaunch(halo_graph ? h->exec_oci_h : (si ? h->exec_si : h->exec_oci), h->stream));
         ++graph_runs;
     }
@@ -1212,6 +1257,7 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
     else if (!si && h->solver == OCI_SOLVER_DENSE) launches += 2 + 2 * main_iters;  // begin, rhs + out per iteration, commit
     else if (si) launches += 3 + main_iters * (h->sweep == OCI_SWEEP_SCAN ? 4 : 2);  // begin, prep, sweep + cells, commit
     else if (halo_graph) launches += 6;  // begin, entry, BF16 loop, exit, loop, commit
+    else if (async_run) launches += 2;   // begin, the barrier-free loop (which ends the step)
     else if (h->use_loop) launches += 1 + 2 * graph_runs + corrections;  // begin, (loop, commit) per graph run, lifts
     else launches += 2 + body_launches(main_iters) + corrections * (unroll + 1);  // begin, bodies, commit, lifts
     int refined = 0;
@@ -1395,6 +1441,20 @@ int oci_create(const oci_problem *p, oci_handle **out)
                 h->cells_grid <= sms * per_sm_loop) {
                 h->cells_loop = h->ks.cells_oci_loop;
                 h->use_loop = true;
+                // its barrier-free variant (S_32, S_64, S_128; measured slower than the
+                // barrier loop on GB300, so only on request)
+                const void *fa = ocik::kernel_async_loop(h->lpc, h->ppl);
+                int per_sm_async = 0;
+                const char *ea = std::getenv("OCI_ASYNC_LOOP");
+                if (fa && h->ks.tma_chunk == 8 && h->ks.tma_stages == 2 && ea && ea[0] == '1' &&
+                    cudaFuncSetAttribute(fa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->cells_smem) ==
+                        cudaSuccess &&
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_async, fa, h->cells_block, h->cells_smem) ==
+                        cudaSuccess &&
+                    h->cells_grid <= sms * per_sm_async) {
+                    h->cells_async = fa;
+                    h->use_async = true;
+                }
             }
             (void)cudaGetLastError();
         }
@@ -1468,6 +1528,27 @@ int oci_create(const oci_problem *p, oci_handle **out)
             }
         }
     }
+    if (h->use_async) {
+        // third face buffer pair, sync block + per-warp completion counts, per-warp partials
+        const size_t tw = (size_t)h->cells_grid * (size_t)(h->cells_block / 32);
+        const size_t fa = (face + 256 + 255) & ~(size_t)255;
+        h->as_zero_bytes = (sizeof(ocik::AsyncSync) + tw * 4 + 15) & ~(size_t)15;
+        const size_t zb = (h->as_zero_bytes + 255) & ~(size_t)255;
+        if (cudaMalloc(&h->async_mem, 2 * fa + zb + 4 * tw * 3 * sizeof(double)) != cudaSuccess) {
+            oci_destroy(h);
+            return OCI_ENOMEM;
+        }
+        char *a = (char *)h->async_mem;
+        h->faceP[2] = a;
+        h->faceM[2] = a + fa;
+        h->as = (ocik::AsyncSync *)(a + 2 * fa);
+        h->as_done = (unsigned *)(a + 2 * fa + sizeof(ocik::AsyncSync));
+        h->as_part = (double *)(a + 2 * fa + zb);
+        if (cudaMemsetAsync(h->async_mem, 0, 2 * fa + zb, h->stream) != cudaSuccess) {
+            oci_destroy(h);
+            return OCI_ECUDA;
+        }
+    }
     if (cudaMallocHost(&h->h_st, sizeof(IterState)) != cudaSuccess) { oci_destroy(h); return OCI_ENOMEM; }
     if (cudaMemsetAsync(h->d_base, 0, total, h->stream) != cudaSuccess ||
         cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
@@ -1508,6 +1589,9 @@ void oci_destroy(oci_handle *h)
     if (h->exec_cont) cudaGraphExecDestroy(h->exec_cont);
     if (h->graph_cont) cudaGraphDestroy(h->graph_cont);
     if (h->exec_oci_h) cudaGraphExecDestroy(h->exec_oci_h);
+    if (h->exec_oci_bar) cudaGraphExecDestroy(h->exec_oci_bar);
+    if (h->graph_oci_bar) cudaGraphDestroy(h->graph_oci_bar);
+    if (h->async_mem) cudaFree(h->async_mem);
     if (h->graph_oci_h) cudaGraphDestroy(h->graph_oci_h);
     if (h->hface_mem) cudaFree(h->hface_mem);
     if (h->nn_mem) cudaFree(h->nn_mem);
@@ -1727,15 +1811,16 @@ int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_la
         auto prepare = [&]() -> int {
             CK(h, cudaLaunchKernel((const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st, 0, h->stream));
             CK(h, cudaMemsetAsync(h->loop_bar, 0, sizeof(unsigned), h->stream));
+            if (h->use_async) CK(h, cudaMemsetAsync(h->as, 0, h->as_zero_bytes, h->stream));
             return OCI_OK;
         };
-        auto launch = [&](int n) -> int {
+        auto launch = [&](int n) -> int {  // the loop a step runs (barrier-free where available)
             h->loop_fixed = n;
             KParams<float> pl = make_params<float>(h, 0, 0);
             h->loop_fixed = 0;
             void *la[] = {&pl};
-            CK(h, cudaLaunchCooperativeKernel(h->cells_loop, dim3(h->cells_grid), dim3(h->cells_block), la,
-                                              h->cells_smem, h->stream));
+            CK(h, cudaLaunchCooperativeKernel(h->use_async ? h->cells_async : h->cells_loop, dim3(h->cells_grid),
+                                              dim3(h->cells_block), la, h->cells_smem, h->stream));
             return OCI_OK;
         };
         if (h->halo == OCI_HALO_BF16) {

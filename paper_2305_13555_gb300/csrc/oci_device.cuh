@@ -64,6 +64,23 @@ struct IterState {
     double resid;      // last relative change of phi
     double d2, p2;     // sum (dphi)^2, sum phi^2 of the last iteration
     double best;       // smallest relative change since the last 10% improvement
+    int rot3;          // this step's iterations rotated through three face buffers
+    int cur_face;      // ... and the buffer holding the latest iterate
+};
+
+// Barrier-free persistent loop (k_cells_tma ASYNC): per-iteration arrival
+// counters and decisions, in a ring of four iterations.  Zeroed before each
+// launch together with the per-warp completion counts that follow it.
+struct AsyncRec {
+    double resid, d2, p2, best;
+    int status, stall, pad0, pad1;
+};
+struct AsyncSync {
+    unsigned cnt[4];      // warps that finished iteration rep (slot rep & 3), cumulative
+    unsigned tag[4];      // rep + 1 once the decision of iteration rep is in rec[rep & 3]
+    unsigned exit_bar;    // blocks that reached the end of the launch
+    unsigned pad[7];
+    AsyncRec rec[4];
 };
 
 struct IterConfig {
@@ -125,6 +142,29 @@ __device__ __forceinline__ r2<double> ld2(const r2<double> *p)
     return {v.x, v.y};
 }
 template <typename R> __device__ __forceinline__ void st2(r2<R> *p, R x, R y) { *p = r2<R>{x, y}; }
+
+// Loads through L2 only (data another SM may have written during the launch).
+__device__ __forceinline__ r2<float> ldcg2(const r2<float> *p)
+{
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ r2<double> ldcg2(const r2<double> *p)
+{
+    const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ r4<float> ldcg4(const r4<float> *p)
+{
+    const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ r4<double> ldcg4(const r4<double> *p)
+{
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
 
 // BF16 storage of a face pair (the (k, k+1/2) values of one ordinate at one
 // face) in one 32-bit word: x in the low half, y in the high half, rounded to
@@ -251,8 +291,8 @@ struct KParams {
     const r2<R> *matpar;   // [n_mat]: (e, s)
     const kmat *matK;      // [n_mat]
     const r2<R> *muw;      // [P]: (mu, w)
-    r2<R> *faceP[2];
-    r2<R> *faceM[2];
+    r2<R> *faceP[3];       // [2]: third buffer of the barrier-free loop (or null)
+    r2<R> *faceM[3];
     r4<R> *psi_edge;
     r4<R> *g;
     r2<R> *refl;           // [P] SI: lagged mirror flux at a reflecting right face
@@ -278,6 +318,11 @@ struct KParams {
     // (pack_bf16x2), same layout and ping-pong parity as faceP / faceM
     unsigned *hfP[2];
     unsigned *hfM[2];
+    // barrier-free persistent loop: sync block, per-warp completion counts
+    // (iterations of this launch), per-block partials [4][blocks][3]
+    AsyncSync *as;
+    unsigned *as_done;
+    double *as_part;
 };
 
 // Reduce V values per lane (s with compensation e) over the LPC lanes of a
@@ -730,6 +775,25 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, u
     return s_ok != 0;
 }
 
+// Thread 0 alone meets the grid (the block's own writes were ordered before
+// it by a block barrier): release-arrive on count, then poll (bounded) until
+// target arrivals; false when the limit expired.
+__device__ __forceinline__ bool grid_arrive_wait(unsigned *count, unsigned target, unsigned limit)
+{
+    __threadfence();
+    atomicAdd(count, 1u);
+    bool ok = false;
+    for (unsigned it = 0; it < limit; ++it) {
+        if (ld_acquire_u32(count) >= target) {
+            ok = true;
+            break;
+        }
+        __nanosleep(32);
+    }
+    __threadfence();
+    return ok;
+}
+
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
 {
     const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
@@ -810,6 +874,78 @@ __device__ __forceinline__ int xpose_idx(int l, int v)
     return 32 * l + 4 * (((v >> 2) ^ l ^ (l >> 3)) & 7) + (v & 3);
 }
 
+// Decision of the persistent loops after iteration it (1-based) from the grid
+// sums a = sum (dphi)^2, b = sum phi^2: the next state and the stall tracking.
+// halo2: the BF16 phase (never final; ST_SWITCH instead).
+__device__ __forceinline__ int loop_decision(double a, double b, bool fault, int it, int fixed_left, bool halo2,
+                                             const IterConfig *cfg, int &stall, double &best, double &resid)
+{
+    if (b > 0.0) resid = sqrt(a / b);
+    else resid = (a == 0.0) ? 0.0 : __longlong_as_double(0x7ff0000000000000LL);
+    int ns = ST_RUNNING;
+    if (fault) ns = ST_TIMEOUT;
+    else if (!(resid == resid) || !(a == a) || !(b == b) || isinf(b)) ns = ST_NAN;
+    else if (fixed_left > 0) ns = it >= fixed_left ? ST_MAXITER : ST_RUNNING;  // timing: a fixed count
+    else if (halo2) {
+        // BF16 phase: never final; ends at the switch threshold, near the
+        // iteration limit, or once BF16 rounding stops the change falling
+        if (resid < cfg->halo_switch || it >= cfg->max_iter - 2) ns = ST_SWITCH;
+        else if (resid < 0.9 * best) {
+            best = resid;
+            stall = 0;
+        } else if (++stall >= cfg->halo_stall) {
+            ns = ST_SWITCH;
+        }
+    }
+    else if (resid < cfg->tol) ns = ST_CONVERGED;
+    else if (it >= cfg->max_iter) ns = ST_MAXITER;
+    if (!halo2 && ns == ST_RUNNING && fixed_left == 0 && cfg->stall_floor > 0.0) {
+        if (cfg->stall_iters < 0) {
+            if (resid < cfg->stall_floor) ns = ST_STALL;
+        } else if (resid < 0.9 * best) {
+            best = resid;
+            stall = 0;
+        } else if (++stall >= cfg->stall_iters && resid < cfg->stall_floor) {
+            ns = ST_STALL;
+        }
+    }
+    return ns;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *a, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *a)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+// Barrier-free loop, lane 0 before iteration rep (>= 1) of the launch: wait
+// until both ring neighbours finished iteration rep-1 and the decision of
+// iteration rep-2 is known.  Returns 1 to go on, 2 when a known decision ends
+// the step, 0 when the wait limit expired.
+__device__ __forceinline__ int async_wait(const AsyncSync *as, const unsigned *done, int left, int right, int rep,
+                                          unsigned limit)
+{
+    for (unsigned it = 0; it < limit; ++it) {
+        if (ld_acquire_u32(&as->tag[(rep - 1) & 3]) == (unsigned)rep)  // decision of rep-1 (every warp finished it)
+            return *(volatile const int *)&as->rec[(rep - 1) & 3].status == ST_RUNNING ? 1 : 2;
+        if (rep < 2 || ld_acquire_u32(&as->tag[(rep - 2) & 3]) == (unsigned)(rep - 1)) {
+            if (rep >= 2 && *(volatile const int *)&as->rec[(rep - 2) & 3].status != ST_RUNNING) return 2;
+            if (ld_acquire_u32(done + left) >= (unsigned)rep && ld_acquire_u32(done + right) >= (unsigned)rep) return 1;
+        }
+        __nanosleep(20);
+    }
+    return 0;
+}
+
+template <typename R, int LPC, int PPL, int MODE>
+__device__ __forceinline__ void percell_body(const KParams<R> &p, int gw, int nwarps, int frd, int fgs,
+                                             const phi_t<R> *phi_psi, const phi_t<R> *phi_pub);
+
 // HALO (OCI only) selects the storage of the face buffers the iteration reads
 // and writes: 0 float pairs in and out; 1 float in, BF16 out (first iteration
 // of the BF16 phase); 2 BF16 in and out (the phase's persistent loop); 3 BF16
@@ -820,7 +956,17 @@ __device__ __forceinline__ int xpose_idx(int l, int v)
 // 11 warps: the warps' own instruction-level parallelism matters more).
 __host__ __device__ constexpr int tma_max_threads(int chunk, int ppl) { return (chunk >= 8 || ppl > 1) ? 384 : 576; }
 
-template <int LPC, int PPL, int CHUNK, int STAGES, int MODE, bool LOOP = false, int HALO = 0>
+// ASYNC (persistent OCI loop, float faces): no grid barrier between
+// iterations.  A warp starts iteration rep once the warps owning the chunks
+// next to its own (its ring neighbours gw - 1, gw + 1) finished rep - 1 and the
+// decision of rep - 2 is known; the last warp of a block to finish an
+// iteration adds its block's warp partials, the last block adds the blocks'
+// partials and publishes the decision (fixed orders: the same sums every run).  An iteration may so run one
+// past the final one; the faces rotate through three buffers, so that
+// speculative iteration overwrites neither the last iteration's input faces
+// nor its moments, and it stops at the first chunk boundary after the decision
+// is seen.  The end of the step (commit) follows one grid barrier.
+template <int LPC, int PPL, int CHUNK, int STAGES, int MODE, bool LOOP = false, int HALO = 0, bool ASYNC = false>
 __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(const KParams<float> p)
 {
     using R = float;
@@ -831,6 +977,7 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
     static_assert(!LOOP || MODE == M_OCI, "the persistent loop runs the OCI iteration only");
     static_assert(HALO == 0 || MODE == M_OCI, "BF16 faces in the OCI iteration only");
     static_assert(!LOOP || HALO == 0 || HALO == 2, "the persistent loops keep one face storage");
+    static_assert(!ASYNC || (LOOP && HALO == 0), "the barrier-free loop is the float-face OCI loop");
     constexpr bool IN_BF = HALO == 2 || HALO == 3, OUT_BF = HALO == 1 || HALO == 2;
     constexpr unsigned FB = IN_BF ? 4u : 8u;  // bytes per face pair read
     extern __shared__ __align__(128) unsigned char smem[];
@@ -936,16 +1083,30 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
     };
     int mK = -1;
     float4 kA = make_float4(0.f, 0.f, 0.f, 0.f), kB = kA;
+    // barrier-free loop: ring neighbours, wait limit, the launch's starting stall state
+    const int nb_left = (gw + tw - 1) % tw, nb_right = (gw + 1) % tw;
+    const unsigned shortfall = LOOP ? (unsigned)p.cfg->bar_shortfall : 0u;
+    const unsigned wlimit = LOOP && p.cfg->bar_poll_limit ? p.cfg->bar_poll_limit : kWaitLimit;
+    const int stall0 = stall;
+    const double best0 = best;
+    // barrier-free loop: per-block warp partials and arrival counts of the last
+    // four iterations (the block's last warp of an iteration sums them)
+    __shared__ double s_wpart[ASYNC ? 4 : 1][ASYNC ? tma_max_threads(CHUNK, PPL) / 32 : 1][3];
+    __shared__ unsigned s_wcnt[4];
+    if constexpr (ASYNC) {
+        if (threadIdx.x < 4) s_wcnt[threadIdx.x] = 0u;
+        __syncthreads();
+    }
 
     for (int rep = 0;; ++rep) {
-        const int frd = PING ? ((base + iter) & 1) : base;
-        const int fwr = frd ^ 1;
+        const int frd = ASYNC ? (base + iter) % 3 : (PING ? ((base + iter) & 1) : base);
+        const int fwr = ASYNC ? (base + iter + 1) % 3 : frd ^ 1;
         const phi_t<R> *phr = iter == 0 ? p.phi0 : p.phi[iter & 1];
         phi_t<R> *phw = p.phi[(iter + 1) & 1];
         const r2<R> *fPr = p.faceP[frd], *fMr = p.faceM[frd];
         r2<R> *fPw = p.faceP[fwr], *fMw = p.faceM[fwr];
-        const unsigned *hPr = p.hfP[frd], *hMr = p.hfM[frd];
-        unsigned *hPw = p.hfP[fwr], *hMw = p.hfM[fwr];
+        const unsigned *hPr = p.hfP[frd & 1], *hMr = p.hfM[frd & 1];  // BF16 phases use parities 0 and 1 only
+        unsigned *hPw = p.hfP[fwr & 1], *hMw = p.hfM[fwr & 1];
         // incident faces at face index f: the staged copy's source, a boundary read
         auto face_src_P = [&](size_t f) -> const void * { return IN_BF ? (const void *)(hPr + f * P) : (const void *)(fPr + f * P); };
         auto face_src_M = [&](size_t f) -> const void * { return IN_BF ? (const void *)(hMr + f * P) : (const void *)(fMr + f * P); };
@@ -984,12 +1145,28 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
             bulk_g2s(st + oQ, p.cellq + c0, bQ, bar);
             bulk_g2s(st + oT, p.mat + c0, bT, bar);
         };
-        if (lane == 0) {
-            // faces written by other blocks in the previous iteration (generic stores,
-            // ordered by the grid barrier) before this thread's bulk copies read them
-            if (LOOP && rep > 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
-            for (int i = 0; i < STAGES - 1; ++i) issue_faces(i);
+        if constexpr (ASYNC) {
+            if (rep > 0) {
+                int go = 0;
+                if (lane == 0) go = async_wait(p.as, p.as_done, nb_left, nb_right, rep, wlimit);
+                go = __shfl_sync(FULL, go, 0);
+                if (go != 1) {
+                    if (go == 0 && lane == 0) atomicExch(&p.st->status, ST_TIMEOUT);
+                    drain_static();
+                    break;
+                }
+                // the neighbours' generic stores (acquired above) before the bulk reads
+                if (lane == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
+            }
         }
+        // (in the barrier loop the first chunks' faces of iterations after the
+        // first were issued right after the previous grid barrier)
+        if (lane == 0 && !(LOOP && !ASYNC && rep > 0))
+            for (int i = 0; i < STAGES - 1; ++i) issue_faces(i);
+        // barrier-free loop: the decision of the previous iteration, polled once
+        // per chunk (the load's latency hidden by the chunk's work)
+        bool prev_known = !ASYNC || rep == 0;
+        bool aborted = false;
 
         float accf_d2 = 0.f, accf_p2 = 0.f;  // per-lane partials; block and grid sums in double
         bool ok_all = true;
@@ -999,6 +1176,8 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
                 fence_proxy_async();
                 issue(i + STAGES - 1);
             }
+            unsigned poll_tag = 0;
+            if (ASYNC && !prev_known && lane == 0 && i + 1 < nmine) poll_tag = ld_relaxed_u32(&p.as->tag[(rep - 1) & 3]);
             const int chunk = gw + i * tw;
             const unsigned char *st = ring + (size_t)stage_of(i) * sbytes;
             if (!mbar_wait(bars + stage_of(i), parity_of(i))) {
@@ -1202,6 +1381,28 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
             else phase_e(BoolTag<false>{});
             fence_proxy_async();  // this lane's phase-A stores into the ring before the next copy into it
             __syncwarp();  // stage i and the transpose buffer fully read
+            if constexpr (ASYNC) {
+                if (!prev_known && i + 1 < nmine) {
+                    int known = 0;  // 1: the previous iteration goes on, 2: it was the last
+                    if (lane == 0 && poll_tag == (unsigned)rep) {
+                        asm volatile("fence.acq_rel.gpu;\n" ::: "memory");
+                        known = *(volatile const int *)&p.as->rec[(rep - 1) & 3].status == ST_RUNNING ? 1 : 2;
+                    }
+                    known = __shfl_sync(FULL, known, 0);
+                    if (known == 1) prev_known = true;
+                    if (known == 2) {
+                        // drop the rest of this speculative iteration, once the
+                        // copies already issued for the next chunks have landed
+                        const int last = i + STAGES < nmine ? i + STAGES : nmine;
+                        for (int k = i + 1; k < last; ++k) (void)mbar_wait(bars + stage_of(k), parity_of(k));
+                        aborted = true;
+                        break;
+                    }
+                }
+            }
+        }
+        if constexpr (ASYNC) {
+            if (aborted) break;
         }
         if (!ok_all) {
             // a copy never completed: record it and wait (bounded) for this warp's
@@ -1214,69 +1415,172 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
             finalize_iteration((double)accf_d2, (double)accf_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond,
                                HALO == 1 ? 1 : (HALO == 3 ? 3 : 0));
             return;
+        } else if constexpr (ASYNC) {
+            rp += nmine;
+            const double wd2 = warp_sum((double)accf_d2), wp2 = warp_sum((double)accf_p2);
+            // the next iteration's invariant copies
+            if (lane == 0 && ok_all)
+                for (int i = 0; i < STAGES - 1; ++i) issue_static(i);
+            // publish: this iteration's face and moment stores (every lane's) before
+            // the completion count and the partials
+            __threadfence();
+            __syncwarp();
+            // two-level fixed-order sum: the block's last warp adds its warps'
+            // partials, the grid's last block adds the blocks' partials and decides
+            int closer = 0;
+            if (lane == 0) {
+                s_wpart[rep & 3][warp][0] = wd2;
+                s_wpart[rep & 3][warp][1] = wp2;
+                s_wpart[rep & 3][warp][2] = ok_all ? 0.0 : 1.0;
+                __threadfence();  // faces, moments and the partial before the counts
+                st_release_u32(p.as_done + gw, (unsigned)rep + 1u);
+                const unsigned bold = atomicAdd(&s_wcnt[rep & 3], 1u);
+                if (bold + 1u == (unsigned)((rep >> 2) + 1) * (unsigned)wpb) {
+                    __threadfence_block();
+                    double a = 0.0, b = 0.0, f = 0.0;
+                    for (int w = 0; w < wpb; ++w) {
+                        a += *(volatile double *)&s_wpart[rep & 3][w][0];
+                        b += *(volatile double *)&s_wpart[rep & 3][w][1];
+                        f += *(volatile double *)&s_wpart[rep & 3][w][2];
+                    }
+                    double *pp = p.as_part + ((size_t)(rep & 3) * gridDim.x + blockIdx.x) * 3;
+                    pp[0] = a;
+                    pp[1] = b;
+                    pp[2] = f;
+                    __threadfence();
+                    const unsigned old = atomicAdd(&p.as->cnt[rep & 3], 1u);
+                    closer = old + 1u == (unsigned)((rep >> 2) + 1) * gridDim.x + shortfall ? 1 : 0;
+                }
+            }
+            closer = __shfl_sync(FULL, closer, 0);
+            if (closer) {
+                // the last block of this iteration: every block's partial, in a fixed order
+                __threadfence();
+                const double *pp = p.as_part + (size_t)(rep & 3) * gridDim.x * 3;
+                double a = 0.0, b = 0.0, f = 0.0;
+                for (int q = lane; q < (int)gridDim.x; q += 32) {
+                    a += __ldcg(pp + 3 * q);
+                    b += __ldcg(pp + 3 * q + 1);
+                    f += __ldcg(pp + 3 * q + 2);
+                }
+                a = warp_sum(a);
+                b = warp_sum(b);
+                f = warp_sum(f);
+                if (lane == 0) {
+                    int pstall = stall0;
+                    double pbest = best0;
+                    if (rep > 0) {
+                        const AsyncRec *pr = &p.as->rec[(rep - 1) & 3];
+                        pstall = *(volatile const int *)&pr->stall;
+                        pbest = *(volatile const double *)&pr->best;
+                    }
+                    const int it = iter + 1;
+                    double resid;
+                    const int ns = loop_decision(a, b, f != 0.0, it, fixed_left, false, p.cfg, pstall, pbest, resid);
+                    AsyncRec *rc = &p.as->rec[rep & 3];
+                    rc->resid = resid;
+                    rc->d2 = a;
+                    rc->p2 = b;
+                    rc->best = pbest;
+                    rc->stall = pstall;
+                    rc->status = ns;
+                    IterState *sw = p.st;
+                    sw->iter = it;
+                    sw->resid = resid;
+                    sw->d2 = a;
+                    sw->p2 = b;
+                    sw->stall = pstall;
+                    sw->best = pbest;
+                    sw->launches += 1;
+                    atomicCAS(&sw->status, ST_RUNNING, ns);  // a recorded timeout stays
+                    __threadfence();
+                    st_release_u32(&p.as->tag[rep & 3], (unsigned)rep + 1u);
+                }
+            }
+            if (!ok_all) break;  // this warp's copies failed: it stops here
+            iter += 1;
         } else {
             rp += nmine;
-            const bool block_ok = __syncthreads_and(ok_all ? 1 : 0) != 0;
+            // per-warp partials and copy status, one block barrier; then thread 0
+            // alone meets the grid
+            __shared__ double s_wd[2][32];
+            __shared__ int s_wok[32];
+            __shared__ double s_ab[2];
+            __shared__ int s_flag[2];  // grid barrier reached; some block reported a copy timeout
+            const double wd2 = warp_sum((double)accf_d2), wp2 = warp_sum((double)accf_p2);
+            if (lane == 0) {
+                s_wd[0][warp] = wd2;
+                s_wd[1][warp] = wp2;
+                s_wok[warp] = ok_all ? 1 : 0;
+            }
+            __syncthreads();
+            bool block_ok = true;
+            for (int w = 0; w < wpb; ++w) block_ok = block_ok && s_wok[w] != 0;
             // the next iteration's invariant copies go out before the barrier
             if (lane == 0 && block_ok)
                 for (int i = 0; i < STAGES - 1; ++i) issue_static(i);
-            double d2 = (double)accf_d2, p2 = (double)accf_p2;
-            block_sum2(d2, p2);
             const int G = gridDim.x;
             double *lp = p.loop_partials + (size_t)(iter & 1) * 3 * G;
+            const IterConfig *cfg = p.cfg;
             if (threadIdx.x == 0) {
+                double d2 = 0.0, p2 = 0.0;
+                for (int w = 0; w < wpb; ++w) {
+                    d2 += s_wd[0][w];
+                    p2 += s_wd[1][w];
+                }
                 lp[3 * blockIdx.x] = d2;
                 lp[3 * blockIdx.x + 1] = p2;
                 lp[3 * blockIdx.x + 2] = block_ok ? 0.0 : 1.0;
+                s_flag[0] = grid_arrive_wait(p.loop_bar, (unsigned)(rep + 1) * (unsigned)G + (unsigned)cfg->bar_shortfall,
+                                             cfg->bar_poll_limit ? cfg->bar_poll_limit : kWaitLimit) ? 1 : 0;
             }
-            const IterConfig *cfg = p.cfg;
-            const bool bar_ok = grid_barrier(p.loop_bar, (unsigned)(rep + 1) * (unsigned)G + (unsigned)cfg->bar_shortfall,
-                                             cfg->bar_poll_limit ? cfg->bar_poll_limit : kWaitLimit);
-            // every block sums the partials in the same fixed order
-            double a = 0.0, b = 0.0, f = 0.0;
-            for (int q = threadIdx.x; q < G; q += blockDim.x) {
-                a += __ldcg(lp + 3 * q);
-                b += __ldcg(lp + 3 * q + 1);
-                f += __ldcg(lp + 3 * q + 2);
-            }
-            block_sum2(a, b);
-            const bool fault = __syncthreads_or(f != 0.0 ? 1 : 0) != 0 || !bar_ok;
-            __shared__ double s_ab[2];
-            if (threadIdx.x == 0) { s_ab[0] = a; s_ab[1] = b; }
             __syncthreads();
-            a = s_ab[0];
-            b = s_ab[1];
+            const bool bar_ok = s_flag[0] != 0;
+            // the next iteration's first incident faces go out now, their latency
+            // hidden by the reduction and decision below (waited for if the step
+            // ends here); the generic stores of the other blocks are ordered by
+            // the grid barrier, the proxy fence orders them before the bulk reads
+            if (lane == 0 && block_ok) {
+                const int nfrd = PING ? ((base + iter + 1) & 1) : base;
+                asm volatile("fence.proxy.async.global;\n" ::: "memory");
+                for (int i = 0; i < STAGES - 1 && i < nmine; ++i) {
+                    const int c0 = (gw + i * tw) * CPC;
+                    const int nv = J - c0 < CPC ? J - c0 : CPC;
+                    unsigned char *stg = ring + (size_t)stage_of(i) * sbytes;
+                    unsigned long long *bar = bars + stage_of(i);
+                    const unsigned bF = round16(nv * P * FB);
+                    const void *srcP = IN_BF ? (const void *)(p.hfP[nfrd] + (size_t)c0 * P)
+                                             : (const void *)(p.faceP[nfrd] + (size_t)c0 * P);
+                    const void *srcM = IN_BF ? (const void *)(p.hfM[nfrd] + (size_t)(c0 + 1) * P)
+                                             : (const void *)(p.faceM[nfrd] + (size_t)(c0 + 1) * P);
+                    mbar_expect_tx_arrive(bar, 2 * bF);
+                    bulk_g2s(stg + oP, srcP, bF, bar);
+                    bulk_g2s(stg + oM, srcM, bF, bar);
+                }
+            }
+            // every block sums the partials in the same fixed order (warp 0)
+            if (warp == 0) {
+                double a = 0.0, b = 0.0, f = 0.0;
+                for (int q = lane; q < G; q += 32) {
+                    a += __ldcg(lp + 3 * q);
+                    b += __ldcg(lp + 3 * q + 1);
+                    f += __ldcg(lp + 3 * q + 2);
+                }
+                a = warp_sum(a);
+                b = warp_sum(b);
+                f = warp_sum(f);
+                if (lane == 0) {
+                    s_ab[0] = a;
+                    s_ab[1] = b;
+                    s_flag[1] = f != 0.0 ? 1 : 0;
+                }
+            }
+            __syncthreads();
+            const double a = s_ab[0], b = s_ab[1];
+            const bool fault = s_flag[1] != 0 || !bar_ok;
             const int it = iter + 1;
             double resid;
-            if (b > 0.0) resid = sqrt(a / b);
-            else resid = (a == 0.0) ? 0.0 : __longlong_as_double(0x7ff0000000000000LL);
-            int ns = ST_RUNNING;
-            if (fault) ns = ST_TIMEOUT;
-            else if (!(resid == resid) || !(a == a) || !(b == b) || isinf(b)) ns = ST_NAN;
-            else if (fixed_left > 0) ns = it >= fixed_left ? ST_MAXITER : ST_RUNNING;  // timing: a fixed count
-            else if (HALO == 2) {
-                // BF16 phase: never final; ends at the switch threshold, near the
-                // iteration limit, or once BF16 rounding stops the change falling
-                if (resid < cfg->halo_switch || it >= cfg->max_iter - 2) ns = ST_SWITCH;
-                else if (resid < 0.9 * best) {
-                    best = resid;
-                    stall = 0;
-                } else if (++stall >= cfg->halo_stall) {
-                    ns = ST_SWITCH;
-                }
-            }
-            else if (resid < cfg->tol) ns = ST_CONVERGED;
-            else if (it >= cfg->max_iter) ns = ST_MAXITER;
-            if (HALO == 0 && ns == ST_RUNNING && fixed_left == 0 && cfg->stall_floor > 0.0) {
-                if (cfg->stall_iters < 0) {
-                    if (resid < cfg->stall_floor) ns = ST_STALL;
-                } else if (resid < 0.9 * best) {
-                    best = resid;
-                    stall = 0;
-                } else if (++stall >= cfg->stall_iters && resid < cfg->stall_floor) {
-                    ns = ST_STALL;
-                }
-            }
+            const int ns = loop_decision(a, b, fault, it, fixed_left, HALO == 2, cfg, stall, best, resid);
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 IterState *sw = p.st;
                 sw->iter = it;
@@ -1291,10 +1595,41 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
             iter = it;
             status = ns;
             if (status != ST_RUNNING || it == cfg->pause_at) {
-                if (block_ok) drain_static();
+                // the next iteration's first copies (invariant part and faces) are
+                // in flight: wait for them before the block's shared memory goes
+                if (block_ok)
+                    for (int i = 0; i < STAGES - 1 && i < nmine; ++i) (void)mbar_wait(bars + stage_of(i), parity_of(i));
                 return;
             }
         }
+    }
+    if constexpr (ASYNC) {
+        // every warp has left the loop (with no copy in flight): one grid
+        // barrier, then the end of the step over all cells
+        __syncthreads();
+        __shared__ int s_exit_ok;
+        if (threadIdx.x == 0) {
+            const bool ok = grid_arrive_wait(&p.as->exit_bar, (unsigned)gridDim.x + shortfall, wlimit);
+            if (!ok) atomicExch(&p.st->status, ST_TIMEOUT);
+            s_exit_ok = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_exit_ok) return;
+        IterState *st = p.st;
+        const int fst = *(volatile const int *)&st->status, fit = *(volatile const int *)&st->iter;
+        const bool go = fit >= 1 && (fst == ST_CONVERGED || (fst == ST_MAXITER && p.cfg->commit_unconverged));
+        // the last iteration read buffer (base + fit - 1) % 3; the next step's
+        // initial iterate goes to one of buffers 0 and 1 other than that one
+        const int frd_last = (base + fit - 1) % 3;
+        const int g_buf = frd_last == 2 ? 0 : 1 - frd_last;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->committed = go ? 1 : 0;
+            st->base_next = go ? g_buf : base;
+            st->rot3 = 1;
+            st->cur_face = (base + fit) % 3;
+        }
+        if (!go) return;
+        percell_body<float, LPC, PPL, C_COMMIT_OCI>(p, gw, tw, frd_last, g_buf, p.phi[fit & 1], p.phi[fit & 1]);
     }
 }
 
@@ -1309,13 +1644,12 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
 //   C_GUESS : initial iterate from psi_edge (after set_state or a rejected step).
 // ---------------------------------------------------------------------------
 template <typename R, int LPC, int PPL, int MODE>
+__device__ __forceinline__ void percell_body(const KParams<R> &p, int gw, int nwarps, int frd, int fgs,
+                                             const phi_t<R> *phi_psi, const phi_t<R> *phi_pub);
+
+template <typename R, int LPC, int PPL, int MODE>
 __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
 {
-    constexpr int SPW = 32 / LPC;
-    constexpr int ROWS = 4;  // cells per segment in flight per pass (loads issued together)
-    const int lane = threadIdx.x & 31;
-    const int seg = lane / LPC, ls = lane % LPC;
-    const int J = p.J, P = p.P;
     IterState *st = p.st;
     const int status = st->status, iter = st->iter, base = st->base;
     bool go = true;
@@ -1345,10 +1679,25 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
         fgs = st->base_next;
     }
     if (!go) return;
+    percell_body<R, LPC, PPL, MODE>(p, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5,
+                                    frd, fgs, phi_psi, phi_pub);
+}
+
+// The per-cell work of k_percell for warp gw of nwarps, face buffers frd (read)
+// and fgs (written); also the end of a step of the barrier-free loop, so every
+// load of data written during the launch goes through L2 (ld.cg).
+template <typename R, int LPC, int PPL, int MODE>
+__device__ __forceinline__ void percell_body(const KParams<R> &p, int gw, int nwarps, int frd, int fgs,
+                                             const phi_t<R> *phi_psi, const phi_t<R> *phi_pub)
+{
+    constexpr int SPW = 32 / LPC;
+    constexpr int ROWS = 4;  // cells per segment in flight per pass (loads issued together)
+    constexpr bool COMMIT = MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI || MODE == C_COMMIT_LIN;
+    const int lane = threadIdx.x & 31;
+    const int seg = lane / LPC, ls = lane % LPC;
+    const int J = p.J, P = p.P;
     const bool refl_l = (MODE == C_COMMIT_OCI || MODE == C_COMMIT_LIN) && p.bc_left == BC_REFLECT;
     const bool refl_r = (MODE == C_COMMIT_OCI || MODE == C_COMMIT_LIN) && p.bc_right == BC_REFLECT;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
     R mu[PPL];
 #pragma unroll
     for (int i = 0; i < PPL; ++i) mu[i] = (ls + LPC * i < P) ? ldg2(p.muw + ls + LPC * i).x : R(0);
@@ -1377,16 +1726,16 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
             for (int i = 0; i < PPL; ++i) {
                 const int pp = ls + LPC * i;
                 const bool ok = valid && pp < P;
-                per[r][i] = ok ? ld4(p.psi_edge + (size_t)cell * P + pp) : r4<R>{0, 0, 0, 0};
+                per[r][i] = ok ? ldcg4(p.psi_edge + (size_t)cell * P + pp) : r4<R>{0, 0, 0, 0};
                 inPr[r][i] = inMr[r][i] = r2<R>{0, 0};
                 if (ok && COMMIT) {
-                    inPr[r][i] = (refl_l && cell == 0) ? ld2(p.faceM[frd] + pp) : ld2(p.faceP[frd] + (size_t)cell * P + pp);
-                    inMr[r][i] = (refl_r && cell == J - 1) ? ld2(p.faceP[frd] + (size_t)J * P + pp)
-                                                          : ld2(p.faceM[frd] + (size_t)(cell + 1) * P + pp);
+                    inPr[r][i] = (refl_l && cell == 0) ? ldcg2(p.faceM[frd] + pp) : ldcg2(p.faceP[frd] + (size_t)cell * P + pp);
+                    inMr[r][i] = (refl_r && cell == J - 1) ? ldcg2(p.faceP[frd] + (size_t)J * P + pp)
+                                                          : ldcg2(p.faceM[frd] + (size_t)(cell + 1) * P + pp);
                     if (MODE == C_COMMIT_LIN) {  // incident h0 + d
-                        const r2<R> a = (refl_l && cell == 0) ? ld2(p.h0M + pp) : ld2(p.h0P + (size_t)cell * P + pp);
-                        const r2<R> b = (refl_r && cell == J - 1) ? ld2(p.h0P + (size_t)J * P + pp)
-                                                                 : ld2(p.h0M + (size_t)(cell + 1) * P + pp);
+                        const r2<R> a = (refl_l && cell == 0) ? ldcg2(p.h0M + pp) : ldcg2(p.h0P + (size_t)cell * P + pp);
+                        const r2<R> b = (refl_r && cell == J - 1) ? ldcg2(p.h0P + (size_t)J * P + pp)
+                                                                 : ldcg2(p.h0M + (size_t)(cell + 1) * P + pp);
                         inPr[r][i].x += a.x; inPr[r][i].y += a.y;
                         inMr[r][i].x += b.x; inMr[r][i].y += b.y;
                     }
@@ -1423,7 +1772,7 @@ __global__ void __launch_bounds__(256) k_percell(const KParams<R> p)
                     if (cell == J - 1 && p.bc_right == BC_REFLECT) {
                         // SI lags a reflecting right face: the first sweep sees the
                         // initial iterate's outgoing +mu flux there.
-                        const r2<R> v = ld2(p.faceP[frd] + (size_t)J * P + pp);
+                        const r2<R> v = ldcg2(p.faceP[frd] + (size_t)J * P + pp);
                         st2(p.refl + pp, v.x, v.y);
                     }
                     continue;
@@ -1624,6 +1973,8 @@ static __global__ void k_step_begin(IterState *st)
     st->resid = 0.0;
     st->stall = 0;
     st->best = __longlong_as_double(0x7ff0000000000000LL);
+    st->rot3 = 0;
+    st->cur_face = st->base;
 }
 
 // Resume a stalled step with the correction iteration: the high-precision

@@ -41,6 +41,8 @@ struct HaloKernels {
 // Returns false if (lpc, ppl) has no instantiation.
 bool kernel_set_f32(int lpc, int ppl, KernelSet *out);
 bool kernel_set_bf16(int lpc, int ppl, HaloKernels *out);
+// The barrier-free persistent OCI loop (8-row chunks, 2-stage ring) or nullptr.
+const void *kernel_async_loop(int lpc, int ppl);
 // Shared-memory bytes per stage of the staged FP32 kernels for P pairs and
 // chunks of `chunk` cell rows.
 unsigned tma_stage_bytes(int lpc, int chunk, int P);
