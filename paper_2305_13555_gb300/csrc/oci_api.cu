@@ -798,7 +798,7 @@ int halo_setup(oci_handle *h)
     CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->hk.loop, h->cells_block, h->cells_smem));
     if (h->cells_grid > sms * per_sm) return OCI_EINVAL;  // the cooperative loop would not fit
     const size_t fb = (size_t)(h->J + 1) * h->P * 4, fa = (fb + 255) & ~(size_t)255;
-    if (cudaMalloc(&h->hface_mem, 4 * fa) != cudaSuccess) return OCI_ENOMEM;
+    if (!h->hface_mem && cudaMalloc(&h->hface_mem, 4 * fa) != cudaSuccess) return OCI_ENOMEM;
     char *b = (char *)h->hface_mem;
     h->hfP[0] = (unsigned *)b;
     h->hfP[1] = (unsigned *)(b + fa);
@@ -826,6 +826,7 @@ int ensure_graphs(oci_handle *h)
         // a cooperative kernel node was refused: iterate with one launch per iteration
         (void)cudaGetLastError();
         h->use_loop = false;
+        h->use_async = false;
         rc = h->prec == OCI_FP64 ? build_graph<double>(h, false, &h->graph_oci, &h->exec_oci)
                                  : build_graph<float>(h, false, &h->graph_oci, &h->exec_oci);
     }
