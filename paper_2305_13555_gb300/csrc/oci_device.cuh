@@ -1408,8 +1408,9 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
             // a copy never completed: record it and wait (bounded) for this warp's
             // outstanding copies before the block's shared memory is released
             if (lane == 0) atomicExch(&p.st->status, ST_TIMEOUT);
-            const int last = broke_at + STAGES - 1 < nmine ? broke_at + STAGES - 1 : nmine;
-            for (int k = broke_at; k < last; ++k) (void)mbar_wait(bars + stage_of(k), parity_of(k));
+            // copies were issued for positions broke_at .. broke_at + STAGES - 1
+            const int last = broke_at + STAGES - 1 < nmine ? broke_at + STAGES - 1 : nmine - 1;
+            for (int k = broke_at; k <= last; ++k) (void)mbar_wait(bars + stage_of(k), parity_of(k));
         }
         if constexpr (!LOOP) {
             finalize_iteration((double)accf_d2, (double)accf_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond,
