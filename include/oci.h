@@ -118,8 +118,10 @@ void oci_destroy(oci_handle *h);
  * of Eqs. scb-mb-a..d): host [J][4].  The copy is enqueued on the handle's
  * stream: from pageable memory q may be reused when the call returns; from
  * page-locked (pinned) memory the copy is asynchronous, so keep q unchanged
- * until the next call that synchronises (oci_step, si_step, oci_fluxes).
- * OCI_EINVAL on NULL. */
+ * until the next call that synchronises (oci_step, si_step, oci_fluxes,
+ * oci_step_wait, oci_sync).  While a step started by oci_step_async runs, the
+ * copy goes to the handle's copy stream and overlaps that step; the next step
+ * applies it.  OCI_EINVAL on NULL. */
 int oci_set_source(oci_handle *h, const double *q);
 
 /* Iteration controls: tolerance (>= 0; 0 iterates to max_iter), iteration cap
@@ -229,6 +231,32 @@ int oci_step(oci_handle *h, oci_stats *st);
  * in its direction of travel, mu < 0 first (so a reflecting left face uses the
  * current sweep; a reflecting right face uses the previous iterate). */
 int si_step(oci_handle *h, oci_stats *st);
+
+/* Pipelined stepping (no counterpart in the paper; it overlaps the host
+ * traffic of consecutive steps with their computation).  oci_step_async
+ * enqueues one OCI step -- the oci_step computation -- on the handle's stream and
+ * returns without waiting; oci_step_wait waits for it, finishes what needs the
+ * host (an FP32 refinement of a stalled step), fills *st (may be NULL) and
+ * returns the status oci_step would have returned.  Between the two, the host
+ * may call oci_set_source (the next step's source, staged on a copy stream)
+ * and oci_fluxes_async; every other call on the handle returns OCI_ESTATE until
+ * oci_step_wait.  oci_step_async returns OCI_ESTATE while a step is pending or
+ * for a handle whose step takes decisions on the host mid-step (a learned
+ * guess attached, the dense solver, backward Euler); use oci_step there. */
+int oci_step_async(oci_handle *h);
+int oci_step_wait(oci_handle *h, oci_stats *st);
+
+/* Copy the moments published by the last step enqueued before this call (as
+ * oci_fluxes, [J][4]) to host memory without waiting: a device snapshot on the
+ * handle's stream (so the next step may overwrite the published moments) and
+ * the copy to phi on the copy stream, overlapping whatever runs next; phi
+ * (page-locked for an asynchronous copy) is complete when the next
+ * oci_step_wait or oci_sync returns.  Two snapshots alternate, so at most two
+ * such copies are in flight.  OCI_EINVAL on NULL, OCI_ENOMEM, OCI_ECUDA. */
+int oci_fluxes_async(oci_handle *h, double *phi);
+
+/* Wait for everything the handle enqueued (its stream and its copy stream). */
+int oci_sync(oci_handle *h);
 
 /* Scalar-flux moments phi = sum_n w_n psi_n of the last committed step
  * (Eq. following the SI sweeps): host [J][4]. */

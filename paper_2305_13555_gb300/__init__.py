@@ -68,6 +68,10 @@ SIGNATURES = {
     "oci_set_sweep": (ctypes.c_int, [_VP, _I32]),
     "oci_set_time_scheme": (ctypes.c_int, [_VP, _I32]),
     "oci_set_halo": (ctypes.c_int, [_VP, _I32]),
+    "oci_step_async": (ctypes.c_int, [_VP]),
+    "oci_step_wait": (ctypes.c_int, [_VP, _VP]),
+    "oci_fluxes_async": (ctypes.c_int, [_VP, _VP]),
+    "oci_sync": (ctypes.c_int, [_VP]),
     "oci_set_wait_limits": (ctypes.c_int, [_VP, ctypes.c_uint32, _I32]),
     "oci_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
     "si_step": (ctypes.c_int, [_VP, ctypes.POINTER(OciStats)]),
@@ -235,6 +239,33 @@ def oci_step(h):
     if rc in (OCI_EINVAL, OCI_ECUDA, OCI_ENOMEM):
         _check(rc, "oci_step", h)
     return rc, st.as_dict()
+
+
+def oci_step_async(h):
+    """Enqueue one OCI step and return at once (see oci.h); raises on any error,
+    OCI_ESTATE included (a step already pending, or a handle whose step needs the host)."""
+    _check(load_library().oci_step_async(h), "oci_step_async", h)
+
+
+def oci_step_wait(h):
+    """Wait for the step oci_step_async enqueued; returns (status, stats dict) as oci_step."""
+    st = OciStats()
+    rc = load_library().oci_step_wait(h, ctypes.byref(st))
+    if rc in (OCI_EINVAL, OCI_ECUDA, OCI_ENOMEM, OCI_ESTATE):
+        _check(rc, "oci_step_wait", h)
+    return rc, st.as_dict()
+
+
+def oci_fluxes_async(h, out):
+    """Enqueue the copy of the published moments into out ([J][4] float64, ideally
+    page-locked); out is complete after the next oci_step_wait or oci_sync."""
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]):
+        raise ValueError("out must be a C-contiguous float64 array")
+    _check(load_library().oci_fluxes_async(h, _ptr(out)), "oci_fluxes_async", h)
+
+
+def oci_sync(h):
+    _check(load_library().oci_sync(h), "oci_sync", h)
 
 
 def si_step(h):

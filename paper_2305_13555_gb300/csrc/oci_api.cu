@@ -191,6 +191,17 @@ struct oci_handle {
     size_t as_zero_bytes = 0;
     cudaGraph_t graph_oci_bar = nullptr;
     cudaGraphExec_t exec_oci_bar = nullptr;
+    // pipelined stepping (oci_step_async / oci_step_wait): a copy stream for the
+    // next step's source and the last step's moments, two device snapshots of
+    // the moments, and the events ordering them against the handle's stream
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_done = nullptr, ev_q_ready = nullptr, ev_q_free = nullptr, ev_snap[2] = {nullptr, nullptr},
+                ev_d2h[2] = {nullptr, nullptr};
+    double *phi_snap[2] = {nullptr, nullptr};
+    int snap_k = 0;
+    bool step_pending = false, q_pending = false;
+    bool pend_halo = false, pend_async = false;
+    int pend_launches = 0;
 };
 
 namespace {
@@ -407,6 +418,7 @@ int upload_source(oci_handle *h, const double *q)
     else
         k_scale_source<float><<<grid, 256, 0, h->stream>>>(h->q_dev, h->dx_dev, h->J, (r4<float> *)h->cellq);
     CK(h, cudaGetLastError());
+    if (h->ev_q_free) CK(h, cudaEventRecord(h->ev_q_free, h->stream));  // q_dev consumed
     h->q_host_valid = false;
     if (h->nn_mem) {
         if (q) {
@@ -421,6 +433,37 @@ int upload_source(oci_handle *h, const double *q)
         CK(h, cudaMemcpyAsync(h->nn_qfeat, qf.data(), sizeof(float) * qf.size(), cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
     }
+    return OCI_OK;
+}
+
+// Pipelined stepping: the copy stream, events and moment snapshots (once).
+int pipe_setup(oci_handle *h)
+{
+    if (h->copy_stream) return OCI_OK;
+    CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&h->ev_done, &h->ev_q_ready, &h->ev_q_free, &h->ev_snap[0], &h->ev_snap[1], &h->ev_d2h[0],
+                           &h->ev_d2h[1]})
+        CK(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    for (int k = 0; k < 2; ++k)
+        if (cudaMalloc((void **)&h->phi_snap[k], (size_t)h->J * 32) != cudaSuccess) return OCI_ENOMEM;
+    return OCI_OK;
+}
+
+// A source staged on the copy stream while a step was running: scale it into
+// the cell sources ahead of the next step.
+int apply_pending_source(oci_handle *h)
+{
+    if (!h->q_pending) return OCI_OK;
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_q_ready, 0));
+    const int grid = std::min((h->J + 255) / 256, 152 * 8);
+    if (h->prec == OCI_FP64)
+        k_scale_source<double><<<grid, 256, 0, h->stream>>>(h->q_dev, h->dx_dev, h->J, (r4<double> *)h->cellq);
+    else
+        k_scale_source<float><<<grid, 256, 0, h->stream>>>(h->q_dev, h->dx_dev, h->J, (r4<float> *)h->cellq);
+    CK(h, cudaGetLastError());
+    CK(h, cudaEventRecord(h->ev_q_free, h->stream));
+    h->q_pending = false;
+    h->q_host_valid = false;
     return OCI_OK;
 }
 
@@ -1143,9 +1186,11 @@ struct StepRange {
 int run_step(oci_handle *h, bool si, oci_stats *st)
 {
     if (!h) return OCI_EINVAL;
+    if (h->step_pending) return OCI_ESTATE;
     const StepRange range(si ? "si_step" : (h->scheme == OCI_TIME_BE ? "oci_step (backward Euler)" : "oci_step"));
     CK(h, cudaSetDevice(h->device));
     int rc = ensure_graphs(h);
+    if (!rc) rc = apply_pending_source(h);
     if (rc) return rc;
     int launches = 0;  // kernels of this library enqueued for the step
     if (!h->guess_valid) {
@@ -1593,6 +1638,14 @@ void oci_destroy(oci_handle *h)
     if (h->exec_oci_bar) cudaGraphExecDestroy(h->exec_oci_bar);
     if (h->graph_oci_bar) cudaGraphDestroy(h->graph_oci_bar);
     if (h->async_mem) cudaFree(h->async_mem);
+    if (h->copy_stream) {
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamDestroy(h->copy_stream);
+    }
+    for (cudaEvent_t e : {h->ev_done, h->ev_q_ready, h->ev_q_free, h->ev_snap[0], h->ev_snap[1], h->ev_d2h[0], h->ev_d2h[1]})
+        if (e) cudaEventDestroy(e);
+    for (double *ps : h->phi_snap)
+        if (ps) cudaFree(ps);
     if (h->graph_oci_h) cudaGraphDestroy(h->graph_oci_h);
     if (h->hface_mem) cudaFree(h->hface_mem);
     if (h->nn_mem) cudaFree(h->nn_mem);
@@ -1612,12 +1665,21 @@ int oci_set_source(oci_handle *h, const double *q)
 {
     if (!h || !q) return OCI_EINVAL;
     CK(h, cudaSetDevice(h->device));
-    return upload_source(h, q);
+    if (!h->step_pending) return upload_source(h, q);
+    // a step is running: stage the copy on the copy stream (once the last
+    // scaling kernel has read q_dev); the next step scales it
+    CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_q_free, 0));
+    CK(h, cudaMemcpyAsync(h->q_dev, q, (size_t)h->J * 32, cudaMemcpyHostToDevice, h->copy_stream));
+    CK(h, cudaEventRecord(h->ev_q_ready, h->copy_stream));
+    h->q_pending = true;
+    h->q_host_valid = false;
+    return OCI_OK;
 }
 
 int oci_set_iteration(oci_handle *h, double tol, int32_t max_iter, int32_t commit_unconverged)
 {
     if (!h || !(tol >= 0.0) || max_iter < 1) return OCI_EINVAL;
+    if (h->step_pending) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     h->cfg.tol = tol;
     h->cfg.max_iter = max_iter;
@@ -1628,6 +1690,7 @@ int oci_set_iteration(oci_handle *h, double tol, int32_t max_iter, int32_t commi
 int oci_set_stream(oci_handle *h, void *cuda_stream)
 {
     if (!h) return OCI_EINVAL;
+    if (h->step_pending) return OCI_ESTATE;
     CK(h, cudaStreamSynchronize(h->stream));
     h->stream = (cudaStream_t)cuda_stream;
     return OCI_OK;
@@ -1636,6 +1699,7 @@ int oci_set_stream(oci_handle *h, void *cuda_stream)
 int oci_set_wait_limits(oci_handle *h, uint32_t poll_limit, int32_t barrier_shortfall)
 {
     if (!h || barrier_shortfall < 0) return OCI_EINVAL;
+    if (h->step_pending) return OCI_ESTATE;
     h->cfg.bar_poll_limit = poll_limit;
     h->cfg.bar_shortfall = barrier_shortfall;
     return OCI_OK;
@@ -1644,6 +1708,7 @@ int oci_set_wait_limits(oci_handle *h, uint32_t poll_limit, int32_t barrier_shor
 int oci_set_halo(oci_handle *h, int32_t halo)
 {
     if (!h || (halo != OCI_HALO_FP32 && halo != OCI_HALO_BF16)) return OCI_EINVAL;
+    if (h->step_pending) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     if (halo == OCI_HALO_BF16 && !h->exec_oci_h) {
         const int rc = halo_setup(h);
@@ -1656,6 +1721,7 @@ int oci_set_halo(oci_handle *h, int32_t halo)
 int oci_set_time_scheme(oci_handle *h, int32_t scheme)
 {
     if (!h || (scheme != OCI_TIME_MB && scheme != OCI_TIME_BE)) return OCI_EINVAL;
+    if (h->step_pending) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     if (scheme == OCI_TIME_BE && !h->be_mem) {
         const int rc = be_setup(h);
@@ -1673,6 +1739,7 @@ int oci_set_time_scheme(oci_handle *h, int32_t scheme)
 int oci_set_solver(oci_handle *h, int32_t solver)
 {
     if (!h || (solver != OCI_SOLVER_WOODBURY && solver != OCI_SOLVER_DENSE)) return OCI_EINVAL;
+    if (h->step_pending) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     if (solver == OCI_SOLVER_DENSE && !h->dense.mem) {
         const int rc = dense_setup(h);
@@ -1688,6 +1755,7 @@ int oci_set_solver(oci_handle *h, int32_t solver)
 int oci_set_sweep(oci_handle *h, int32_t sweep)
 {
     if (!h || (sweep != OCI_SWEEP_MARCH && sweep != OCI_SWEEP_SCAN)) return OCI_EINVAL;
+    if (h->step_pending) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     if (sweep == h->sweep) return OCI_OK;
     if (sweep == OCI_SWEEP_SCAN && !h->scan_mem) {
@@ -1714,6 +1782,106 @@ int oci_set_sweep(oci_handle *h, int32_t sweep)
 int oci_step(oci_handle *h, oci_stats *st) { return run_step(h, false, st); }
 
 int si_step(oci_handle *h, oci_stats *st) { return run_step(h, true, st); }
+
+int oci_step_async(oci_handle *h)
+{
+    if (!h) return OCI_EINVAL;
+    if (h->step_pending || h->nn_mode != OCI_NN_OFF || h->solver != OCI_SOLVER_WOODBURY || h->scheme != OCI_TIME_MB)
+        return OCI_ESTATE;
+    CK(h, cudaSetDevice(h->device));
+    int rc = pipe_setup(h);
+    if (!rc) rc = ensure_graphs(h);
+    if (!rc) rc = apply_pending_source(h);
+    if (rc) return rc;
+    int launches = 0;
+    if (!h->guess_valid) {
+        if ((rc = launch_guess(h))) return rc;
+        ++launches;
+    }
+    if ((rc = set_device_cfg(h, h->cfg))) return rc;
+    const bool halo_graph = h->halo == OCI_HALO_BF16 && h->exec_oci_h && h->cfg.max_iter >= 4;
+    CK(h, cudaEventRecord(h->ev0, h->stream));
+    CK(h, cudaGraphLaunch(halo_graph ? h->exec_oci_h : h->exec_oci, h->stream));
+    CK(h, cudaEventRecord(h->ev1, h->stream));
+    CK(h, cudaMemcpyAsync(h->h_st, h->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaEventRecord(h->ev_done, h->stream));
+    h->step_pending = true;
+    h->pend_halo = halo_graph;
+    h->pend_async = !halo_graph && h->use_async;
+    h->pend_launches = launches;
+    return OCI_OK;
+}
+
+int oci_step_wait(oci_handle *h, oci_stats *st)
+{
+    if (!h) return OCI_EINVAL;
+    if (!h->step_pending) return OCI_ESTATE;
+    CK(h, cudaSetDevice(h->device));
+    h->step_pending = false;
+    CK(h, cudaEventSynchronize(h->ev_done));
+    CK(h, cudaStreamSynchronize(h->copy_stream));  // the moments copied out before this step
+    IterState s = *h->h_st;
+    const int unroll = (h->staged && h->pdl_graph) ? kUnroll : 1;
+    int launches = h->pend_launches;
+    if (h->pend_halo) launches += 6;
+    else if (h->pend_async) launches += 2;
+    else if (h->use_loop) launches += 3;
+    else launches += 2 + unroll * ((s.iter + unroll - 1) / unroll);
+    int refined = 0;
+    if (s.status == ocik::ST_STALL && h->cells_lin && h->ks.refine) {
+        const int main_iters = s.iter;
+        int rc = refine_step(h, &s);
+        if (rc) return rc;
+        refined = 1;
+        launches += 2 + (s.iter - main_iters);
+        CK(h, cudaEventRecord(h->ev1, h->stream));
+        if ((rc = read_state(h, &s))) return rc;
+    }
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    h->guess_valid = s.committed != 0;
+    const int status = map_status(s.status);
+    if (st) {
+        st->iters = s.iter;
+        st->status = status;
+        st->residual = s.resid;
+        st->seconds = ms * 1e-3;
+        st->committed = s.committed;
+        st->nn_accepts = 0;
+        st->nn_rejects = 0;
+        st->refined = refined;
+        st->launches = launches;
+    }
+    return status;
+}
+
+int oci_fluxes_async(oci_handle *h, double *phi)
+{
+    if (!h || !phi) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    int rc = pipe_setup(h);
+    if (rc) return rc;
+    const int k = h->snap_k;
+    // snapshot on the handle's stream (after the last enqueued step), host copy on
+    // the copy stream; the snapshot is reused once its previous host copy is done
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_d2h[k], 0));
+    CK(h, cudaMemcpyAsync(h->phi_snap[k], h->phi_out, (size_t)h->J * 32, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaEventRecord(h->ev_snap[k], h->stream));
+    CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_snap[k], 0));
+    CK(h, cudaMemcpyAsync(phi, h->phi_snap[k], (size_t)h->J * 32, cudaMemcpyDeviceToHost, h->copy_stream));
+    CK(h, cudaEventRecord(h->ev_d2h[k], h->copy_stream));
+    h->snap_k = k ^ 1;
+    return OCI_OK;
+}
+
+int oci_sync(oci_handle *h)
+{
+    if (!h) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->copy_stream) CK(h, cudaStreamSynchronize(h->copy_stream));
+    return OCI_OK;
+}
 
 int oci_fluxes(const oci_handle *hc, double *phi)
 {
@@ -1766,6 +1934,7 @@ int oci_get_state(const oci_handle *hc, double *psi)
 int oci_set_state(oci_handle *h, const double *psi)
 {
     if (!h || !psi) return OCI_EINVAL;
+    if (h->step_pending) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     return load_state(h, psi);
 }
@@ -1773,6 +1942,7 @@ int oci_set_state(oci_handle *h, const double *psi)
 int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_launch)
 {
     if (!h || n_iter < 1 || !seconds_per_launch) return OCI_EINVAL;
+    if (h->step_pending) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     int rc = launch_guess(h);
     if (rc) return rc;
@@ -1905,6 +2075,7 @@ int oci_nn_attach(oci_handle *h, const float *params, int32_t mode, int32_t k_co
 {
     if (!h || mode < OCI_NN_OFF || mode > OCI_NN_GUESS_ADAPTIVE) return OCI_EINVAL;
     if (mode != OCI_NN_OFF && (!params || k_corr < 1)) return OCI_EINVAL;
+    if (h->step_pending) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     if (mode == OCI_NN_OFF) {
         h->nn_mode = OCI_NN_OFF;

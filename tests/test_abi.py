@@ -102,4 +102,8 @@ def test_null_handle_calls(lib):
     assert lib.oci_fluxes(None, None) == pkg.OCI_EINVAL
     assert lib.oci_set_iteration(None, 1e-8, 10, 0) == pkg.OCI_EINVAL
     assert lib.oci_set_halo(None, pkg.OCI_HALO_BF16) == pkg.OCI_EINVAL
+    assert lib.oci_step_async(None) == pkg.OCI_EINVAL
+    assert lib.oci_step_wait(None, None) == pkg.OCI_EINVAL
+    assert lib.oci_fluxes_async(None, None) == pkg.OCI_EINVAL
+    assert lib.oci_sync(None) == pkg.OCI_EINVAL
     lib.oci_destroy(None)
