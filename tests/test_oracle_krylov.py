@@ -1,4 +1,4 @@
-"""Why OCI is not wrapped in GMRES (the survey's last 'next' row): on the
+"""Why OCI is not wrapped in GMRES (Krylov acceleration of the OCI map): on the
 whole-problem system of one time step (oracle.brute, assembled from the
 balance equations), OCI is block Jacobi over cells, and GMRES preconditioned by
 it -- i.e. GMRES whose operator is the OCI map -- needs about as many
