@@ -135,7 +135,13 @@ class ClockSampler:
             self.proc.kill()
             self.proc.wait()
         self.reader.join(timeout=5)
-        inside = [ln for t, ln in self.lines if t0 <= t <= t1]
+        return self.summarize(self.lines, t0, t1)
+
+    @staticmethod
+    def summarize(lines, t0, t1):
+        """Median SM clock, maximum clock and active slowdown reasons of the
+        (arrival time, csv line) samples stamped inside [t0, t1]."""
+        inside = [ln for t, ln in lines if t0 <= t <= t1]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in inside:
