@@ -776,22 +776,20 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, u
 }
 
 // Thread 0 alone meets the grid (the block's own writes were ordered before
-// it by a block barrier): release-arrive on count, then poll (bounded) until
-// target arrivals; false when the limit expired.
+// it by a block barrier): release-arrive on count (fence, then the atomic),
+// then poll (bounded) with acquire loads until target arrivals; false when
+// the limit expired.  The acquire load that sees the target, followed by the
+// caller's block barrier, orders the other blocks' released writes before
+// every thread's later reads, so no fence follows it.
 __device__ __forceinline__ bool grid_arrive_wait(unsigned *count, unsigned target, unsigned limit)
 {
     __threadfence();
     atomicAdd(count, 1u);
-    bool ok = false;
     for (unsigned it = 0; it < limit; ++it) {
-        if (ld_acquire_u32(count) >= target) {
-            ok = true;
-            break;
-        }
+        if (ld_acquire_u32(count) >= target) return true;
         __nanosleep(32);
     }
-    __threadfence();
-    return ok;
+    return false;
 }
 
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
