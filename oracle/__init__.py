@@ -13,6 +13,8 @@ Contents
   * ``si_iteration``        -- one source iteration: per-ordinate 4x4 sweeps
                                (Sec. "Source Iteration (SI)").
   * ``run``                 -- the time-step driver for either scheme.
+  * ``be_oci_iteration``, ``be_si_iteration``, ``run_be`` -- the same for the
+                               backward-Euler scheme (the disabled section).
   * ``oracle.brute``        -- whole-problem dense solve assembled directly from
                                the SCB-MB balance equations (tiny slabs).
   * ``oracle.nn``           -- FP64 plain-loop 1-D CNN forward/backward.
@@ -58,6 +60,8 @@ def load_library(path):
     lib.oracle_run.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                ctypes.c_int32, ctypes.c_int32, dp, dp, dp, dp, ctypes.c_int32]
     lib.oracle_be_run.argtypes = lib.oracle_run.argtypes
+    lib.oracle_be_oci_iteration.argtypes = [ctypes.POINTER(_Problem), dp, dp, dp, dp]
+    lib.oracle_be_si_iteration.argtypes = [ctypes.POINTER(_Problem), dp, dp, dp, dp, dp]
     lib.oracle_max_threads.restype = ctypes.c_int
     return lib
 
@@ -142,6 +146,30 @@ def si_iteration(prob, psi_edge, phi_in, psi_in, lib=None):
     err = _load(lib).oracle_si_iteration(ctypes.byref(p.s), _ptr(pe), _ptr(fi), _ptr(pi), _ptr(po), _ptr(ph))
     if err:
         raise RuntimeError(f"oracle_si_iteration failed ({err})")
+    return po, ph
+
+
+def be_oci_iteration(prob, psi_prev, psi_in, lib=None):
+    """One backward-Euler OCI iteration from iterate ``psi_in`` [J][N][2] with
+    psi^{n-1} = ``psi_prev``; returns (psi_out [J][N][2], phi [J][2])."""
+    p = _as_problem(prob)
+    pp, pi = _f64(psi_prev, (p.J, p.N, 2)), _f64(psi_in, (p.J, p.N, 2))
+    po, ph = np.zeros((p.J, p.N, 2)), np.zeros((p.J, 2))
+    err = _load(lib).oracle_be_oci_iteration(ctypes.byref(p.s), _ptr(pp), _ptr(pi), _ptr(po), _ptr(ph))
+    if err:
+        raise RuntimeError(f"oracle_be_oci_iteration failed ({err})")
+    return po, ph
+
+
+def be_si_iteration(prob, psi_prev, phi_in, psi_in, lib=None):
+    """One backward-Euler SI iteration with lagged scalar flux ``phi_in`` [J][2]
+    (``psi_in`` supplies a lagged reflecting right face)."""
+    p = _as_problem(prob)
+    pp, fi, pi = _f64(psi_prev, (p.J, p.N, 2)), _f64(phi_in, (p.J, 2)), _f64(psi_in, (p.J, p.N, 2))
+    po, ph = np.zeros((p.J, p.N, 2)), np.zeros((p.J, 2))
+    err = _load(lib).oracle_be_si_iteration(ctypes.byref(p.s), _ptr(pp), _ptr(fi), _ptr(pi), _ptr(po), _ptr(ph))
+    if err:
+        raise RuntimeError(f"oracle_be_si_iteration failed ({err})")
     return po, ph
 
 

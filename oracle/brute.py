@@ -26,8 +26,27 @@ def _bc(x):
     return _BC_NAMES[x] if isinstance(x, str) else int(x)
 
 
-def step_system(prob, psi_edge):
-    """Assemble (M, rhs) for one time step from psi_{k-1/2} = psi_edge [J][N][2]."""
+def step_parts(prob, psi_edge):
+    """Assemble one time step's whole-problem system from psi_{k-1/2} = psi_edge
+    [J][N][2], with the matrix split by the kind of coupling each entry makes:
+
+      "own"           the cell's own streaming, collision and time terms, with
+                      the upstream closure where the upstream corner lies in the
+                      same cell (mu > 0 at the right face, mu < 0 at the left);
+      "scatter"       the isotropic scattering entries, Delta x Sigma_s w_n / 4
+                      on the same corner and time moment of every ordinate;
+      "neighbour"     the upstream closure that reads the adjacent cell's
+                      corner (mu > 0 from cell j-1, mu < 0 from cell j+1);
+      "reflect_left", "reflect_right"
+                      a reflecting face's closure: the mirror ordinate's
+                      outgoing corner of cell 0 or cell J-1.
+
+    Returns (parts, rhs); the whole-problem matrix is the sum of the parts.  The
+    iteration schemes are splittings of this one matrix (Sec. "One-Cell
+    Inversion (OCI)": each cell solved with its neighbours' fluxes from the
+    previous iterate; Sec. "Source Iteration (SI)": sweeps with the scattering
+    source from the previous iterate), so the parts let a test build each
+    scheme's iteration map without the oracle's code."""
     J, N = int(prob["n_cells"]), int(prob["n_ord"])
     P = N // 2
     mu, w = np.polynomial.legendre.leggauss(N)
@@ -43,7 +62,8 @@ def step_system(prob, psi_edge):
     pe = np.asarray(psi_edge, float).reshape(J, N, 2)
 
     n = 4 * N * J
-    M = np.zeros((n, n))
+    parts = {k: np.zeros((n, n)) for k in ("own", "scatter", "neighbour", "reflect_left", "reflect_right")}
+    M = parts["own"]
     b = np.zeros(n)
 
     def u(j, m, c):
@@ -57,20 +77,24 @@ def step_system(prob, psi_edge):
             if mu[m] > 0:
                 M[row, u(j, m, cR)] += coef
             elif j + 1 < J:
-                M[row, u(j + 1, m, cL)] += coef
+                parts["neighbour"][row, u(j + 1, m, cL)] += coef
             elif bcr == BC_REFLECT:
-                M[row, u(J - 1, N - 1 - m, cR)] += coef
+                parts["reflect_right"][row, u(J - 1, N - 1 - m, cR)] += coef
             elif bcr == BC_INCIDENT and psr is not None:
                 b[row] -= coef * psr[P - 1 - m, t]
         else:
             if mu[m] < 0:
                 M[row, u(j, m, cL)] += coef
             elif j > 0:
-                M[row, u(j - 1, m, cR)] += coef
+                parts["neighbour"][row, u(j - 1, m, cR)] += coef
             elif bcl == BC_REFLECT:
-                M[row, u(0, N - 1 - m, cL)] += coef
+                parts["reflect_left"][row, u(0, N - 1 - m, cL)] += coef
             elif bcl == BC_INCIDENT and psl is not None:
                 b[row] -= coef * psl[m - P, t]
+
+    def add_scatter(row, j, c):
+        for k in range(N):
+            parts["scatter"][row, u(j, k, c)] -= dx[j] / 4 * sigs[j] * w[k]
 
     for j in range(J):
         h = dx[j] / 2.0
@@ -83,8 +107,7 @@ def step_system(prob, psi_edge):
             M[r, u(j, m, 0)] += mm / 2 + h * sig[j]
             M[r, u(j, m, 1)] += mm / 2
             add_edge(r, -mm, j, m, 0, "left")
-            for k in range(N):
-                M[r, u(j, k, 0)] -= h / 2 * sigs[j] * w[k]
+            add_scatter(r, j, 0)
             b[r] += h / 2 * q[j, 0]
             # (b): right half, time average
             r = u(j, m, 1)
@@ -93,8 +116,7 @@ def step_system(prob, psi_edge):
             add_edge(r, mm, j, m, 0, "right")
             M[r, u(j, m, 0)] -= mm / 2
             M[r, u(j, m, 1)] += -mm / 2 + h * sig[j]
-            for k in range(N):
-                M[r, u(j, k, 1)] -= h / 2 * sigs[j] * w[k]
+            add_scatter(r, j, 1)
             b[r] += h / 2 * q[j, 1]
             # (c): left half, end of step (time derivative over dt/2)
             r = u(j, m, 2)
@@ -102,8 +124,7 @@ def step_system(prob, psi_edge):
             M[r, u(j, m, 0)] -= h * inv_v / (dt / 2)
             M[r, u(j, m, 3)] += mm / 2
             add_edge(r, -mm, j, m, 1, "left")
-            for k in range(N):
-                M[r, u(j, k, 2)] -= h / 2 * sigs[j] * w[k]
+            add_scatter(r, j, 2)
             b[r] += h / 2 * q[j, 2]
             # (d): right half, end of step
             r = u(j, m, 3)
@@ -111,10 +132,16 @@ def step_system(prob, psi_edge):
             M[r, u(j, m, 1)] -= h * inv_v / (dt / 2)
             M[r, u(j, m, 2)] -= mm / 2
             add_edge(r, mm, j, m, 1, "right")
-            for k in range(N):
-                M[r, u(j, k, 3)] -= h / 2 * sigs[j] * w[k]
+            add_scatter(r, j, 3)
             b[r] += h / 2 * q[j, 3]
-    return M, b
+    return parts, b
+
+
+def step_system(prob, psi_edge):
+    """Assemble (M, rhs) for one time step from psi_{k-1/2} = psi_edge [J][N][2]:
+    every balance equation as one row, both closures unlagged."""
+    parts, b = step_parts(prob, psi_edge)
+    return sum(parts.values()), b
 
 
 def solve_step(prob, psi_edge):
@@ -141,14 +168,16 @@ def run(prob, n_steps, psi_edge=None):
     return pe, np.array(phis)
 
 
-def be_step_system(prob, psi_prev):
-    """Assemble (M, rhs) for one backward-Euler step from psi^{n-1} = psi_prev
-    [J][N][2]: per cell, ordinate and half-cell the SCB balance
+def be_step_parts(prob, psi_prev):
+    """Assemble one backward-Euler step from psi^{n-1} = psi_prev [J][N][2]:
+    per cell, ordinate and half-cell the SCB balance
     mu (psi_out_face - psi_in_face) + Sigma_hat dx/2 psi_corner
         = dx/2 [Sigma_s/2 phi_corner + Q/2 + psi^{n-1}_corner/(v dt)],
     Sigma_hat = Sigma + 1/(v dt), with the midpoint value (psi_L + psi_R)/2 at
     x_j and the upstream corner at the cell edges (unlagged), Q = Q_{k+1/2}.
-    Unknown u(j, m, c) = (j*N + m)*2 + c, c in (L, R)."""
+    Unknown u(j, m, c) = (j*N + m)*2 + c, c in (L, R).  The matrix comes split
+    into the same parts as ``step_parts`` (own, scatter, neighbour,
+    reflect_left, reflect_right); returns (parts, rhs)."""
     J, N = int(prob["n_cells"]), int(prob["n_ord"])
     P = N // 2
     mu, w = np.polynomial.legendre.leggauss(N)
@@ -163,7 +192,8 @@ def be_step_system(prob, psi_prev):
     psr = None if prob.get("psi_bc_right") is None else np.asarray(prob["psi_bc_right"], float).reshape(P, 2)
     pp = np.asarray(psi_prev, float).reshape(J, N, 2)
     n = 2 * N * J
-    M = np.zeros((n, n))
+    parts = {k: np.zeros((n, n)) for k in ("own", "scatter", "neighbour", "reflect_left", "reflect_right")}
+    M = parts["own"]
     b = np.zeros(n)
 
     def u(j, m, c):
@@ -175,18 +205,18 @@ def be_step_system(prob, psi_prev):
             if mu[m] < 0:
                 M[row, u(j, m, 0)] += coef
             elif j > 0:
-                M[row, u(j - 1, m, 1)] += coef
+                parts["neighbour"][row, u(j - 1, m, 1)] += coef
             elif bcl == BC_REFLECT:
-                M[row, u(0, N - 1 - m, 0)] += coef
+                parts["reflect_left"][row, u(0, N - 1 - m, 0)] += coef
             elif bcl == BC_INCIDENT and psl is not None:
                 b[row] -= coef * psl[m - P, 1]
         else:
             if mu[m] > 0:
                 M[row, u(j, m, 1)] += coef
             elif j + 1 < J:
-                M[row, u(j + 1, m, 0)] += coef
+                parts["neighbour"][row, u(j + 1, m, 0)] += coef
             elif bcr == BC_REFLECT:
-                M[row, u(J - 1, N - 1 - m, 1)] += coef
+                parts["reflect_right"][row, u(J - 1, N - 1 - m, 1)] += coef
             elif bcr == BC_INCIDENT and psr is not None:
                 b[row] -= coef * psr[P - 1 - m, 1]
 
@@ -204,9 +234,15 @@ def be_step_system(prob, psi_prev):
                 add_face(r, -sgn * mm, j, m, side)
                 M[r, u(j, m, c)] += h * sh
                 for k in range(N):
-                    M[r, u(j, k, c)] -= h / 2 * sigs[j] * w[k]
+                    parts["scatter"][r, u(j, k, c)] -= h / 2 * sigs[j] * w[k]
                 b[r] += h / 2 * q[j, 2 + c] + h * inv_vdt * pp[j, m, c]
-    return M, b
+    return parts, b
+
+
+def be_step_system(prob, psi_prev):
+    """(M, rhs) of one backward-Euler step (the sum of ``be_step_parts``)."""
+    parts, b = be_step_parts(prob, psi_prev)
+    return sum(parts.values()), b
 
 
 def be_solve_step(prob, psi_prev):

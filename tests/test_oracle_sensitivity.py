@@ -43,17 +43,55 @@ MUTANTS = {
     "gl_weight_norm": ("double wi = 2.0 / ((1.0 - x * x) * dp * dp);", "double wi = 1.0 / ((1.0 - x * x) * dp * dp);"),
     # upwind closure taken from the wrong corner of the upstream cell
     "upwind_corner": ("if (j > 0) return psi[ix_psi(j - 1, m, cR, N)];", "if (j > 0) return psi[ix_psi(j - 1, m, cL, N)];"),
+    # OCI as forward Gauss-Seidel over cells: the mu > 0 incident flux read from the
+    # left neighbour's new iterate (cells taken in order on one thread), not iterate l
+    "oci_gauss_seidel": [
+        ("const double ink = incident(p, mu, psi_in, j, m, 0);",
+         "const double ink = incident(p, mu, (mu[m] > 0.0 && j > 0) ? psi_out : psi_in, j, m, 0);"),
+        ("const double inh = incident(p, mu, psi_in, j, m, 1);",
+         "const double inh = incident(p, mu, (mu[m] > 0.0 && j > 0) ? psi_out : psi_in, j, m, 1);"),
+        ("#pragma omp parallel\n        {\n            double *c = malloc(sizeof(double) * (size_t)n4);\n"
+         "#pragma omp for schedule(static)\n",
+         "        {\n            double *c = malloc(sizeof(double) * (size_t)n4);\n"),
+    ],
+    # SI: reflecting left face lagged (iterate l) instead of the current sweep's mu < 0 flux
+    "si_reflect_left_lagged": [
+        ("ink = psi_out[ix_psi(0, N - 1 - m, 0, N)];", "ink = psi_in[ix_psi(0, N - 1 - m, 0, N)];"),
+        ("inh = psi_out[ix_psi(0, N - 1 - m, 2, N)];", "inh = psi_in[ix_psi(0, N - 1 - m, 2, N)];"),
+    ],
 }
 
 
 def _build_mutant(tmp_path, name):
-    old, new = MUTANTS[name]
+    edits = MUTANTS[name]
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    for old, new in ([edits] if isinstance(edits, tuple) else edits):
+        assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+        src = src.replace(old, new)
     path = tmp_path / f"{name}.c"
-    path.write_text(src.replace(old, new))
+    path.write_text(src)
     lib = obuild.build(force=True, src=str(path), out=str(tmp_path / f"lib{name}.so"))
     return oracle.load_library(lib)
+
+
+def _map_fails(p, lib):
+    """One OCI and one SI iteration from a random iterate against the splittings
+    of the whole-problem matrix (the pins of test_oracle_map)."""
+    J, N = int(p["n_cells"]), int(p["n_ord"])
+    pe = np.asarray(p["psi0"]).reshape(J, N, 2)
+    parts, b = brute.step_parts(p, pe)
+    psi_l = np.random.default_rng(1).uniform(-0.5, 1.5, (J, N, 4))
+    _, w = np.polynomial.legendre.leggauss(N)
+    D = parts["own"] + parts["scatter"]
+    R = parts["neighbour"] + parts["reflect_left"] + parts["reflect_right"]
+    want = np.linalg.solve(D, b - R @ psi_l.ravel())
+    got, _ = oracle.oci_iteration(p, pe, psi_l, lib=lib)
+    if np.abs(got.ravel() - want).max() > 1e-12 * np.abs(want).max():
+        return True
+    L = parts["own"] + parts["neighbour"] + parts["reflect_left"]
+    want = np.linalg.solve(L, b - (parts["scatter"] + parts["reflect_right"]) @ psi_l.ravel())
+    got, _ = oracle.si_iteration(p, pe, np.einsum("n,jnc->jc", w, psi_l), psi_l, lib=lib)
+    return bool(np.abs(got.ravel() - want).max() > 1e-12 * np.abs(want).max())
 
 
 def _pins_fail(lib):
@@ -64,6 +102,8 @@ def _pins_fail(lib):
         return True
     for bcl, bcr in (("reflect", "incident"), ("incident", "reflect")):
         p = workloads.random_small(seed=77, J=5, N=4, bc_left=bcl, bc_right=bcr)
+        if _map_fails(p, lib):
+            return True
         pe_b, ph_b = brute.run(p, 2)
         for method in ("oci", "si"):
             r = oracle.run(p, method, 2, tol=1e-13, max_iter=5000, lib=lib)
@@ -129,3 +169,20 @@ def test_be_mutant_is_caught(tmp_path, name):
     path.write_text(src.replace(old, new))
     lib = oracle.load_library(obuild.build(force=True, src=str(path), out=str(tmp_path / f"lib{name}.so")))
     assert _be_pins_fail(lib), f"planted mistake {name} passed every BE pin"
+
+
+@pytest.mark.parametrize("name", ["oci_gauss_seidel", "si_reflect_left_lagged"])
+def test_map_mutants_keep_the_fixed_point(tmp_path, name):
+    """These two mistakes change only the order of the iteration, not where it
+    converges: the converged-solution pins alone pass them, and only the
+    one-iteration map pin catches them."""
+    lib = _build_mutant(tmp_path, name)
+    for bcl, bcr in (("reflect", "incident"), ("incident", "reflect")):
+        p = workloads.random_small(seed=77, J=5, N=4, bc_left=bcl, bc_right=bcr)
+        _, ph_b = brute.run(p, 2)
+        for method in ("oci", "si"):
+            r = oracle.run(p, method, 2, tol=1e-13, max_iter=5000, lib=lib)
+            assert r["status"] == 0
+            assert np.abs(r["phi_steps"] - ph_b).max() <= 1e-9 * np.abs(ph_b).max()
+    assert any(_map_fails(workloads.random_small(seed=77, J=5, N=4, bc_left=l, bc_right=r), lib)
+               for l, r in (("reflect", "incident"), ("incident", "reflect")))
