@@ -6,20 +6,28 @@ tolerance (relative change of phi < 1e-8): the whole hot path -- halo gather,
 per-ordinate block solves, scattering-moment reduction, capacitance solve,
 back-substitution, residual -- every iteration, plus the end-of-step commit.
 
-Default workload: the production homogeneous slab (65536 cells, S_64, Sigma = 1,
-c = 0.9, dx = 0.1 mfp, dt = 0.05, v = 1, Q = 1, reflecting left / vacuum right),
-FP32 angular flux with compensated moments and double-float capacitance /
-residual difference.  ``compare`` adds SI (the paper's march and the parallel
-prefix), FP64 OCI and backward-Euler OCI on the same slab, the plain-vs-learned-
-guess comparison on four thin-cell deployment slabs, and the dense per-material
-inverse against the Woodbury kernel at S_128.  ``value`` = cell-ordinate updates
-per second (cells x ordinates x iterations / device time), summed over replicas;
-``e2e`` = the same through the C ABI with pinned host buffers (source in, fluxes
-out).  Prints one JSON line.
+Default workload: the seeded layered slab (131072 cells in 8-32 layers,
+sigma_t = 10^U(-2,2), c ~ U(0, 0.999), optical thickness per cell U(0.05, 5),
+sources U(0, 10) on a random half of the layers, S_64, dt = 0.02, v = 1,
+vacuum faces, 100-step trajectory from psi0 = 0, tol 1e-8), FP32 angular flux
+with compensated moments and double-float capacitance / residual difference.
+Its ~212 MB working set exceeds the L2, so every iteration streams from HBM.
+``compare`` adds: the 65536-cell homogeneous slab (one point of the quadrature
+sweep) as a second headline-style line; the OCI-vs-SI sweep over c, dx and N on
+that slab (OCI FP32 / FP64, SI with the paper's march and with the parallel
+prefix); SI, FP64 OCI and backward-Euler OCI on the default workload; the error
+of the FP32 and BF16-halo paths against the FP64 path per configuration; the
+plain-vs-learned-guess comparison on eight thin-cell deployment slabs and one
+200-step deployment trajectory; and the dense per-material inverse against the
+Woodbury kernel at S_128.  ``value`` = cell-ordinate updates per second (cells
+x ordinates x iterations / device time), summed over replicas; ``e2e`` = the
+same through the C ABI with pinned host buffers (source in, fluxes out).
+Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload slab|hetero] [--precision fp32|fp64]
-                  [--no-compare] [--no-cpu-baseline] [--only-compare solvers|learned|dense]
+                  [--workload hetero|slab] [--precision fp32|fp64]
+                  [--no-compare] [--no-cpu-baseline]
+                  [--only-compare solvers|learned|dense|sweep|errors|deploy200]
 """
 import argparse
 import hashlib
@@ -45,13 +53,14 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2305_13555_gb300", "csrc", "oci_device.cu
 
 def make_problem(args):
     if args.workload == "slab":
-        p = workloads.config2(N=args.n_ord, c=args.c, dx=args.dx, J=args.cells, n_steps=50)
+        p = workloads.config2(N=args.n_ord, c=args.c, dx=args.dx, J=args.cells or 65536, n_steps=50)
         desc = (f"homogeneous slab {p['n_cells']} cells, S_{p['n_ord']}, sigma_t=1, c={args.c}, dx={args.dx} mfp, "
-                f"dt=0.05, v=1, Q=1, reflect/vacuum, tol 1e-8")
+                f"dt=0.05, v=1, Q=1, reflect/vacuum, 50-step trajectory, tol 1e-8")
     else:
-        p = workloads.config4(seed=args.seed, J=args.cells if args.cells != 65536 else 131072, n_steps=100)
-        desc = (f"seeded layered slab {p['n_cells']} cells, S_64, sigma_t 10^U(-2,2), c U(0,0.999), "
-                f"tau U(0.05,5), dt=0.02, vacuum/vacuum, tol 1e-8 (seed {args.seed})")
+        p = workloads.config4(seed=args.seed, J=args.cells or 131072, n_steps=100)
+        desc = (f"seeded layered slab {p['n_cells']} cells in {int(p['layer'].max()) + 1} layers, S_64, "
+                f"sigma_t 10^U(-2,2), c U(0,0.999), tau U(0.05,5), Q U(0,10) on half the layers, dt=0.02, v=1, "
+                f"vacuum/vacuum, 100-step trajectory, tol 1e-8 (seed {args.seed})")
     return p, desc
 
 
@@ -221,7 +230,7 @@ def run_ours(args, rank, world):
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
         launches += restart_if_due()  # host call between steps, outside the steps' device time
-        flush.zero_()  # evict the ~100 MB working set from L2 between timed steps
+        flush.zero_()  # evict the previous step's data from L2 between timed steps
         rc, st = s.step()
         assert rc == pkg.OCI_OK, (rc, st)
         iters.append(st["iters"])
@@ -249,21 +258,11 @@ def run_ours(args, rank, world):
                 "nominal_peak_gbs": NOMINAL_HBM_GBS, "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                 "kernel": ("k_cells_tma<OCI> persistent loop (figures per iteration; 50 iterations per launch)"
                            if args.precision == "fp32" else "k_cells<double, OCI> (one launch per iteration)"),
-                "iteration_us": round(t_launch * 1e6, 3), "algorithmic_bytes_per_iteration": abytes}
-
-    # the same kernel on the layered 131072-cell S_64 slab, whose ~212 MB working set
-    # does not fit in L2 (every iteration streams from HBM)
-    beyond = None
-    if args.precision == "fp32" and rank == 0:
-        p4 = workloads.config4(seed=args.seed, J=131072, n_steps=2)
-        s4 = pkg.Solver(p4, precision="fp32", tol=p4["tol"], stream=stream.cuda_stream)
-        t4 = pkg.oci_profile_iterations(s4.h, 50)
-        s4.close()
-        b4 = algorithmic_bytes(131072, 64, 4)
-        beyond = {"workload": f"layered slab 131072 cells, S_64 (seed {args.seed})", "iteration_us": round(t4 * 1e6, 3),
-                  "achieved": round(b4 / t4 / 1e9, 1), "frac": round(b4 / t4 / 1e9 / peak, 4),
-                  "algorithmic_bytes_per_iteration": b4}
-    roofline["beyond_l2"] = beyond
+                "iteration_us": round(t_launch * 1e6, 3), "algorithmic_bytes_per_iteration": abytes,
+                "algorithmic_bytes": "24 B per cell-ordinate (2 incident, 2 time-edge, 2 outgoing words) + 84 B per "
+                                     "cell (phi in and out as double-float, source moments, material id)"
+                                     if rs == 4 else "48 B per cell-ordinate + 100 B per cell",
+                "working_set_vs_l2": f"{abytes / 1e6:.0f} MB per iteration against a 129 MB L2"}
 
     # end to end through the C ABI with host buffers: source in, fluxes out, both in
     # pinned host memory (page-locked, so the copies are direct DMA), pipelined
@@ -305,7 +304,11 @@ def run_ours(args, rank, world):
     compare = {}
     if not args.no_compare and rank == 0:
         compare = run_compare(args, pkg, torch, stream)
+        compare["slab_65536"] = run_slab_point(args, pkg, torch, stream)
+        compare["err_vs_fp64"] = run_errors(args, pkg, torch, stream)
+        compare["sweep_oci_vs_si"] = run_sweep(args, pkg, torch, stream)
         compare["learned_guess"] = run_learned(args, pkg, torch, stream)
+        compare["deploy_200_steps"] = run_deploy200(args, pkg, torch, stream)
         compare["dense_inverse_s128"] = run_dense(args, pkg, torch, stream)
     return {
         "n_traj": n_traj, "value": value, "units": units, "dev_time": dev_time, "wall": wall, "iters": iters, "launches": launches,
@@ -352,74 +355,185 @@ def run_compare(args, pkg, torch, stream):
                          "iters_per_step": sum(its) / len(its)}
             if t_it is not None:
                 out[name]["s_per_iteration"] = t_it
-    if args.precision == "fp32":
-        # the BF16 halo's iteration against the FP32 one on the 131072-cell layered
-        # slab, whose working set does not fit in L2
-        p4 = workloads.config4(seed=args.seed, J=131072, n_steps=2)
-        row = {"workload": f"layered slab 131072 cells, S_64 (seed {args.seed})"}
-        for halo in ("fp32", "bf16"):
-            s = pkg.Solver(p4, precision="fp32", tol=p4["tol"], stream=stream.cuda_stream, halo=halo)
-            row[f"s_per_iteration_{halo}_halo"] = pkg.oci_profile_iterations(s.h, 50)
-            s.close()
-        out["bf16_halo_beyond_l2"] = row
     return out
+
+
+def _run_steps(pkg, stream, prob, n_steps, precision="fp32", method="oci", sweep="march", halo="fp32", tol=None,
+               nn=0, W=None, k_corr=50, max_iter=100000, keep_phi=False, skip=0):
+    """Steps 1..n_steps of a trajectory from psi0 on one handle: per-step device
+    seconds and iterations (steps after the first ``skip`` are summarised), the
+    published fluxes of every step if asked, or the failing status."""
+    s = pkg.Solver(prob, precision=precision, tol=prob["tol"] if tol is None else tol, stream=stream.cuda_stream,
+                   max_iter=max_iter, sweep=sweep, halo=halo)
+    try:
+        if nn:
+            pkg.oci_nn_attach(s.h, W, nn, k_corr)
+        its, secs, phis = [], [], []
+        for k in range(n_steps):
+            rc, st = s.step(method)
+            if rc != pkg.OCI_OK:
+                return {"failed_status": rc, "failed_at_step": k + 1}
+            its.append(st["iters"])
+            secs.append(st["seconds"])
+            if keep_phi:
+                phis.append(s.fluxes())
+    finally:
+        s.close()
+    J, N = prob["n_cells"], prob["n_ord"]
+    ti, ts = its[skip:], secs[skip:]
+    out = {"s_per_step": sum(ts) / len(ts), "iters_per_step": sum(ti) / len(ti),
+           "updates_per_s": J * N * sum(ti) / sum(ts), "steps": f"{skip + 1}-{n_steps}"}
+    if keep_phi:
+        out["phi"] = phis
+    return out
+
+
+def run_slab_point(args, pkg, torch, stream):
+    """The 65536-cell homogeneous slab (S_64, c = 0.9, dx = 0.1 mfp, reflecting
+    left / vacuum right, dt = 0.05): its 50-step trajectory and the iteration
+    kernel's roofline there (working set ~106 MB, inside the L2 across the
+    iterations of a step, so that fraction is not an HBM figure)."""
+    prob = workloads.config2(N=64, c=0.9, dx=0.1, J=65536, n_steps=50)
+    rec = _run_steps(pkg, stream, prob, 50)
+    s = pkg.Solver(prob, precision="fp32", tol=prob["tol"], stream=stream.cuda_stream)
+    t = pkg.oci_profile_iterations(s.h, 50)
+    s.close()
+    peak = float(load_peaks()[0]["hbm_gbs"])
+    b = algorithmic_bytes(65536, 64, 4)
+    rec.update(workload="homogeneous slab 65536 cells, S_64, c=0.9, dx=0.1 mfp, dt=0.05, reflect/vacuum, 50 steps",
+               iteration_us=round(t * 1e6, 3), achieved_gbs=round(b / t / 1e9, 1),
+               frac_l2_assisted=round(b / t / 1e9 / peak, 4), traffic=read_traffic("slab_fp32_S64_J65536"),
+               note="working set ~106 MB stays in L2 across a step's iterations: algorithmic bytes over the HBM "
+                    "copy peak, not an HBM fraction")
+    return rec
+
+
+def _maxrel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def run_errors(args, pkg, torch, stream):
+    """Error of the reduced-precision paths against the FP64 path per
+    configuration: the published scalar-flux moments of every step of a
+    trajectory, FP32 (and the BF16 incident-flux halo) at the configuration's
+    tolerance against FP64 OCI converged to 1e-12 (the FP64 path matches the FP64
+    oracle to 1e-12 at a fixed iteration count); max over the steps of
+    max|phi - phi_ref| / max|phi_ref|.  FP64 at the configuration's tolerance is
+    listed too: what of the error is the stopping tolerance, not the rounding."""
+    cases = [
+        ("config2_slab65536_S64_c0.9_dx0.1", workloads.config2(N=64, c=0.9, dx=0.1, J=65536, n_steps=50), 50),
+        ("config3_slab16384_S128", workloads.config3(n_steps=20), 20),
+        (f"config4_layered131072_S64_seed{args.seed}", workloads.config4(seed=args.seed, n_steps=100), 100),
+        (f"config5_deploy131072_S64_seed{args.nn_seed}", workloads.config5_deploy(args.nn_seed, n_steps=10), 10),
+    ]
+    out = {"definition": "max over steps of max|phi - phi_fp64| / max|phi_fp64| (4 moments, all cells); "
+                         "reference: GPU FP64 OCI at tol 1e-12"}
+    for name, prob, n in cases:
+        ref = _run_steps(pkg, stream, prob, n, "fp64", tol=1e-12, keep_phi=True)
+        if "phi" not in ref:
+            out[name] = {"reference_failed": ref}
+            continue
+        rec = {"steps": n, "tol": prob["tol"]}
+        for key, prec, halo in (("fp32", "fp32", "fp32"), ("fp32_bf16_halo", "fp32", "bf16"), ("fp64", "fp64", "fp32")):
+            if halo == "bf16" and prob["n_ord"] % 8:
+                continue
+            r = _run_steps(pkg, stream, prob, n, prec, halo=halo, keep_phi=True)
+            rec[key] = (max(_maxrel(a, b) for a, b in zip(r["phi"], ref["phi"])) if "phi" in r else r)
+        out[name] = rec
+    return out
+
+
+def run_sweep(args, pkg, torch, stream, n_steps=None):
+    """OCI against SI on the 65536-cell homogeneous slab over the scattering
+    ratio, the cell width and the quadrature order (c in {0.5, 0.9, 0.99}, dx in
+    {0.01, 0.1, 1, 10} mfp, S_32 and S_64; Sigma = 1, dt = 0.05, reflecting left /
+    vacuum right, tol 1e-8): iterations and device seconds per converged step
+    over the trajectory's first steps, for OCI in FP32 and FP64, SI with the
+    paper's march and SI with the parallel prefix (FP32)."""
+    n_steps = n_steps or args.sweep_steps
+    rows = []
+    for N in (32, 64):
+        for c in (0.5, 0.9, 0.99):
+            for dx in (0.01, 0.1, 1.0, 10.0):
+                prob = workloads.config2(N=N, c=c, dx=dx, J=65536, n_steps=n_steps)
+                row = {"N": N, "c": c, "dx": dx}
+                for key, prec, method, sweep in (("oci_fp32", "fp32", "oci", "march"), ("oci_fp64", "fp64", "oci", "march"),
+                                                 ("si_march_fp32", "fp32", "si", "march"),
+                                                 ("si_scan_fp32", "fp32", "si", "scan")):
+                    r = _run_steps(pkg, stream, prob, n_steps, prec, method, sweep)
+                    row[key] = ({"iters": round(r["iters_per_step"], 2), "ms": round(r["s_per_step"] * 1e3, 4)}
+                                if "s_per_step" in r else r)
+                best_si = min((row[k]["ms"] for k in ("si_march_fp32", "si_scan_fp32") if "ms" in row[k]), default=None)
+                if "ms" in row["oci_fp32"] and "ms" in row["si_march_fp32"]:
+                    row["si_march_over_oci_fp32_time"] = round(row["si_march_fp32"]["ms"] / row["oci_fp32"]["ms"], 3)
+                if "ms" in row["oci_fp32"] and best_si is not None:
+                    row["best_si_over_oci_fp32_time"] = round(best_si / row["oci_fp32"]["ms"], 3)
+                rows.append(row)
+    return {"workload": f"homogeneous slab 65536 cells, Sigma=1, dt=0.05, v=1, Q=1, reflect/vacuum, tol 1e-8; "
+                        f"steps 1-{n_steps} of each trajectory from psi0 = 0",
+            "paper_context": "paper: up to 3.4x OCI over SI wall clock (RTX 2060 mobile, CuPy/cuSPARSE GMRES, "
+                             "homogeneous slab L=10, Sigma=2, Q=0.1, 5 steps); context only",
+            "rows": rows}
+
+
+# Deployment slabs on which the learned guess is evaluated, fixed before any was
+# measured (the four slabs looked at while the method was built, 7-10, are not
+# among them).
+GAIN_SEEDS = (101, 102, 103, 104, 105, 106, 107, 108)
 
 
 def run_learned(args, pkg, torch, stream):
     """The metric's "plain vs NN+FP32" part on thin-cell deployment slabs
     (131072 cells, S_64, sigma_t dx ~ U(0.01, 0.1), c ~ U(0.9, 0.999), dt = 0.02):
     seconds and iterations per converged step of plain FP32 OCI and FP32 OCI with
-    the trained network's initial guess on four seeded slabs (2 warm-up and 6
-    timed steps each, from the same initial state; the guess always, and the
-    adaptive mode that keeps it only if a plain/guessed trial shows a gain), and,
-    on the first slab, plain
-    FP64 OCI and FP32 SI with the paper's march and with the parallel prefix."""
+    the trained network (the guess on every step, and the adaptive mode that keeps
+    it only where a plain/guessed trial shows a gain) on eight seeded slabs fixed
+    in advance, steps 3-8 of each trajectory (2 steps in, the same initial state)."""
     from paper_2305_13555_gb300 import learned
     if not os.path.exists(learned.DEFAULT_WEIGHTS):
         return {"unavailable": "no trained weights"}
     W = learned.load_weights()
-    seeds = [args.nn_seed, args.nn_seed - 1, args.nn_seed + 1, args.nn_seed + 2]
     out = {"workload": "config-5 deployment slabs: 131072 cells, S_64, thin cells (sigma_t dx 0.01-0.1), "
-                       "c 0.9-0.999, dt 0.02, vacuum/vacuum, tol 1e-8", "seeds": seeds}
-
-    def run(prob, prec, method, nn, n_w, n_t, sweep):
-        s = pkg.Solver(prob, precision=prec, tol=1e-8, stream=stream.cuda_stream, max_iter=50000, sweep=sweep)
-        if nn:
-            pkg.oci_nn_attach(s.h, W, nn, 50)
-        its, secs, rc = [], [], pkg.OCI_OK
-        for k in range(n_w + n_t):
-            rc, st = s.step(method)
-            if rc != pkg.OCI_OK:
-                break
-            if k >= n_w:
-                its.append(st["iters"])
-                secs.append(st["seconds"])
-        s.close()
-        if rc != pkg.OCI_OK:
-            return {"failed_status": rc}
-        return {"s_per_step": sum(secs) / len(secs), "iters_per_step": sum(its) / len(its),
-                "updates_per_s": 131072 * 64 * sum(its) / sum(secs), "steps_timed": n_t, "after_steps": n_w}
-
+                       "c 0.9-0.999, dt 0.02, vacuum/vacuum, tol 1e-8; steps 3-8", "seeds": list(GAIN_SEEDS)}
     per_seed = {}
-    for i, seed in enumerate(seeds):
-        prob = workloads.config5_deploy(seed, J=131072, N=64, n_steps=16)
-        rec = {"fp32_plain": run(prob, "fp32", "oci", 0, 2, 6, "march"),
-               "fp32_nn_guess": run(prob, "fp32", "oci", pkg.OCI_NN_GUESS, 2, 6, "march"),
-               "fp32_nn_adaptive": run(prob, "fp32", "oci", pkg.OCI_NN_GUESS_ADAPTIVE, 2, 6, "march")}
-        if i == 0:
-            rec["fp64_plain"] = run(prob, "fp64", "oci", 0, 2, 2, "march")
-            rec["si_fp32"] = run(prob, "fp32", "si", 0, 2, 2, "march")
-            rec["si_scan_fp32"] = run(prob, "fp32", "si", 0, 2, 6, "scan")
+    for seed in GAIN_SEEDS:
+        prob = workloads.config5_deploy(seed, J=131072, N=64, n_steps=8)
+        rec = {}
+        for key, nn in (("fp32_plain", 0), ("fp32_nn_guess", pkg.OCI_NN_GUESS),
+                        ("fp32_nn_adaptive", pkg.OCI_NN_GUESS_ADAPTIVE)):
+            r = _run_steps(pkg, stream, prob, 8, "fp32", nn=nn, W=W, max_iter=50000, skip=2)
+            rec[key] = r
         per_seed[str(seed)] = rec
     out["per_seed"] = per_seed
-    ok = [r for r in per_seed.values() if "s_per_step" in r["fp32_plain"] and "s_per_step" in r["fp32_nn_guess"]]
-    if ok:
-        out["nn_over_plain_time_ratio_mean"] = sum(r["fp32_nn_guess"]["s_per_step"] / r["fp32_plain"]["s_per_step"]
-                                                   for r in ok) / len(ok)
-        ad = [r for r in ok if "s_per_step" in r["fp32_nn_adaptive"]]
-        if ad:
-            out["adaptive_over_plain_time_ratio_mean"] = sum(
-                r["fp32_nn_adaptive"]["s_per_step"] / r["fp32_plain"]["s_per_step"] for r in ad) / len(ad)
+    for key in ("fp32_nn_guess", "fp32_nn_adaptive"):
+        ok = [r for r in per_seed.values() if "s_per_step" in r["fp32_plain"] and "s_per_step" in r[key]]
+        if ok:
+            out[f"{key}_over_plain_time_ratio_mean"] = sum(r[key]["s_per_step"] / r["fp32_plain"]["s_per_step"]
+                                                           for r in ok) / len(ok)
+            out[f"{key}_over_plain_iters_ratio_mean"] = sum(r[key]["iters_per_step"] / r["fp32_plain"]["iters_per_step"]
+                                                            for r in ok) / len(ok)
+    return out
+
+
+def run_deploy200(args, pkg, torch, stream):
+    """One whole 200-step deployment trajectory (131072 cells, S_64, thin cells,
+    c 0.9-0.999, dt 0.02, tol 1e-8, seed --nn-seed): device seconds and
+    iterations per converged step of plain FP32 OCI, FP32 OCI with the learned
+    guess (adaptive), plain FP64 OCI, and SI (FP32, the paper's march and the
+    parallel prefix)."""
+    from paper_2305_13555_gb300 import learned
+    W = learned.load_weights() if os.path.exists(learned.DEFAULT_WEIGHTS) else None
+    n = args.deploy_steps
+    prob = workloads.config5_deploy(args.nn_seed, J=131072, N=64, n_steps=n)
+    out = {"workload": f"deployment slab 131072 cells, S_64, seed {args.nn_seed}, steps 1-{n}, tol 1e-8"}
+    runs = [("oci_fp32_plain", "fp32", "oci", "march", 0), ("oci_fp64_plain", "fp64", "oci", "march", 0),
+            ("si_march_fp32", "fp32", "si", "march", 0), ("si_scan_fp32", "fp32", "si", "scan", 0),
+            ("si_scan_fp64", "fp64", "si", "scan", 0)]
+    if W is not None:
+        runs.insert(1, ("oci_fp32_nn_adaptive", "fp32", "oci", "march", pkg.OCI_NN_GUESS_ADAPTIVE))
+        runs.insert(2, ("oci_fp32_nn_guess", "fp32", "oci", "march", pkg.OCI_NN_GUESS))
+    for key, prec, method, sweep, nn in runs:
+        out[key] = _run_steps(pkg, stream, prob, n, prec, method, sweep, nn=nn, W=W, max_iter=50000)
     return out
 
 
@@ -527,17 +641,19 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="slab", choices=["slab", "hetero"])
+    ap.add_argument("--workload", default="hetero", choices=["hetero", "slab"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--n-ord", type=int, default=64)
-    ap.add_argument("--cells", type=int, default=65536)
+    ap.add_argument("--cells", type=int, default=0, help="0: the workload's own size")
     ap.add_argument("--c", type=float, default=0.9)
     ap.add_argument("--dx", type=float, default=0.1)
     ap.add_argument("--seed", type=int, default=4)
-    ap.add_argument("--nn-seed", type=int, default=8)
+    ap.add_argument("--nn-seed", type=int, default=GAIN_SEEDS[0])
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only-compare", choices=["solvers", "learned", "dense"],
+    ap.add_argument("--sweep-steps", type=int, default=50)
+    ap.add_argument("--deploy-steps", type=int, default=200)
+    ap.add_argument("--only-compare", choices=["solvers", "learned", "dense", "sweep", "errors", "deploy200", "slab"],
                     help="run one comparison block alone and print it (for profiling its kernels)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -547,7 +663,8 @@ def main():
         import paper_2305_13555_gb300 as pkg
         pkg.load_library()
         stream = torch.cuda.current_stream()
-        fn = {"solvers": run_compare, "learned": run_learned, "dense": run_dense}[args.only_compare]
+        fn = {"solvers": run_compare, "learned": run_learned, "dense": run_dense, "sweep": run_sweep,
+              "errors": run_errors, "deploy200": run_deploy200, "slab": run_slab_point}[args.only_compare]
         print(json.dumps({args.only_compare: fn(args, pkg, torch, stream)}))
         return
 
@@ -572,7 +689,9 @@ def main():
             "data": "synthetic",
             "config": {"workload": r["desc"], "cells": r["J"], "ordinates": r["N"],
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "flushed (256 MiB write) between timed steps; iterations within a step reuse L2",
+                       "l2": "flushed (256 MiB write) between timed steps; the working set (~212 MB per iteration "
+                             "at 131072 cells, S_64) exceeds the 129 MB L2" if r["J"] * r["N"] * 24 > 129e6 else
+                             "flushed (256 MiB write) between timed steps; iterations within a step reuse L2",
                        "trajectory": f"{r['n_traj']} time steps from psi0 = 0, replayed from psi0 (oci_set_state) "
                                      f"when warm-up + timed steps exceed it"},
             "iters_per_step": sum(r["iters"]) / len(r["iters"]),

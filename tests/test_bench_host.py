@@ -46,18 +46,18 @@ class _FakeOracle:
         return 16
 
 
-def _args(steps, warmup):
-    return argparse.Namespace(gpus=1, steps=steps, warmup=warmup, impl="reference", workload="slab",
-                              precision="fp32", n_ord=64, cells=65536, c=0.9, dx=0.1, seed=4, nn_seed=8)
+def _args(steps, warmup, workload="slab", cells=65536):
+    return argparse.Namespace(gpus=1, steps=steps, warmup=warmup, impl="reference", workload=workload,
+                              precision="fp32", n_ord=64, cells=cells, c=0.9, dx=0.1, seed=4, nn_seed=101)
 
 
-def _run_reference(monkeypatch, steps, warmup, rate):
+def _run_reference(monkeypatch, steps, warmup, rate, **kw):
     import sys
     clock = [0.0]
     fake = _FakeOracle(clock, rate)
     monkeypatch.setitem(sys.modules, "oracle", fake)
     monkeypatch.setattr(bench.time, "perf_counter", lambda: clock[0])
-    r = bench.run_reference(_args(steps, warmup), budget_s=150.0)
+    r = bench.run_reference(_args(steps, warmup, **kw), budget_s=150.0)
     return r, clock[0], fake
 
 
@@ -77,3 +77,12 @@ def test_reference_arm_scales_the_slab_down_for_many_steps(monkeypatch):
     assert total < 1.1 * 150.0  # warm-up and timed steps within the budget (plus the probe)
     assert abs(r["value"] - 65536 * 64 / 0.2) < 1e-6 * r["value"]  # the same rate, measured on the smaller slab
     assert r["e2e"]["value"] == r["value"] and r["impl"] == "reference"
+
+
+def test_reference_arm_on_the_default_layered_slab(monkeypatch):
+    """The default workload (cells = 0: the 131072-cell layered slab) with the
+    driver's step counts: two iterations of the whole problem per step fit."""
+    r, total, fake = _run_reference(monkeypatch, steps=20, warmup=5, rate=131072 / 0.5, workload="hetero", cells=0)
+    assert set(fake.cells) == {131072}
+    assert "131072-cell S_64" in r["cpu_baseline"]["sample"] and "layered slab" in r["config"]["workload"]
+    assert total < 150.0

@@ -419,3 +419,23 @@ def test_barrier_free_loop_stalled_step_refines(monkeypatch):
             rc, st = s.step()
             assert rc == pkg.OCI_OK and st["refined"] == 1, (rc, st)
             assert _rel(s.fluxes(), ref["phi_steps"][k]) < FP32_TOL
+
+
+def test_full_size_config4_converged_fp32_bound():
+    """131072-cell seeded layered slab, S_64 (the benchmark's headline workload
+    and launch configuration): three converged FP32 steps against the FP64 path
+    converged to 1e-12 (itself the oracle's map to 1e-12 at a fixed iteration
+    count, tests above), element-wise over every moment of every cell, within
+    the FP32 bound."""
+    prob = workloads.config4(seed=4, n_steps=3)
+    with pkg.Solver(prob, precision="fp64", tol=1e-12) as s:
+        ref = []
+        for _ in range(3):
+            rc, st = s.step("oci")
+            assert rc == pkg.OCI_OK, (rc, st)
+            ref.append(s.fluxes())
+    with pkg.Solver(prob, precision="fp32", tol=1e-8) as s:
+        for k in range(3):
+            rc, st = s.step("oci")
+            assert rc == pkg.OCI_OK, (rc, st)
+            assert _rel(s.fluxes(), ref[k]) < FP32_TOL
