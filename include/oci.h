@@ -289,6 +289,62 @@ int oci_set_state(oci_handle *h, const double *psi_edge);
  * restarts from it.  Used by the benchmark's roofline figure. */
 int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_launch);
 
+/* ------------------------------------------------- domain decomposition
+ * OCI is block Jacobi over cells: within an iteration every cell needs only
+ * its neighbours' incident fluxes from the previous iterate, so a slab can be
+ * split into cell ranges that iterate independently and exchange only the
+ * angular flux crossing each cut, once per iteration, plus two sums for the
+ * convergence test (Sec. "GPU Implementations": splitting the problem over
+ * several accelerators within an iteration).  A sub-domain is an ordinary
+ * handle created for its own cells with OCI_BC_INCIDENT (zero data) on every
+ * side that is a cut; the physical faces keep their own conditions.  One time
+ * step of a decomposed slab, on every sub-domain:
+ *   oci_dd_begin(h);
+ *   do {
+ *     oci_dd_export(h, out_left, out_right);   (exchange: a sub-domain's
+ *     oci_dd_import(h, in_left, in_right);      out_right is its right
+ *     oci_dd_iterate(h, sums);                  neighbour's in_left, and
+ *     total = sum of sums over sub-domains;     out_left its left
+ *     oci_dd_decide(h, total, &done, &stats);   neighbour's in_right)
+ *   } while (!done);
+ * With the same inputs every cell's arithmetic is that of the undivided
+ * slab's iteration (FP64 results agree bit for bit); only the order of the
+ * two global sums can differ.  Decomposed steps use the Woodbury solver and
+ * the multiple-balance scheme (OCI_EINVAL otherwise), ignore an attached
+ * network and the FP32 stall refinement (a step ends at tol or max_iter), and
+ * run one launch per iteration.  While a decomposed step is open, every other
+ * call on the handle except these returns OCI_ESTATE. */
+
+/* Open a decomposed time step (initial iterate as in oci_step). */
+int oci_dd_begin(oci_handle *h);
+
+/* The current iterate's outgoing angular flux at the two faces: out_left gets
+ * the mu < 0 flux leaving through the left face, out_right the mu > 0 flux
+ * leaving through the right face; DEVICE pointers to [N/2][2] values (time
+ * moments k, k+1/2) of the handle's storage type (double in OCI_FP64, float in
+ * OCI_FP32), pair p = ordinate pair (mu_p, -mu_p) ascending in mu_p; either
+ * may be NULL.  Enqueued on the handle's stream, no synchronisation. */
+int oci_dd_export(oci_handle *h, void *out_left, void *out_right);
+
+/* The incident angular flux at the two faces for the next iteration: in_left
+ * the mu > 0 flux entering through the left face, in_right the mu < 0 flux
+ * entering through the right face; same layout and type as oci_dd_export;
+ * NULL keeps a face's own boundary condition.  Enqueued, no synchronisation. */
+int oci_dd_import(oci_handle *h, const void *in_left, const void *in_right);
+
+/* One OCI iteration of the sub-domain's cells; sums (HOST double[2]) receives
+ * sum (phi^{l+1} - phi^l)^2 and sum (phi^{l+1})^2 over its cells and the four
+ * moments.  Synchronises the handle's stream. */
+int oci_dd_iterate(oci_handle *h, double *sums);
+
+/* Take the step's decision from the sums totalled over all sub-domains (HOST
+ * double[2]): relative change sqrt(sums[0] / sums[1]) < tol ends the step
+ * (committed), max_iter iterations end it (committed only with
+ * commit_unconverged), a non-finite sum ends it with OCI_ENAN.  *done = 0:
+ * iterate again (returns OCI_OK); *done = 1: the step is closed and the
+ * return value and *stats (may be NULL) are those oci_step would give. */
+int oci_dd_decide(oci_handle *h, const double *sums, int32_t *done, oci_stats *stats);
+
 /* ------------------------------------------------- learned guess (oci_nn.h) */
 enum { OCI_NN_OFF = 0, OCI_NN_GUESS = 1, OCI_NN_GUESS_CORRECT = 2, OCI_NN_GUESS_ADAPTIVE = 3 };
 

@@ -84,6 +84,61 @@ int oci_nn_train_step(float *params, float *adam_m, float *adam_v, int32_t step,
                       const float *tgt, int32_t batch, int32_t n_cells, double *loss, void *workspace,
                       size_t workspace_bytes, void *stream);
 
+/* Trajectory data and controls of oci_nn_train. */
+typedef struct {
+    int32_t n_traj;            /* trajectories T >= 1 */
+    int32_t n_steps;           /* steps S >= 1 per trajectory; sample (t, n), n = 1..S, predicts step n */
+    int32_t n_cells;           /* cells J >= 1 (every trajectory the same size) */
+    const double *phi;         /* [T][S+1][J][4]: moments of the initial state (n = 0) and of
+                                  each converged step, as published by oci_fluxes_device */
+    const float *stat;         /* [T][J][4] static features (oci_nn_static_features) */
+    const float *qfeat;        /* [T][J] source feature (oci_nn_static_features) */
+    int32_t epochs;            /* >= 1 */
+    int32_t batch;             /* samples per minibatch, >= 1; the last incomplete batch of an
+                                  epoch is dropped */
+    float lr;                  /* peak learning rate; epoch e (0-based) uses
+                                  lr (1 + cos(pi e / epochs)) / 2 */
+    float val_frac;            /* fraction of the samples held out for validation, in [0, 1) */
+    uint64_t seed;             /* shuffle (and, with init_params NULL, initialisation) seed */
+    const float *init_params;  /* [count] starting parameters, or NULL for the library's
+                                  initialisation (below) */
+    void *stream;              /* cudaStream_t for all work */
+} oci_nn_train_cfg;
+
+/* What oci_nn_train did (host struct). */
+typedef struct {
+    int32_t epochs_done, steps_done;  /* Adam steps taken (step numbers 1..steps_done) */
+    int32_t n_train, n_val;           /* samples in the training and validation sets */
+    double train_loss;                /* mean loss of the sampled minibatches of the last epoch
+                                         (every 50th minibatch, starting with the first) */
+    double val_loss;                  /* mean loss over the validation minibatches after the last
+                                         epoch (batches of min(batch, n_val) samples; NaN if n_val = 0) */
+} oci_nn_train_stats;
+
+/* The whole training procedure of the network on trajectories that the
+ * library's own solver produced (the paper has no counterpart): minibatch
+ * Adam (oci_nn_train_step) on the mean-squared error of oci_nn_targets, with
+ * the sample order, the train/validation split and the learning-rate
+ * schedule fixed here so that a run is reproducible bit for bit.
+ *   Samples are numbered k = t S + (n - 1).  Shuffles are Fisher-Yates passes
+ *   "for i = len-1 down to 1: swap a[i] and a[j], j = h mod (i + 1)" with
+ *   h = splitmix64(seed + r * 2^32 + i), splitmix64 being Vigna's finaliser
+ *   (z = x + 0x9E3779B97F4A7C15; z = (z ^ z>>30) * 0xBF58476D1CE4E5B9;
+ *   z = (z ^ z>>27) * 0x94D049BB133111EB; return z ^ z>>31), all modulo 2^64.
+ *   Round r = 0 shuffles the list 0..T S - 1; its first floor(T S val_frac)
+ *   entries are the validation set, the rest the training list, which round
+ *   r = e + 1 shuffles in place at the start of epoch e.  Minibatch b of an
+ *   epoch is training-list entries [b batch, (b + 1) batch); Adam step numbers
+ *   count from 1 over the whole run.
+ *   Initialisation when init_params is NULL: every weight of a layer with CI
+ *   input channels is sqrt(6 / (5 CI)) (2 u - 1), u = (splitmix64(seed ^
+ *   0x5DEECE66D + i) >> 11) 2^-53 for flat parameter index i; biases 0.
+ * weights_out: DEVICE [count], the trained FP32 parameters.  stats: HOST, may
+ * be NULL.  Allocates its own device buffers (released before it returns) and
+ * synchronises `stream` while it runs.  Returns 0, 1 (OCI_EINVAL) for NULL
+ * data or out-of-range sizes, 2 (OCI_ENOMEM), 3 (OCI_ECUDA). */
+int oci_nn_train(const oci_nn_train_cfg *cfg, float *weights_out, oci_nn_train_stats *stats);
+
 /* Largest n_cells accepted by oci_nn_forward_noalloc. */
 #define OCI_NN_NOALLOC_MAX_CELLS 16384
 
@@ -98,7 +153,10 @@ int oci_nn_train_step(float *params, float *adam_m, float *adam_v, int32_t step,
  * memory plan), or a host that only hands over its input and output buffers.
  * Every GPU that loads the library holds the array until the process exits.
  * The first call on a device looks up the array's device address (with that
- * device current), so make the first call before any stream capture.  All
+ * device current), so make the first call before any stream capture; after a
+ * reset of the device's primary context (cudaDeviceReset) the next call looks
+ * it up again, so make that call before any capture too.  Devices with an
+ * index of 64 or more are not supported (OCI_EINVAL).  All
  * calls share the one array and it keeps the last call's contents: calls that
  * can overlap on the GPU (different streams, concurrent host threads) race,
  * so serialise them.  Nothing in it needs to start at zero.  in [13][n_cells]

@@ -82,6 +82,11 @@ SIGNATURES = {
     "oci_query": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "oci_profile_iterations": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(ctypes.c_double)]),
     "oci_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "oci_dd_begin": (ctypes.c_int, [_VP]),
+    "oci_dd_export": (ctypes.c_int, [_VP, _VP, _VP]),
+    "oci_dd_import": (ctypes.c_int, [_VP, _VP, _VP]),
+    "oci_dd_iterate": (ctypes.c_int, [_VP, _VP]),
+    "oci_dd_decide": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(OciStats)]),
     "oci_nn_attach": (ctypes.c_int, [_VP, _VP, _I32, _I32]),
     "oci_nn_static_features": (ctypes.c_int, [_VP, _VP, _VP]),
     # include/oci_nn.h
@@ -96,6 +101,7 @@ SIGNATURES = {
     "oci_nn_train_step": (ctypes.c_int, [_VP, _VP, _VP, _I32, ctypes.c_float, _VP, _VP, _I32, _I32,
                                          ctypes.POINTER(ctypes.c_double), _VP, ctypes.c_size_t, _VP]),
     "oci_nn_forward_noalloc": (ctypes.c_int, [_VP, _VP, _I32, _VP, _VP]),
+    "oci_nn_train": (ctypes.c_int, [_VP, _VP, _VP]),
     "oci_last_cuda_error": (ctypes.c_char_p, [_VP]),
 }
 
@@ -314,6 +320,38 @@ def oci_set_state(h, psi):
     _check(load_library().oci_set_state(h, _ptr(psi)), "oci_set_state", h)
 
 
+def oci_dd_begin(h):
+    _check(load_library().oci_dd_begin(h), "oci_dd_begin", h)
+
+
+def oci_dd_export(h, out_left, out_right):
+    """Outgoing cut fluxes into device tensors [N/2][2] of the handle's storage dtype (or None)."""
+    _check(load_library().oci_dd_export(h, _dp(out_left), _dp(out_right)), "oci_dd_export", h)
+
+
+def oci_dd_import(h, in_left, in_right):
+    """Incident cut fluxes from device tensors [N/2][2] (or None: keep the face's own condition)."""
+    _check(load_library().oci_dd_import(h, _dp(in_left), _dp(in_right)), "oci_dd_import", h)
+
+
+def oci_dd_iterate(h):
+    """One iteration of the sub-domain; returns its (sum dphi^2, sum phi^2)."""
+    sums = np.zeros(2)
+    _check(load_library().oci_dd_iterate(h, _ptr(sums)), "oci_dd_iterate", h)
+    return sums
+
+
+def oci_dd_decide(h, total):
+    """The step's decision from the global sums: (done, status, stats)."""
+    t = np.ascontiguousarray(total, dtype=np.float64)
+    done = ctypes.c_int32()
+    st = OciStats()
+    rc = load_library().oci_dd_decide(h, _ptr(t), ctypes.byref(done), ctypes.byref(st))
+    if rc not in (OCI_OK, OCI_ENOTCONV, OCI_ENAN):
+        _check(rc, "oci_dd_decide", h)
+    return bool(done.value), rc, st.as_dict()
+
+
 class Solver:
     """Owns one handle.  ``step()`` / ``si_step()`` advance one time step."""
 
@@ -448,3 +486,36 @@ def oci_nn_train_step(params, m, v, step, lr, inp, tgt, workspace, want_loss=Tru
            "oci_nn_train_step")
     return loss.value if want_loss else None
 
+
+
+class OciNNTrainCfg(ctypes.Structure):
+    _fields_ = [
+        ("n_traj", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("n_cells", ctypes.c_int32),
+        ("phi", ctypes.c_void_p), ("stat", ctypes.c_void_p), ("qfeat", ctypes.c_void_p),
+        ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("val_frac", ctypes.c_float),
+        ("seed", ctypes.c_uint64), ("init_params", ctypes.c_void_p), ("stream", ctypes.c_void_p),
+    ]
+
+
+class OciNNTrainStats(ctypes.Structure):
+    _fields_ = [
+        ("epochs_done", ctypes.c_int32), ("steps_done", ctypes.c_int32), ("n_train", ctypes.c_int32),
+        ("n_val", ctypes.c_int32), ("train_loss", ctypes.c_double), ("val_loss", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def oci_nn_train(phi, stat, qfeat, weights_out, epochs=20, batch=32, lr=1e-3, val_frac=0.05, seed=0,
+                 init_params=None, stream=None):
+    """The library's training procedure (oci_nn_train in oci_nn.h) on device
+    tensors phi [T][S+1][J][4] (float64), stat [T][J][4], qfeat [T][J] (float32);
+    writes the trained parameters into the device tensor weights_out and
+    returns the run's statistics."""
+    T, S1, J = phi.shape[0], phi.shape[1], phi.shape[2]
+    cfg = OciNNTrainCfg(T, S1 - 1, J, _dp(phi), _dp(stat), _dp(qfeat), int(epochs), int(batch), float(lr),
+                        float(val_frac), int(seed) & ((1 << 64) - 1), _dp(init_params), _stream(stream))
+    st = OciNNTrainStats()
+    _check(load_library().oci_nn_train(ctypes.byref(cfg), _dp(weights_out), ctypes.byref(st)), "oci_nn_train")
+    return st.as_dict()

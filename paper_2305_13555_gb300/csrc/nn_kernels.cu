@@ -11,9 +11,11 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <mutex>
+#include <vector>
 
 #include "../../include/oci_nn.h"
 
@@ -399,23 +401,97 @@ static __device__ __align__(256) unsigned char g_nn_scratch[kStaticWeightBytes +
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-void *g_scratch_addr[kMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id;  // context the address belongs to (0: none yet)
+    void *addr;
+};
+ScratchSlot g_scratch[kMaxDevices] = {};
+
+// Unique id of the calling thread's current CUDA context (driver entry points
+// resolved through the runtime, so the library does not link libcuda).
+int current_context_id(unsigned long long *id)
+{
+    typedef int (*get_current_t)(void **);
+    typedef int (*get_id_t)(void *, unsigned long long *);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+            qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+            return 3;
+        get_current = (get_current_t)a;
+        get_id = (get_id_t)b;
+    }
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, id) != 0) return 3;
+    return 0;
+}
 
 // Device address of g_nn_scratch on the current device (the host-side symbol
-// is only a stand-in).  Looked up once per device, with that device current.
+// is only a stand-in).  Looked up with that device current, once per device
+// and context: a reset of the device's primary context (cudaDeviceReset)
+// reloads the module, and the next call looks the address up again.
 int scratch_address(void **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 3;
     if (dev < 0 || dev >= kMaxDevices) return 1;
+    if (cudaSetDevice(dev) != cudaSuccess) return 3;  // makes the device's primary context current
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long ctx = 0;
+    if (current_context_id(&ctx)) return 3;
+    ScratchSlot &s = g_scratch[dev];
+    if (!s.addr || s.ctx_id != ctx) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_nn_scratch) != cudaSuccess || !p) return 3;
-        g_scratch_addr[dev] = p;
+        s.addr = p;
+        s.ctx_id = ctx;
     }
-    *out = g_scratch_addr[dev];
+    *out = s.addr;
     return 0;
+}
+
+// ------------------------------------------------------------ training driver
+// Minibatch gather of oci_nn_train: sample k = t S + (n - 1) of the list idx
+// (entries [b0, b0 + B)) -> phi_n, phi_{n-1}, phi_{max(n-2, 0)} [B][J][4]
+// (double), stat [B][J][4] and qfeat [B][J].
+__global__ void k_gather(const double *__restrict__ phi, const float *__restrict__ stat,
+                         const float *__restrict__ qfeat, const int *__restrict__ idx, int b0, int S, int J,
+                         double *__restrict__ phin, double *__restrict__ phi1, double *__restrict__ phi2,
+                         float *__restrict__ st_b, float *__restrict__ qf_b)
+{
+    const int b = blockIdx.y;
+    const int k = idx[b0 + b];
+    const int t = k / S, n = k % S + 1;
+    const size_t JB = (size_t)J * 4;
+    const double *base = phi + (size_t)t * (S + 1) * JB;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < J * 4; e += gridDim.x * blockDim.x) {
+        phin[b * JB + e] = base[(size_t)n * JB + e];
+        phi1[b * JB + e] = base[(size_t)(n - 1) * JB + e];
+        phi2[b * JB + e] = base[(size_t)(n >= 2 ? n - 2 : 0) * JB + e];
+        st_b[b * JB + e] = stat[(size_t)t * JB + e];
+        if (e < J) qf_b[(size_t)b * J + e] = qfeat[(size_t)t * J + e];
+    }
+}
+
+// Vigna's splitmix64 finaliser (the generator the training order is defined by).
+inline uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void shuffle_round(std::vector<int> &a, uint64_t seed, uint64_t r)
+{
+    for (size_t i = a.size(); i-- > 1;) {
+        const uint64_t j = splitmix64(seed + (r << 32) + i) % (uint64_t)(i + 1);
+        std::swap(a[i], a[j]);
+    }
 }
 
 }  // namespace ocinn
@@ -495,6 +571,122 @@ int oci_nn_train_step(float *params, float *adam_m, float *adam_v, int32_t step,
     k_adam<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, adam_m, adam_v, w.grad, NPARAM, lr, b1, b2, 1e-8f, c1, c2,
                                                  w.wb);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int oci_nn_train(const oci_nn_train_cfg *cfg, float *weights_out, oci_nn_train_stats *stats)
+{
+    if (!cfg || !weights_out || !cfg->phi || !cfg->stat || !cfg->qfeat) return 1;
+    const int T = cfg->n_traj, S = cfg->n_steps, J = cfg->n_cells, B = cfg->batch;
+    if (T < 1 || S < 1 || J < 1 || B < 1 || cfg->epochs < 1 || !(cfg->val_frac >= 0.f && cfg->val_frac < 1.f) ||
+        (int64_t)T * S > (int64_t)1 << 30)
+        return 1;
+    cudaStream_t s = (cudaStream_t)cfg->stream;
+    const int n_all = T * S;
+    const int n_val = (int)std::floor((double)n_all * cfg->val_frac);
+    const int n_tr = n_all - n_val;
+    if (n_tr < B) return 1;  // not one full minibatch
+    std::vector<int> all(n_all);
+    for (int k = 0; k < n_all; ++k) all[k] = k;
+    shuffle_round(all, cfg->seed, 0);
+    std::vector<int> val(all.begin(), all.begin() + n_val), tr(all.begin() + n_val, all.end());
+    // device buffers: one allocation
+    const size_t cells = (size_t)B * J;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+    const size_t o_p = take(4 * (size_t)NPARAM), o_m = take(4 * (size_t)NPARAM), o_v = take(4 * (size_t)NPARAM);
+    const size_t o_idx = take(4 * (size_t)n_all);
+    const size_t o_phin = take(8 * cells * 4), o_phi1 = take(8 * cells * 4), o_phi2 = take(8 * cells * 4);
+    const size_t o_st = take(4 * cells * 4), o_qf = take(4 * cells), o_in = take(4 * cells * 13),
+                 o_tgt = take(4 * cells * 4), o_sc = take(4 * (size_t)B);
+    const size_t ws_bytes = workspace_layout(B, J, nullptr, nullptr);
+    const size_t o_ws = take(ws_bytes);
+    char *mem = nullptr;
+    if (cudaMalloc(&mem, off) != cudaSuccess) return 2;
+    float *p = (float *)(mem + o_p), *m = (float *)(mem + o_m), *v = (float *)(mem + o_v);
+    int *d_idx = (int *)(mem + o_idx);
+    double *phin = (double *)(mem + o_phin), *phi1 = (double *)(mem + o_phi1), *phi2 = (double *)(mem + o_phi2);
+    float *st_b = (float *)(mem + o_st), *qf_b = (float *)(mem + o_qf), *inp = (float *)(mem + o_in),
+          *tgt = (float *)(mem + o_tgt), *sc = (float *)(mem + o_sc);
+    void *ws = mem + o_ws;
+    int rc = 0;
+    auto cuda_ok = [&](cudaError_t e) { if (e != cudaSuccess && !rc) rc = 3; return rc == 0; };
+    if (cfg->init_params) {
+        cuda_ok(cudaMemcpyAsync(p, cfg->init_params, 4 * (size_t)NPARAM, cudaMemcpyDeviceToDevice, s));
+    } else {
+        std::vector<float> h(NPARAM, 0.f);
+        for (int l = 0; l < NL; ++l) {
+            const double bound = std::sqrt(6.0 / (KW * CH[l]));
+            for (int i = layer_off(l); i < layer_off(l) + layer_w(l); ++i) {
+                const double u = (double)(splitmix64((cfg->seed ^ 0x5DEECE66Dull) + (uint64_t)i) >> 11) *
+                                 (1.0 / 9007199254740992.0);
+                h[i] = (float)(bound * (2.0 * u - 1.0));
+            }
+        }
+        cuda_ok(cudaMemcpy(p, h.data(), 4 * (size_t)NPARAM, cudaMemcpyHostToDevice));
+    }
+    cuda_ok(cudaMemsetAsync(m, 0, 4 * (size_t)NPARAM, s));
+    cuda_ok(cudaMemsetAsync(v, 0, 4 * (size_t)NPARAM, s));
+    const dim3 ggrid((J * 4 + 255) / 256 < 64 ? (J * 4 + 255) / 256 : 64, 1);
+    auto batch_inputs = [&](int b0, int nb) {
+        k_gather<<<dim3(ggrid.x, nb), 256, 0, s>>>(cfg->phi, cfg->stat, cfg->qfeat, d_idx, b0, S, J, phin, phi1, phi2,
+                                                    st_b, qf_b);
+        if (!cuda_ok(cudaGetLastError())) return false;
+        if (oci_nn_features(phi1, phi2, st_b, qf_b, nb, J, inp, sc, s) || oci_nn_targets(phin, phi1, sc, nb, J, tgt, s)) {
+            if (!rc) rc = 3;
+            return false;
+        }
+        return true;
+    };
+    int step = 0, ep = 0;
+    double train_loss = NAN, val_loss = NAN;
+    for (ep = 0; ep < cfg->epochs && !rc; ++ep) {
+        shuffle_round(tr, cfg->seed, (uint64_t)ep + 1);
+        if (!cuda_ok(cudaMemcpyAsync(d_idx, tr.data(), 4 * (size_t)n_tr, cudaMemcpyHostToDevice, s))) break;
+        const float lr_ep = (float)(cfg->lr * 0.5 * (1.0 + std::cos(3.14159265358979323846 * ep / cfg->epochs)));
+        double lsum = 0.0;
+        int lcnt = 0;
+        for (int b0 = 0, bi = 0; b0 + B <= n_tr && !rc; b0 += B, ++bi) {
+            if (!batch_inputs(b0, B)) break;
+            ++step;
+            double l = 0.0;
+            const bool want = bi % 50 == 0;
+            if (oci_nn_train_step(p, m, v, step, lr_ep, inp, tgt, B, J, want ? &l : nullptr, ws, ws_bytes, s)) {
+                rc = 3;
+                break;
+            }
+            if (want) { lsum += l; ++lcnt; }
+        }
+        train_loss = lcnt ? lsum / lcnt : NAN;
+        if (rc) break;
+        // validation: the held-out samples in minibatches of min(batch, n_val)
+        if (n_val > 0) {
+            const int vb = n_val < B ? n_val : B;
+            if (!cuda_ok(cudaMemcpyAsync(d_idx, val.data(), 4 * (size_t)n_val, cudaMemcpyHostToDevice, s))) break;
+            double vs = 0.0;
+            int vc = 0;
+            for (int b0 = 0; b0 + vb <= n_val && !rc; b0 += vb) {
+                if (!batch_inputs(b0, vb)) break;
+                double l = 0.0;
+                if (oci_nn_loss_grad(p, inp, tgt, vb, J, nullptr, &l, ws, ws_bytes, s)) { rc = 3; break; }
+                vs += l;
+                ++vc;
+            }
+            val_loss = vc ? vs / vc : NAN;
+        }
+    }
+    if (!rc) cuda_ok(cudaMemcpyAsync(weights_out, p, 4 * (size_t)NPARAM, cudaMemcpyDeviceToDevice, s));
+    if (!rc) cuda_ok(cudaStreamSynchronize(s));
+    cudaStreamSynchronize(s);
+    cudaFree(mem);
+    if (stats) {
+        stats->epochs_done = ep;
+        stats->steps_done = step;
+        stats->n_train = n_tr;
+        stats->n_val = n_val;
+        stats->train_loss = train_loss;
+        stats->val_loss = val_loss;
+    }
+    return rc;
 }
 
 int oci_nn_forward_noalloc(const float *params, const float *in, int32_t n_cells, float *out, void *stream)

@@ -198,6 +198,9 @@ struct oci_handle {
     cudaEvent_t ev_done = nullptr, ev_q_ready = nullptr, ev_q_free = nullptr, ev_snap[2] = {nullptr, nullptr},
                 ev_d2h[2] = {nullptr, nullptr};
     double *phi_snap[2] = {nullptr, nullptr};
+    // domain decomposition (oci_dd_*): a step driven one iteration at a time
+    bool dd_active = false;
+    int dd_iter = 0;
     int snap_k = 0;
     bool step_pending = false, q_pending = false;
     bool pend_halo = false, pend_async = false;
@@ -610,7 +613,7 @@ int add_loop(oci_handle *h, cudaGraph_t g, const cudaGraphNode_t *dep, cudaGraph
 }
 
 // Step graph: begin -> [si_prep] -> WHILE { [march ->] cells } -> commit
-// (OCI with the persistent loop: begin -> loop -> commit).
+// (OCI with the persistent loop: begin -> loop, which ends the step itself).
 template <typename R>
 int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout, bool bar_loop = false)
 {
@@ -652,9 +655,12 @@ int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout
         return OCI_OK;
     }
     if (!si && h->use_loop) {
+        // the persistent loop ends the step itself (commit in the same launch)
         cudaGraphNode_t n_loop;
-        rc = add_loop(h, g, &n_prev, &n_loop, a_plain);
-        if (!rc) rc = add_kernel(h, g, &n_commit, &n_loop, 1, h->ks.commit_oci, dim3(h->grid_pc), dim3(kBlock), a_plain);
+        KParams<R> lc = plain;
+        lc.loop_commit = 1;
+        void *a_lc[] = {&lc};
+        rc = add_loop(h, g, &n_prev, &n_loop, a_lc);
         if (rc) return rc;
         CK(h, cudaGraphInstantiate(eout, g, 0));
         *gout = g;
@@ -711,7 +717,8 @@ int build_graph(oci_handle *h, bool si, cudaGraph_t *gout, cudaGraphExec_t *eout
     return OCI_OK;
 }
 
-// Continuation of a paused OCI step: WHILE { cells } -> commit.
+// Continuation of a paused OCI step: WHILE { cells } -> commit (or the
+// persistent loop, which commits in the same launch).
 template <typename R>
 int build_cont_graph(oci_handle *h)
 {
@@ -724,9 +731,11 @@ int build_cont_graph(oci_handle *h)
     void *a_plain[] = {&plain};
     void *a_loop[] = {&loop};
     if (h->use_loop) {
-        cudaGraphNode_t n_loop, n_commit;
-        int rc = add_loop(h, g, nullptr, &n_loop, a_plain);
-        if (!rc) rc = add_kernel(h, g, &n_commit, &n_loop, 1, h->ks.commit_oci, dim3(h->grid_pc), dim3(kBlock), a_plain);
+        cudaGraphNode_t n_loop;
+        KParams<R> lc = plain;
+        lc.loop_commit = 1;
+        void *a_lc[] = {&lc};
+        int rc = add_loop(h, g, nullptr, &n_loop, a_lc);
         if (rc) return rc;
         CK(h, cudaGraphInstantiate(&h->exec_cont, g, 0));
         h->graph_cont = g;
@@ -778,7 +787,7 @@ int build_lin_graph(oci_handle *h)
 
 // OCI step with the BF16 halo: begin -> entry iteration (float faces in, BF16
 // out) -> BF16 persistent loop (until ST_SWITCH) -> exit iteration (BF16 in,
-// float out) -> FP32 persistent loop -> commit.  The last iteration always
+// float out) -> FP32 persistent loop (which commits).  The last iteration always
 // reads float faces, so the commit is the plain one.
 int build_halo_graph(oci_handle *h)
 {
@@ -789,7 +798,7 @@ int build_halo_graph(oci_handle *h)
     IterState *st = h->d_st;
     void *a_st[] = {&st};
     const dim3 grid(h->cells_grid), block(h->cells_block);
-    cudaGraphNode_t n_begin, n_entry, n_hloop, n_exit, n_loop, n_commit, n_zero;
+    cudaGraphNode_t n_begin, n_entry, n_hloop, n_exit, n_loop, n_zero;
     int rc = add_kernel(h, g, &n_begin, nullptr, 0, (const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st);
     if (!rc) rc = add_kernel(h, g, &n_entry, &n_begin, 1, h->hk.entry, grid, block, a_plain, h->cells_smem);
     if (rc) return rc;
@@ -805,9 +814,11 @@ int build_halo_graph(oci_handle *h)
     cudaLaunchAttributeValue v{};
     v.cooperative = 1;
     CK(h, cudaGraphKernelNodeSetAttribute(n_hloop, cudaLaunchAttributeCooperative, &v));
+    KParams<float> lc = plain;
+    lc.loop_commit = 1;
+    void *a_lc[] = {&lc};
     rc = add_kernel(h, g, &n_exit, &n_hloop, 1, h->hk.exit, grid, block, a_plain, h->cells_smem);
-    if (!rc) rc = add_loop(h, g, &n_exit, &n_loop, a_plain);
-    if (!rc) rc = add_kernel(h, g, &n_commit, &n_loop, 1, h->ks.commit_oci, dim3(h->grid_pc), dim3(kBlock), a_plain);
+    if (!rc) rc = add_loop(h, g, &n_exit, &n_loop, a_lc);
     if (rc) return rc;
     CK(h, cudaGraphInstantiate(&h->exec_oci_h, g, 0));
     h->graph_oci_h = g;
@@ -1183,10 +1194,67 @@ struct StepRange {
     ~StepRange() { nvtxRangePop(); }
 };
 
+// Domain decomposition: the cut faces of the iterate the next iteration reads
+// (face buffer (base + iter) & 1, read on the device).  Export: the outgoing
+// -mu flux at face 0 and +mu flux at face J (written by cells 0 and J-1);
+// import: the incident +mu flux at face 0 and -mu flux at face J (the boundary
+// slots, which no cell writes).  [P] r2 (k, k+1/2) per pair; NULL skips a side.
+template <typename R>
+__global__ void k_dd_faces(const IterState *st, r2<R> *fP0, r2<R> *fP1, r2<R> *fM0, r2<R> *fM1, int J, int P,
+                           r2<R> *left, r2<R> *right, int import)
+{
+    const int b = (st->base + st->iter) & 1;
+    r2<R> *fP = b ? fP1 : fP0, *fM = b ? fM1 : fM0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        if (import) {
+            if (left) fP[i] = left[i];
+            if (right) fM[(size_t)J * P + i] = right[i];
+        } else {
+            if (left) left[i] = fM[i];
+            if (right) right[i] = fP[(size_t)J * P + i];
+        }
+    }
+}
+
+// Domain decomposition: the step's decision taken from the global sums.
+__global__ void k_dd_decide(IterState *st, int status, double resid, double d2, double p2)
+{
+    st->status = status;
+    st->resid = resid;
+    st->d2 = d2;
+    st->p2 = p2;
+}
+
+int dd_faces(oci_handle *h, void *left, void *right, int import)
+{
+    const int grid = (h->P + 255) / 256;
+    if (h->prec == OCI_FP64)
+        k_dd_faces<double><<<grid, 256, 0, h->stream>>>(h->d_st, (r2<double> *)h->faceP[0], (r2<double> *)h->faceP[1],
+                                                        (r2<double> *)h->faceM[0], (r2<double> *)h->faceM[1], h->J,
+                                                        h->P, (r2<double> *)left, (r2<double> *)right, import);
+    else
+        k_dd_faces<float><<<grid, 256, 0, h->stream>>>(h->d_st, (r2<float> *)h->faceP[0], (r2<float> *)h->faceP[1],
+                                                       (r2<float> *)h->faceM[0], (r2<float> *)h->faceM[1], h->J, h->P,
+                                                       (r2<float> *)left, (r2<float> *)right, import);
+    CK(h, cudaGetLastError());
+    return OCI_OK;
+}
+
+// One OCI iteration as a single launch (no graph, no local decision: the
+// device controls of a decomposed step never end it).
+int dd_iteration(oci_handle *h)
+{
+    KParams<double> pd = make_params<double>(h, 0, 0);
+    KParams<float> pf = make_params<float>(h, 0, 0);
+    void *args[] = {h->prec == OCI_FP64 ? (void *)&pd : (void *)&pf};
+    CK(h, cudaLaunchKernel(h->cells_oci, dim3(h->cells_grid), dim3(h->cells_block), args, h->cells_smem, h->stream));
+    return OCI_OK;
+}
+
 int run_step(oci_handle *h, bool si, oci_stats *st)
 {
     if (!h) return OCI_EINVAL;
-    if (h->step_pending) return OCI_ESTATE;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
     const StepRange range(si ? "si_step" : (h->scheme == OCI_TIME_BE ? "oci_step (backward Euler)" : "oci_step"));
     CK(h, cudaSetDevice(h->device));
     int rc = ensure_graphs(h);
@@ -1575,7 +1643,7 @@ int oci_create(const oci_problem *p, oci_handle **out)
         }
     }
     if (h->use_async) {
-        // third face buffer pair, sync block + per-warp completion counts, per-warp partials
+        // third face buffer pair, sync block + per-block completion flags, per-block partials
         const size_t tw = (size_t)h->cells_grid * (size_t)(h->cells_block / 32);
         const size_t fa = (face + 256 + 255) & ~(size_t)255;
         h->as_zero_bytes = (sizeof(ocik::AsyncSync) + tw * 4 + 15) & ~(size_t)15;
@@ -1679,7 +1747,7 @@ int oci_set_source(oci_handle *h, const double *q)
 int oci_set_iteration(oci_handle *h, double tol, int32_t max_iter, int32_t commit_unconverged)
 {
     if (!h || !(tol >= 0.0) || max_iter < 1) return OCI_EINVAL;
-    if (h->step_pending) return OCI_ESTATE;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     h->cfg.tol = tol;
     h->cfg.max_iter = max_iter;
@@ -1690,7 +1758,7 @@ int oci_set_iteration(oci_handle *h, double tol, int32_t max_iter, int32_t commi
 int oci_set_stream(oci_handle *h, void *cuda_stream)
 {
     if (!h) return OCI_EINVAL;
-    if (h->step_pending) return OCI_ESTATE;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
     CK(h, cudaStreamSynchronize(h->stream));
     h->stream = (cudaStream_t)cuda_stream;
     return OCI_OK;
@@ -1699,7 +1767,7 @@ int oci_set_stream(oci_handle *h, void *cuda_stream)
 int oci_set_wait_limits(oci_handle *h, uint32_t poll_limit, int32_t barrier_shortfall)
 {
     if (!h || barrier_shortfall < 0) return OCI_EINVAL;
-    if (h->step_pending) return OCI_ESTATE;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
     h->cfg.bar_poll_limit = poll_limit;
     h->cfg.bar_shortfall = barrier_shortfall;
     return OCI_OK;
@@ -1708,7 +1776,7 @@ int oci_set_wait_limits(oci_handle *h, uint32_t poll_limit, int32_t barrier_shor
 int oci_set_halo(oci_handle *h, int32_t halo)
 {
     if (!h || (halo != OCI_HALO_FP32 && halo != OCI_HALO_BF16)) return OCI_EINVAL;
-    if (h->step_pending) return OCI_ESTATE;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     if (halo == OCI_HALO_BF16 && !h->exec_oci_h) {
         const int rc = halo_setup(h);
@@ -1721,7 +1789,7 @@ int oci_set_halo(oci_handle *h, int32_t halo)
 int oci_set_time_scheme(oci_handle *h, int32_t scheme)
 {
     if (!h || (scheme != OCI_TIME_MB && scheme != OCI_TIME_BE)) return OCI_EINVAL;
-    if (h->step_pending) return OCI_ESTATE;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     if (scheme == OCI_TIME_BE && !h->be_mem) {
         const int rc = be_setup(h);
@@ -1739,7 +1807,7 @@ int oci_set_time_scheme(oci_handle *h, int32_t scheme)
 int oci_set_solver(oci_handle *h, int32_t solver)
 {
     if (!h || (solver != OCI_SOLVER_WOODBURY && solver != OCI_SOLVER_DENSE)) return OCI_EINVAL;
-    if (h->step_pending) return OCI_ESTATE;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     if (solver == OCI_SOLVER_DENSE && !h->dense.mem) {
         const int rc = dense_setup(h);
@@ -1755,7 +1823,7 @@ int oci_set_solver(oci_handle *h, int32_t solver)
 int oci_set_sweep(oci_handle *h, int32_t sweep)
 {
     if (!h || (sweep != OCI_SWEEP_MARCH && sweep != OCI_SWEEP_SCAN)) return OCI_EINVAL;
-    if (h->step_pending) return OCI_ESTATE;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     if (sweep == h->sweep) return OCI_OK;
     if (sweep == OCI_SWEEP_SCAN && !h->scan_mem) {
@@ -1934,15 +2002,109 @@ int oci_get_state(const oci_handle *hc, double *psi)
 int oci_set_state(oci_handle *h, const double *psi)
 {
     if (!h || !psi) return OCI_EINVAL;
-    if (h->step_pending) return OCI_ESTATE;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     return load_state(h, psi);
+}
+
+int oci_dd_begin(oci_handle *h)
+{
+    if (!h) return OCI_EINVAL;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
+    if (h->solver != OCI_SOLVER_WOODBURY || h->scheme != OCI_TIME_MB) return OCI_EINVAL;
+    CK(h, cudaSetDevice(h->device));
+    int rc = apply_pending_source(h);
+    if (rc) return rc;
+    if (!h->guess_valid && (rc = launch_guess(h))) return rc;
+    // the step ends only by oci_dd_decide: no tolerance, count or stall exit on the device
+    IterConfig c = h->cfg;
+    c.tol = 0.0;
+    c.max_iter = 0x3fffffff;
+    c.stall_floor = 0.0;
+    c.pause_at = -1;
+    if ((rc = set_device_cfg(h, c))) return rc;
+    CK(h, cudaEventRecord(h->ev0, h->stream));
+    IterState *st = h->d_st;
+    void *a_st[] = {&st};
+    CK(h, cudaLaunchKernel((const void *)&ocik::k_step_begin, dim3(1), dim3(1), a_st, 0, h->stream));
+    h->dd_active = true;
+    h->dd_iter = 0;
+    return OCI_OK;
+}
+
+int oci_dd_export(oci_handle *h, void *out_left, void *out_right)
+{
+    if (!h) return OCI_EINVAL;
+    if (!h->dd_active) return OCI_ESTATE;
+    return dd_faces(h, out_left, out_right, 0);
+}
+
+int oci_dd_import(oci_handle *h, const void *in_left, const void *in_right)
+{
+    if (!h) return OCI_EINVAL;
+    if (!h->dd_active) return OCI_ESTATE;
+    return dd_faces(h, const_cast<void *>(in_left), const_cast<void *>(in_right), 1);
+}
+
+int oci_dd_iterate(oci_handle *h, double *sums)
+{
+    if (!h || !sums) return OCI_EINVAL;
+    if (!h->dd_active) return OCI_ESTATE;
+    int rc = dd_iteration(h);
+    IterState s{};
+    if (!rc) rc = read_state(h, &s);
+    if (rc) return rc;
+    ++h->dd_iter;
+    sums[0] = s.d2;
+    sums[1] = s.p2;
+    return OCI_OK;
+}
+
+int oci_dd_decide(oci_handle *h, const double *sums, int32_t *done, oci_stats *stats)
+{
+    if (!h || !sums || !done) return OCI_EINVAL;
+    if (!h->dd_active || h->dd_iter < 1) return OCI_ESTATE;
+    const double a = sums[0], b = sums[1];
+    double resid;
+    if (b > 0.0) resid = std::sqrt(a / b);
+    else resid = a == 0.0 ? 0.0 : INFINITY;
+    int ns = ocik::ST_RUNNING;
+    if (!(resid == resid) || !(a == a) || !(b == b) || std::isinf(b)) ns = ocik::ST_NAN;
+    else if (resid < h->cfg.tol) ns = ocik::ST_CONVERGED;
+    else if (h->dd_iter >= h->cfg.max_iter) ns = ocik::ST_MAXITER;
+    *done = ns != ocik::ST_RUNNING;
+    if (!*done) return OCI_OK;
+    void *a_dec[] = {&h->d_st, &ns, &resid, const_cast<double *>(&a), const_cast<double *>(&b)};
+    CK(h, cudaLaunchKernel((const void *)&k_dd_decide, dim3(1), dim3(1), a_dec, 0, h->stream));
+    KParams<double> pd = make_params<double>(h, 0, 0);
+    KParams<float> pf = make_params<float>(h, 0, 0);
+    void *args[] = {h->prec == OCI_FP64 ? (void *)&pd : (void *)&pf};
+    CK(h, cudaLaunchKernel(h->ks.commit_oci, dim3(h->grid_pc), dim3(kBlock), args, 0, h->stream));
+    CK(h, cudaEventRecord(h->ev1, h->stream));
+    IterState s{};
+    int rc = read_state(h, &s);
+    if (rc) return rc;
+    h->dd_active = false;
+    h->guess_valid = s.committed != 0;
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    const int status = map_status(s.status);
+    if (stats) {
+        *stats = oci_stats{};
+        stats->iters = s.iter;
+        stats->status = status;
+        stats->residual = resid;
+        stats->seconds = ms * 1e-3;
+        stats->committed = s.committed;
+        stats->launches = 3 + 3 * h->dd_iter;  // begin, decision, commit; per iteration import, export, cells
+    }
+    return status;
 }
 
 int oci_profile_iterations(oci_handle *h, int32_t n_iter, double *seconds_per_launch)
 {
     if (!h || n_iter < 1 || !seconds_per_launch) return OCI_EINVAL;
-    if (h->step_pending) return OCI_ESTATE;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     int rc = launch_guess(h);
     if (rc) return rc;
@@ -2075,7 +2237,7 @@ int oci_nn_attach(oci_handle *h, const float *params, int32_t mode, int32_t k_co
 {
     if (!h || mode < OCI_NN_OFF || mode > OCI_NN_GUESS_ADAPTIVE) return OCI_EINVAL;
     if (mode != OCI_NN_OFF && (!params || k_corr < 1)) return OCI_EINVAL;
-    if (h->step_pending) return OCI_ESTATE;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
     CK(h, cudaSetDevice(h->device));
     if (mode == OCI_NN_OFF) {
         h->nn_mode = OCI_NN_OFF;

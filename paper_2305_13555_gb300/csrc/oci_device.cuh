@@ -70,13 +70,13 @@ struct IterState {
 
 // Barrier-free persistent loop (k_cells_tma ASYNC): per-iteration arrival
 // counters and decisions, in a ring of four iterations.  Zeroed before each
-// launch together with the per-warp completion counts that follow it.
+// launch together with the per-block completion flags that follow it.
 struct AsyncRec {
     double resid, d2, p2, best;
     int status, stall, pad0, pad1;
 };
 struct AsyncSync {
-    unsigned cnt[4];      // warps that finished iteration rep (slot rep & 3), cumulative
+    unsigned cnt[4];      // blocks that finished iteration rep (slot rep & 3), cumulative
     unsigned tag[4];      // rep + 1 once the decision of iteration rep is in rec[rep & 3]
     unsigned exit_bar;    // blocks that reached the end of the launch
     unsigned pad[7];
@@ -314,12 +314,15 @@ struct KParams {
     double *loop_partials;
     unsigned *loop_bar;
     int loop_fixed;
+    // persistent OCI loop: end the step in the same launch (commit after the
+    // final decision) instead of a separate k_percell launch
+    int loop_commit;
     // BF16-halo phase of the FP32 OCI iteration: the face buffers as bf16 pairs
     // (pack_bf16x2), same layout and ping-pong parity as faceP / faceM
     unsigned *hfP[2];
     unsigned *hfM[2];
-    // barrier-free persistent loop: sync block, per-warp completion counts
-    // (iterations of this launch), per-block partials [4][blocks][3]
+    // barrier-free persistent loop: sync block, per-block completion flags
+    // (iterations of this launch finished), per-block partials [4][blocks][3]
     AsyncSync *as;
     unsigned *as_done;
     double *as_part;
@@ -744,41 +747,18 @@ __global__ void __launch_bounds__(256) k_cells(const KParams<R> p)
 constexpr unsigned kWaitLimit = 1u << 22;
 template <bool B> struct BoolTag { static constexpr bool value = B; };
 
-// Grid-wide barrier of the persistent loop (all blocks resident: cooperative
-// launch).  The arrival counter starts at 0 for each launch; the k-th barrier
-// waits until it reaches k * gridDim.x.  Bounded: false after kWaitLimit polls.
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *a)
 {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
     return v;
 }
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, unsigned limit)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(count, 1u);
-        bool ok = false;
-        for (unsigned it = 0; it < limit; ++it) {
-            if (ld_acquire_u32(count) >= target) {
-                ok = true;
-                break;
-            }
-            __nanosleep(32);
-        }
-        __threadfence();
-        s_ok = ok ? 1 : 0;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// Thread 0 alone meets the grid (the block's own writes were ordered before
-// it by a block barrier): release-arrive on count (fence, then the atomic),
-// then poll (bounded) with acquire loads until target arrivals; false when
-// the limit expired.  The acquire load that sees the target, followed by the
+// Grid-wide barrier of the persistent loop (all blocks resident: cooperative
+// launch).  The arrival counter starts at 0 for each launch; the k-th barrier
+// waits until it reaches k * gridDim.x.  Thread 0 alone meets the grid (the
+// block's own writes were ordered before it by a block barrier): release-
+// arrive on count (fence, then the atomic), then poll (bounded) with acquire
+// loads until target arrivals; false when the limit expired.  The acquire load that sees the target, followed by the
 // caller's block barrier, orders the other blocks' released writes before
 // every thread's later reads, so no fence follows it.
 __device__ __forceinline__ bool grid_arrive_wait(unsigned *count, unsigned target, unsigned limit)
@@ -921,25 +901,6 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *a)
     return v;
 }
 
-// Barrier-free loop, lane 0 before iteration rep (>= 1) of the launch: wait
-// until both ring neighbours finished iteration rep-1 and the decision of
-// iteration rep-2 is known.  Returns 1 to go on, 2 when a known decision ends
-// the step, 0 when the wait limit expired.
-__device__ __forceinline__ int async_wait(const AsyncSync *as, const unsigned *done, int left, int right, int rep,
-                                          unsigned limit)
-{
-    for (unsigned it = 0; it < limit; ++it) {
-        if (ld_acquire_u32(&as->tag[(rep - 1) & 3]) == (unsigned)rep)  // decision of rep-1 (every warp finished it)
-            return *(volatile const int *)&as->rec[(rep - 1) & 3].status == ST_RUNNING ? 1 : 2;
-        if (rep < 2 || ld_acquire_u32(&as->tag[(rep - 2) & 3]) == (unsigned)(rep - 1)) {
-            if (rep >= 2 && *(volatile const int *)&as->rec[(rep - 2) & 3].status != ST_RUNNING) return 2;
-            if (ld_acquire_u32(done + left) >= (unsigned)rep && ld_acquire_u32(done + right) >= (unsigned)rep) return 1;
-        }
-        __nanosleep(20);
-    }
-    return 0;
-}
-
 template <typename R, int LPC, int PPL, int MODE>
 __device__ __forceinline__ void percell_body(const KParams<R> &p, int gw, int nwarps, int frd, int fgs,
                                              const phi_t<R> *phi_psi, const phi_t<R> *phi_pub);
@@ -955,15 +916,20 @@ __device__ __forceinline__ void percell_body(const KParams<R> &p, int gw, int nw
 __host__ __device__ constexpr int tma_max_threads(int chunk, int ppl) { return (chunk >= 8 || ppl > 1) ? 384 : 576; }
 
 // ASYNC (persistent OCI loop, float faces): no grid barrier between
-// iterations.  A warp starts iteration rep once the warps owning the chunks
-// next to its own (its ring neighbours gw - 1, gw + 1) finished rep - 1 and the
-// decision of rep - 2 is known; the last warp of a block to finish an
-// iteration adds its block's warp partials, the last block adds the blocks'
-// partials and publishes the decision (fixed orders: the same sums every run).  An iteration may so run one
-// past the final one; the faces rotate through three buffers, so that
-// speculative iteration overwrites neither the last iteration's input faces
-// nor its moments, and it stops at the first chunk boundary after the decision
-// is seen.  The end of the step (commit) follows one grid barrier.
+// iterations.  Block b owns a contiguous run of chunks; only its two edge
+// chunks read faces another block writes.  Per iteration a block meets at one
+// block barrier; its warp 0 then publishes the block's partial sums of the
+// iteration just finished and a "finished" flag for the neighbouring blocks,
+// and arrives at a counter; the last block to arrive adds every block's
+// partial in a fixed order and publishes the decision (the same sums every
+// run).  The other warps go straight on with the next iteration's interior
+// chunks; an edge chunk waits for its neighbouring block's flag.  An
+// iteration may so start before the previous one is decided: the faces
+// rotate through three buffers, so that speculative iteration overwrites
+// neither the decided iteration's input faces nor its moments; it stops at the
+// first chunk boundary after the decision is seen, and no iteration starts
+// writing before the decision of the one two back is known.  The end of the
+// step (commit) follows one grid barrier.
 template <int LPC, int PPL, int CHUNK, int STAGES, int MODE, bool LOOP = false, int HALO = 0, bool ASYNC = false>
 __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(const KParams<float> p)
 {
@@ -1003,7 +969,19 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
 
     const int nchunks = (J + CPC - 1) / CPC;
     const int gw = blockIdx.x * wpb + warp, tw = gridDim.x * wpb;
-    const int nmine = gw < nchunks ? (nchunks - 1 - gw) / tw + 1 : 0;
+    // Chunk ownership.  Barrier loop: chunk gw + i tw (round robin over every
+    // warp of the grid).  ASYNC: block b owns the contiguous chunks [cb0, cb1),
+    // its warps take them round robin, and warp 0 takes its first chunk (the
+    // block's left edge) last, so that both edge chunks -- the only ones that
+    // read faces written by another block -- come at the end of an iteration.
+    const int cb0 = ASYNC ? (int)(((long long)blockIdx.x * nchunks) / gridDim.x) : 0;
+    const int cb1 = ASYNC ? (int)(((long long)(blockIdx.x + 1) * nchunks) / gridDim.x) : 0;
+    const int nmine = ASYNC ? (warp < cb1 - cb0 ? (cb1 - cb0 - 1 - warp) / wpb + 1 : 0)
+                            : (gw < nchunks ? (nchunks - 1 - gw) / tw + 1 : 0);
+    auto chunk_of = [&](int i) -> int {
+        if constexpr (ASYNC) return cb0 + warp + ((warp == 0 && nmine > 1) ? (i + 1) % nmine : i) * wpb;
+        else return gw + i * tw;
+    };
     // ring position of this iteration's local chunk 0 (the ring runs on across
     // the iterations of the persistent loop): local chunk i uses stage
     // (rp + i) % STAGES with phase parity ((rp + i) / STAGES) & 1
@@ -1013,7 +991,7 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
 
     auto issue_static = [&](int i) {  // lane 0: iteration-invariant copies of local chunk i
         if (i >= nmine) return;
-        const int c0 = (gw + i * tw) * CPC;
+        const int c0 = chunk_of(i) * CPC;
         const int nv = J - c0 < CPC ? J - c0 : CPC;
         unsigned char *st = ring + (size_t)stage_of(i) * sbytes;
         unsigned long long *bar = bars + stage_of(i);
@@ -1023,13 +1001,16 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
         bulk_g2s(st + oQ, p.cellq + c0, bQ, bar);
         bulk_g2s(st + oT, p.mat + c0, bT, bar);
     };
-    // complete the phases of copies issued for chunks that will not run
+    // complete the phases of copies issued for chunks that will not run (the
+    // ASYNC loop issues every copy of a chunk at once, none ahead of its iteration)
     auto drain_static = [&]() {
-        if (lane == 0)
-            for (int i = 0; i < STAGES - 1 && i < nmine; ++i) mbar_arrive(bars + stage_of(i));
-        for (int i = 0; i < STAGES - 1 && i < nmine; ++i) (void)mbar_wait(bars + stage_of(i), parity_of(i));
+        if constexpr (!ASYNC) {
+            if (lane == 0)
+                for (int i = 0; i < STAGES - 1 && i < nmine; ++i) mbar_arrive(bars + stage_of(i));
+            for (int i = 0; i < STAGES - 1 && i < nmine; ++i) (void)mbar_wait(bars + stage_of(i), parity_of(i));
+        }
     };
-    if (lane == 0)
+    if (!ASYNC && lane == 0)
         for (int i = 0; i < STAGES - 1; ++i) issue_static(i);
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
     int iter, base;
@@ -1081,20 +1062,142 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
     };
     int mK = -1;
     float4 kA = make_float4(0.f, 0.f, 0.f, 0.f), kB = kA;
-    // barrier-free loop: ring neighbours, wait limit, the launch's starting stall state
-    const int nb_left = (gw + tw - 1) % tw, nb_right = (gw + 1) % tw;
+    // ASYNC: the blocks owning the chunks next to this block's edges (-1: none;
+    // block b owns [floor(b n / G), floor((b + 1) n / G)), so chunk c belongs to
+    // block floor(((c + 1) G - 1) / n)), wait limit, the launch's starting stall state
+    auto chunk_owner = [&](int c) { return (int)((((long long)c + 1) * gridDim.x - 1) / nchunks); };
+    const int nb_left = (ASYNC && cb1 > cb0 && cb0 > 0) ? chunk_owner(cb0 - 1) : -1;
+    const int nb_right = (ASYNC && cb1 > cb0 && cb1 < nchunks) ? chunk_owner(cb1) : -1;
     const unsigned shortfall = LOOP ? (unsigned)p.cfg->bar_shortfall : 0u;
     const unsigned wlimit = LOOP && p.cfg->bar_poll_limit ? p.cfg->bar_poll_limit : kWaitLimit;
     const int stall0 = stall;
     const double best0 = best;
-    // barrier-free loop: per-block warp partials and arrival counts of the last
-    // four iterations (the block's last warp of an iteration sums them)
-    __shared__ double s_wpart[ASYNC ? 4 : 1][ASYNC ? tma_max_threads(CHUNK, PPL) / 32 : 1][3];
-    __shared__ unsigned s_wcnt[4];
+    // ASYNC: per-warp partials of the last two iterations, and the block's stop flag
+    // (set by any warp that saw the step end; read by all after a block barrier)
+    __shared__ double s_wpart[ASYNC ? 2 : 1][ASYNC ? tma_max_threads(CHUNK, PPL) / 32 : 1][3];
+    // (two slots by iteration parity: iteration r sets slot r & 1, read by every
+    // thread after the block barrier at the top of iteration r + 1, while the
+    // first warps already running r + 1 may set the other slot)
+    __shared__ int s_stop[2];
     if constexpr (ASYNC) {
-        if (threadIdx.x < 4) s_wcnt[threadIdx.x] = 0u;
+        if (threadIdx.x < 2) s_stop[threadIdx.x] = 0;
         __syncthreads();
     }
+    // ASYNC, lane 0: bounded wait for the decision of iteration q of this launch;
+    // 1 the step goes on, 2 it ended there, 0 the wait ran out
+    auto wait_decision = [&](int q) -> int {
+        for (unsigned it = 0; it < wlimit; ++it) {
+            if (ld_acquire_u32(&p.as->tag[q & 3]) == (unsigned)q + 1u)
+                return *(volatile const int *)&p.as->rec[q & 3].status == ST_RUNNING ? 1 : 2;
+            __nanosleep(20);
+        }
+        return 0;
+    };
+
+    // End of a step inside the persistent loops (multiple balance: psi_{k+1/2} of
+    // every ordinate and corner, A^{-1}(c + s phi) with the incident faces the last
+    // iteration read (buffer frd_l), becomes psi_edge; its outgoing corners, in
+    // buffer fgs, are the next step's initial iterate; phi is published).  Each
+    // warp streams its own chunks through its ring, so the pass runs at an
+    // iteration's memory-level parallelism.  It starts at ring position rp with
+    // no copy in flight; it writes psi_edge of its own cells and buffer fgs.
+    auto ring_commit = [&](int frd_l, int fgs, const phi_t<R> *phf) {
+        auto issue_commit = [&](int i) {  // lane 0: every copy of local chunk i
+            if (i >= nmine) return;
+            const int c0 = chunk_of(i) * CPC;
+            const int nv = J - c0 < CPC ? J - c0 : CPC;
+            unsigned char *stg = ring + (size_t)stage_of(i) * sbytes;
+            unsigned long long *bar = bars + stage_of(i);
+            const unsigned bF = round16(nv * P * 8u), bE = round16(nv * P * 16u), bQ = nv * 16u,
+                           bT = round16(nv * 4u);
+            mbar_expect_tx_arrive(bar, 2 * bF + bE + bQ + bT);
+            bulk_g2s(stg + oP, p.faceP[frd_l] + (size_t)c0 * P, bF, bar);
+            bulk_g2s(stg + oM, p.faceM[frd_l] + (size_t)(c0 + 1) * P, bF, bar);
+            bulk_g2s(stg + oE, p.psi_edge + (size_t)c0 * P, bE, bar);
+            bulk_g2s(stg + oQ, p.cellq + c0, bQ, bar);
+            bulk_g2s(stg + oT, p.mat + c0, bT, bar);
+        };
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.global;\n" ::: "memory");
+            for (int i = 0; i < STAGES - 1; ++i) issue_commit(i);
+        }
+        int broke = nmine;
+        for (int i = 0; i < nmine; ++i) {
+            if (lane == 0) {
+                fence_proxy_async();
+                issue_commit(i + STAGES - 1);
+            }
+            const int chunk = chunk_of(i);
+            // this lane's rows' moments, loaded before the wait
+            float2 fph[CHUNK][4];
+#pragma unroll
+            for (int r = 0; r < CHUNK; ++r) {
+                const int cell = chunk * CPC + r * SPW + seg;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    fph[r][c] = cell < J ? __ldcg(phf + 4 * (size_t)cell + c) : make_float2(0.f, 0.f);
+            }
+            if (!mbar_wait(bars + stage_of(i), parity_of(i))) {
+                broke = i;
+                break;
+            }
+            const unsigned char *stg = ring + (size_t)stage_of(i) * sbytes;
+            const r2<R> *sP = reinterpret_cast<const r2<R> *>(stg + oP);
+            const r2<R> *sM = reinterpret_cast<const r2<R> *>(stg + oM);
+            const r4<R> *sE = reinterpret_cast<const r4<R> *>(stg + oE);
+            const r4<R> *sQ = reinterpret_cast<const r4<R> *>(stg + oQ);
+            const int *sT = reinterpret_cast<const int *>(stg + oT);
+#pragma unroll
+            for (int r = 0; r < CHUNK; ++r) {
+                const int cl = r * SPW + seg;
+                const int cell = chunk * CPC + cl;
+                if (cell >= J) continue;
+                coefs(sT[cl]);
+                const r4<R> qd = sQ[cl];
+                const R Fkl = PhiStore<R>::real(fph[r][0]) * cs, Fkr = PhiStore<R>::real(fph[r][1]) * cs,
+                        Fhl = PhiStore<R>::real(fph[r][2]) * cs, Fhr = PhiStore<R>::real(fph[r][3]) * cs;
+#pragma unroll
+                for (int t = 0; t < PPL; ++t) {
+                    const int pp = ls + LPC * t;
+                    if (pp >= P) continue;
+                    const Coef<R> &a = ac[t];
+                    const r4<R> pe = sE[cl * P + pp];
+                    const r2<R> inP = (refl_l && cell == 0) ? ldcg2(p.faceM[frd_l] + pp) : sP[cl * P + pp];
+                    const r2<R> inM = (refl_r && cell == J - 1) ? ldcg2(p.faceP[frd_l] + (size_t)J * P + pp)
+                                                                : sM[cl * P + pp];
+                    R ukr = qd.x + ce * pe.x + Fkl, uki = qd.y + ce * pe.y + Fkr, uhr = qd.z + Fhl, uhi = qd.w + Fhr;
+                    R vkr = qd.x + ce * pe.z + Fkl, vki = -(qd.y + ce * pe.w) - Fkr, vhr = qd.z + Fhl,
+                      vhi = -qd.w - Fhr;
+                    ukr += mw[t].x * inP.x; uhr += mw[t].x * inP.y;
+                    vki -= mw[t].x * inM.x; vhi -= mw[t].x * inM.y;
+                    // end-of-step components (k+1/2): second rows of A^{-1}
+                    const R phr_ = a.ur * ukr - a.ui * uki + a.vr * uhr - a.vi * uhi;
+                    const R phi_ = a.ur * uki + a.ui * ukr + a.vr * uhi + a.vi * uhr;
+                    const R mhr = a.ur * vkr - a.ui * vki + a.vr * vhr - a.vi * vhi;
+                    const R mhi = a.ur * vki + a.ui * vkr + a.vr * vhi + a.vi * vhr;
+                    st4(p.psi_edge + (size_t)cell * P + pp, phr_, phi_, mhr, -mhi);
+                    st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, phi_, phi_);
+                    st2(p.faceM[fgs] + (size_t)cell * P + pp, mhr, mhr);
+                }
+                for (int c = ls; c < 4; c += LPC) {
+                    const float2 v = c == 0 ? fph[r][0] : c == 1 ? fph[r][1] : c == 2 ? fph[r][2] : fph[r][3];
+                    p.phi_out[4 * (size_t)cell + c] = PhiStore<R>::wide(v);
+                    p.phi0[4 * (size_t)cell + c] = (c & 1) ? fph[r][3] : fph[r][2];
+                }
+            }
+            fence_proxy_async();
+            __syncwarp();  // stage i fully read before a copy reuses it
+        }
+        if (broke < nmine) {
+            // a copy never completed: record it and wait (bounded) for this warp's
+            // outstanding copies before the shared memory goes
+            if (lane == 0) atomicExch(&p.st->status, ST_TIMEOUT);
+            const int last = broke + STAGES - 1 < nmine ? broke + STAGES - 1 : nmine - 1;
+            for (int k = broke; k <= last; ++k) (void)mbar_wait(bars + stage_of(k), parity_of(k));
+        } else {
+            rp += nmine;
+        }
+    };
 
     for (int rep = 0;; ++rep) {
         const int frd = ASYNC ? (base + iter) % 3 : (PING ? ((base + iter) & 1) : base);
@@ -1119,7 +1222,7 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
 
         auto issue_faces = [&](int i) {  // lane 0: this iteration's incident faces of local chunk i
             if (i >= nmine) return;
-            const int c0 = (gw + i * tw) * CPC;
+            const int c0 = chunk_of(i) * CPC;
             const int nv = J - c0 < CPC ? J - c0 : CPC;
             unsigned char *st = ring + (size_t)stage_of(i) * sbytes;
             unsigned long long *bar = bars + stage_of(i);
@@ -1130,7 +1233,32 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
         };
         auto issue = [&](int i) {  // lane 0: all copies of local chunk i
             if (i >= nmine) return;
-            const int c0 = (gw + i * tw) * CPC;
+            if constexpr (ASYNC) {
+                // an edge chunk reads faces the neighbouring block wrote in the
+                // previous iteration: wait (bounded) until that block published it
+                const int c = chunk_of(i);
+                if (rep > 0 && ((c == cb0 && nb_left >= 0) || (c == cb1 - 1 && nb_right >= 0))) {
+                    // A neighbour that stopped does not publish: it stopped because the
+                    // decision of iteration rep - 2 ended the step, which ends this one too.
+                    int ok = 1;
+                    for (int s = 0; s < 2 && ok == 1; ++s) {
+                        const int nb = s == 0 ? (c == cb0 ? nb_left : -1) : (c == cb1 - 1 ? nb_right : -1);
+                        if (nb < 0) continue;
+                        for (unsigned it = 0; ld_acquire_u32(p.as_done + nb) < (unsigned)rep; ++it) {
+                            if (it >= wlimit) { ok = 0; break; }
+                            if (rep >= 2 && ld_acquire_u32(&p.as->tag[(rep - 2) & 3]) == (unsigned)rep - 1u &&
+                                *(volatile const int *)&p.as->rec[(rep - 2) & 3].status != ST_RUNNING) { ok = 2; break; }
+                            __nanosleep(20);
+                        }
+                    }
+                    if (ok != 1) {
+                        if (ok == 0) atomicExch(&p.st->status, ST_TIMEOUT);
+                        s_stop[rep & 1] = 1;
+                    }
+                    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+                }
+            }
+            const int c0 = chunk_of(i) * CPC;
             const int nv = J - c0 < CPC ? J - c0 : CPC;
             unsigned char *st = ring + (size_t)stage_of(i) * sbytes;
             unsigned long long *bar = bars + stage_of(i);
@@ -1145,38 +1273,142 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
         };
         if constexpr (ASYNC) {
             if (rep > 0) {
-                int go = 0;
-                if (lane == 0) go = async_wait(p.as, p.as_done, nb_left, nb_right, rep, wlimit);
-                go = __shfl_sync(FULL, go, 0);
-                if (go != 1) {
-                    if (go == 0 && lane == 0) atomicExch(&p.st->status, ST_TIMEOUT);
-                    drain_static();
-                    break;
+                __syncthreads();  // every warp of the block finished (or gave up) iteration rep - 1
+                if (s_stop[(rep - 1) & 1]) break;
+                if (warp == 0) {
+                    // publish iteration q = rep - 1: the block's partial (its warps' in
+                    // a fixed order), then "finished q" for the neighbouring blocks,
+                    // then the arrival; the last block to arrive sums every block's
+                    // partial in a fixed order and publishes the decision
+                    const int q = rep - 1;
+                    int closer = 0;
+                    if (lane == 0) {
+                        double a = 0.0, b = 0.0, f = 0.0;
+                        for (int w = 0; w < wpb; ++w) {
+                            a += s_wpart[q & 1][w][0];
+                            b += s_wpart[q & 1][w][1];
+                            f += s_wpart[q & 1][w][2];
+                        }
+                        double *pp = p.as_part + ((size_t)(q & 3) * gridDim.x + blockIdx.x) * 3;
+                        pp[0] = a;
+                        pp[1] = b;
+                        pp[2] = f;
+                        // the block's faces and moments of q (ordered before this thread by
+                        // the block barrier) and the partial, before the flag and the count
+                        __threadfence();
+                        st_release_u32(p.as_done + blockIdx.x, (unsigned)rep);
+                        const unsigned old = atomicAdd(&p.as->cnt[q & 3], 1u);
+                        closer = old + 1u == (unsigned)((q >> 2) + 1) * gridDim.x + shortfall ? 1 : 0;
+                    }
+                    closer = __shfl_sync(FULL, closer, 0);
+                    if (closer) {
+                        __threadfence();
+                        const double *pp = p.as_part + (size_t)(q & 3) * gridDim.x * 3;
+                        double a = 0.0, b = 0.0, f = 0.0;
+                        for (int k = lane; k < (int)gridDim.x; k += 32) {
+                            a += __ldcg(pp + 3 * k);
+                            b += __ldcg(pp + 3 * k + 1);
+                            f += __ldcg(pp + 3 * k + 2);
+                        }
+                        a = warp_sum(a);
+                        b = warp_sum(b);
+                        f = warp_sum(f);
+                        if (lane == 0) {
+                            int pstall = stall0, pstatus = ST_RUNNING;
+                            double pbest = best0;
+                            bool okq = true;
+                            if (q > 0) {
+                                // the previous decision's state (published before every
+                                // block could arrive for q; waited for all the same)
+                                okq = wait_decision(q - 1) != 0;
+                                const AsyncRec *pr = &p.as->rec[(q - 1) & 3];
+                                pstall = *(volatile const int *)&pr->stall;
+                                pbest = *(volatile const double *)&pr->best;
+                                pstatus = *(volatile const int *)&pr->status;
+                            }
+                            AsyncRec *rc = &p.as->rec[q & 3];
+                            if (okq && pstatus != ST_RUNNING) {
+                                // every block finished a speculative iteration after the
+                                // step had ended: keep the earlier decision
+                                rc->status = pstatus;
+                                rc->stall = pstall;
+                                rc->best = pbest;
+                            } else {
+                                const int it = iter;  // 1-based number of iteration q
+                                double resid;
+                                const int ns = loop_decision(a, b, f != 0.0 || !okq, it, fixed_left, false, p.cfg,
+                                                             pstall, pbest, resid);
+                                rc->resid = resid;
+                                rc->d2 = a;
+                                rc->p2 = b;
+                                rc->best = pbest;
+                                rc->stall = pstall;
+                                rc->status = ns;
+                                IterState *sw = p.st;
+                                sw->iter = it;
+                                sw->resid = resid;
+                                sw->d2 = a;
+                                sw->p2 = b;
+                                sw->stall = pstall;
+                                sw->best = pbest;
+                                sw->launches += 1;
+                                atomicCAS(&sw->status, ST_RUNNING, ns);  // a recorded timeout stays
+                            }
+                            __threadfence();
+                            st_release_u32(&p.as->tag[q & 3], (unsigned)q + 1u);
+                        }
+                    }
                 }
-                // the neighbours' generic stores (acquired above) before the bulk reads
+                // the block's own faces of rep - 1 (ordered by the block barrier)
+                // before this warp's bulk reads of them
                 if (lane == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
             }
+            // every copy of the first chunks of this iteration (an edge chunk waits
+            // for its neighbouring block inside issue)
+            if (lane == 0)
+                for (int i = 0; i < STAGES - 1; ++i) issue(i);
+        } else {
+            // (in the barrier loop the first chunks' faces of iterations after the
+            // first were issued right after the previous grid barrier)
+            if (lane == 0 && !(LOOP && rep > 0))
+                for (int i = 0; i < STAGES - 1; ++i) issue_faces(i);
         }
-        // (in the barrier loop the first chunks' faces of iterations after the
-        // first were issued right after the previous grid barrier)
-        if (lane == 0 && !(LOOP && !ASYNC && rep > 0))
-            for (int i = 0; i < STAGES - 1; ++i) issue_faces(i);
-        // barrier-free loop: the decision of the previous iteration, polled once
-        // per chunk (the load's latency hidden by the chunk's work)
+        // ASYNC: positions of the ring this iteration used; the decision of
+        // iteration rep - 1, polled once per chunk (the load's latency hidden by
+        // the chunk's work), ends a speculative iteration early
+        int consumed = nmine;
         bool prev_known = !ASYNC || rep == 0;
-        bool aborted = false;
+        bool skip = false;
+        if constexpr (ASYNC) {
+            if (rep >= 2) {
+                // this iteration overwrites the faces and moments iteration rep - 2
+                // read: its decision must be known (and not final) first
+                int go = 1;
+                if (lane == 0) go = wait_decision(rep - 2);
+                go = __shfl_sync(FULL, go, 0);
+                if (go != 1) {
+                    if (lane == 0) {
+                        if (go == 0) atomicExch(&p.st->status, ST_TIMEOUT);
+                        s_stop[rep & 1] = 1;
+                    }
+                    consumed = STAGES - 1 < nmine ? STAGES - 1 : nmine;
+                    for (int k = 0; k < consumed; ++k) (void)mbar_wait(bars + stage_of(k), parity_of(k));
+                    skip = true;
+                }
+            }
+        }
 
         float accf_d2 = 0.f, accf_p2 = 0.f;  // per-lane partials; block and grid sums in double
         bool ok_all = true;
         int broke_at = nmine;
-        for (int i = 0; i < nmine; ++i) {
+        for (int i = 0; i < (skip ? 0 : nmine); ++i) {
             if (lane == 0) {
                 fence_proxy_async();
                 issue(i + STAGES - 1);
             }
             unsigned poll_tag = 0;
             if (ASYNC && !prev_known && lane == 0 && i + 1 < nmine) poll_tag = ld_relaxed_u32(&p.as->tag[(rep - 1) & 3]);
-            const int chunk = gw + i * tw;
+            const int chunk = chunk_of(i);
             const unsigned char *st = ring + (size_t)stage_of(i) * sbytes;
             if (!mbar_wait(bars + stage_of(i), parity_of(i))) {
                 ok_all = false;
@@ -1393,14 +1625,12 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
                         // copies already issued for the next chunks have landed
                         const int last = i + STAGES < nmine ? i + STAGES : nmine;
                         for (int k = i + 1; k < last; ++k) (void)mbar_wait(bars + stage_of(k), parity_of(k));
-                        aborted = true;
+                        consumed = last;
+                        if (lane == 0) s_stop[rep & 1] = 1;
                         break;
                     }
                 }
             }
-        }
-        if constexpr (ASYNC) {
-            if (aborted) break;
         }
         if (!ok_all) {
             // a copy never completed: record it and wait (bounded) for this warp's
@@ -1415,88 +1645,16 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
                                HALO == 1 ? 1 : (HALO == 3 ? 3 : 0));
             return;
         } else if constexpr (ASYNC) {
-            rp += nmine;
+            // the warp's partial, added up by the block at the top of the next
+            // iteration; a copy that never completed stops the step
+            rp += consumed;
             const double wd2 = warp_sum((double)accf_d2), wp2 = warp_sum((double)accf_p2);
-            // the next iteration's invariant copies
-            if (lane == 0 && ok_all)
-                for (int i = 0; i < STAGES - 1; ++i) issue_static(i);
-            // publish: this iteration's face and moment stores (every lane's) before
-            // the completion count and the partials
-            __threadfence();
-            __syncwarp();
-            // two-level fixed-order sum: the block's last warp adds its warps'
-            // partials, the grid's last block adds the blocks' partials and decides
-            int closer = 0;
             if (lane == 0) {
-                s_wpart[rep & 3][warp][0] = wd2;
-                s_wpart[rep & 3][warp][1] = wp2;
-                s_wpart[rep & 3][warp][2] = ok_all ? 0.0 : 1.0;
-                __threadfence();  // faces, moments and the partial before the counts
-                st_release_u32(p.as_done + gw, (unsigned)rep + 1u);
-                const unsigned bold = atomicAdd(&s_wcnt[rep & 3], 1u);
-                if (bold + 1u == (unsigned)((rep >> 2) + 1) * (unsigned)wpb) {
-                    __threadfence_block();
-                    double a = 0.0, b = 0.0, f = 0.0;
-                    for (int w = 0; w < wpb; ++w) {
-                        a += *(volatile double *)&s_wpart[rep & 3][w][0];
-                        b += *(volatile double *)&s_wpart[rep & 3][w][1];
-                        f += *(volatile double *)&s_wpart[rep & 3][w][2];
-                    }
-                    double *pp = p.as_part + ((size_t)(rep & 3) * gridDim.x + blockIdx.x) * 3;
-                    pp[0] = a;
-                    pp[1] = b;
-                    pp[2] = f;
-                    __threadfence();
-                    const unsigned old = atomicAdd(&p.as->cnt[rep & 3], 1u);
-                    closer = old + 1u == (unsigned)((rep >> 2) + 1) * gridDim.x + shortfall ? 1 : 0;
-                }
+                s_wpart[rep & 1][warp][0] = wd2;
+                s_wpart[rep & 1][warp][1] = wp2;
+                s_wpart[rep & 1][warp][2] = ok_all ? 0.0 : 1.0;
+                if (!ok_all) s_stop[rep & 1] = 1;
             }
-            closer = __shfl_sync(FULL, closer, 0);
-            if (closer) {
-                // the last block of this iteration: every block's partial, in a fixed order
-                __threadfence();
-                const double *pp = p.as_part + (size_t)(rep & 3) * gridDim.x * 3;
-                double a = 0.0, b = 0.0, f = 0.0;
-                for (int q = lane; q < (int)gridDim.x; q += 32) {
-                    a += __ldcg(pp + 3 * q);
-                    b += __ldcg(pp + 3 * q + 1);
-                    f += __ldcg(pp + 3 * q + 2);
-                }
-                a = warp_sum(a);
-                b = warp_sum(b);
-                f = warp_sum(f);
-                if (lane == 0) {
-                    int pstall = stall0;
-                    double pbest = best0;
-                    if (rep > 0) {
-                        const AsyncRec *pr = &p.as->rec[(rep - 1) & 3];
-                        pstall = *(volatile const int *)&pr->stall;
-                        pbest = *(volatile const double *)&pr->best;
-                    }
-                    const int it = iter + 1;
-                    double resid;
-                    const int ns = loop_decision(a, b, f != 0.0, it, fixed_left, false, p.cfg, pstall, pbest, resid);
-                    AsyncRec *rc = &p.as->rec[rep & 3];
-                    rc->resid = resid;
-                    rc->d2 = a;
-                    rc->p2 = b;
-                    rc->best = pbest;
-                    rc->stall = pstall;
-                    rc->status = ns;
-                    IterState *sw = p.st;
-                    sw->iter = it;
-                    sw->resid = resid;
-                    sw->d2 = a;
-                    sw->p2 = b;
-                    sw->stall = pstall;
-                    sw->best = pbest;
-                    sw->launches += 1;
-                    atomicCAS(&sw->status, ST_RUNNING, ns);  // a recorded timeout stays
-                    __threadfence();
-                    st_release_u32(&p.as->tag[rep & 3], (unsigned)rep + 1u);
-                }
-            }
-            if (!ok_all) break;  // this warp's copies failed: it stops here
             iter += 1;
         } else {
             rp += nmine;
@@ -1543,7 +1701,7 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
                 const int nfrd = PING ? ((base + iter + 1) & 1) : base;
                 asm volatile("fence.proxy.async.global;\n" ::: "memory");
                 for (int i = 0; i < STAGES - 1 && i < nmine; ++i) {
-                    const int c0 = (gw + i * tw) * CPC;
+                    const int c0 = chunk_of(i) * CPC;
                     const int nv = J - c0 < CPC ? J - c0 : CPC;
                     unsigned char *stg = ring + (size_t)stage_of(i) * sbytes;
                     unsigned long long *bar = bars + stage_of(i);
@@ -1598,6 +1756,31 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
                 // in flight: wait for them before the block's shared memory goes
                 if (block_ok)
                     for (int i = 0; i < STAGES - 1 && i < nmine; ++i) (void)mbar_wait(bars + stage_of(i), parity_of(i));
+                if constexpr (HALO == 0) {
+                    // End of the step in the same launch (multiple balance: psi_{k+1/2}
+                    // of every ordinate and corner, A^{-1}(c + s phi) with the incident
+                    // faces the last iteration read, becomes psi_edge; its outgoing
+                    // corners are the next step's initial iterate; phi is published).
+                    // Every block took the same decision, and the faces the last
+                    // iteration read (buffer frd_last) and its moments were complete at
+                    // the grid barrier above.  Each warp streams its own chunks through
+                    // its ring again, so the pass runs at the iteration's memory-level
+                    // parallelism.  It writes psi_edge of its own cells and the other
+                    // face buffer, which other blocks' discarded prefetches may still be
+                    // reading.
+                    if (p.loop_commit && status != ST_RUNNING) {
+                        const bool go = status == ST_CONVERGED || (status == ST_MAXITER && cfg->commit_unconverged);
+                        const int frd_l = (base + it - 1) & 1, fgs = frd_l ^ 1;
+                        if (blockIdx.x == 0 && threadIdx.x == 0) {
+                            p.st->committed = go ? 1 : 0;
+                            p.st->base_next = go ? fgs : base;
+                        }
+                        if (go && block_ok) {
+                            rp += STAGES - 1;  // the prefetched positions are spent; their data is not used
+                            ring_commit(frd_l, fgs, p.phi[it & 1]);
+                        }
+                    }
+                }
                 return;
             }
         }
@@ -1628,7 +1811,7 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
             st->cur_face = (base + fit) % 3;
         }
         if (!go) return;
-        percell_body<float, LPC, PPL, C_COMMIT_OCI>(p, gw, tw, frd_last, g_buf, p.phi[fit & 1], p.phi[fit & 1]);
+        ring_commit(frd_last, g_buf, p.phi[fit & 1]);
     }
 }
 

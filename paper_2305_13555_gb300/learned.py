@@ -3,9 +3,10 @@
 The network (include/oci_nn.h) predicts a time step's converged scalar-flux
 moments from the two previous steps' moments and per-cell material / source
 inputs.  Its training data are trajectories produced by this library's own OCI
-solver on seeded slabs (``workloads.config5_train``); training runs the
-library's forward / backward / Adam kernels.  PyTorch only holds device arrays
-and gathers minibatches.  The paper has no learned component.
+solver on seeded slabs (``workloads.config5_train``); training is one
+call of the library's oci_nn_train (minibatches, epochs, schedule and
+validation inside the library, on its forward / backward / Adam kernels).
+PyTorch only holds device arrays.  The paper has no learned component.
 
 Usage (on a GPU):
     python -m paper_2305_13555_gb300.learned --trajectories 2000 --epochs 20 \
@@ -19,7 +20,7 @@ import time
 import numpy as np
 
 from . import (OCI_OK, Solver, oci_fluxes_device, oci_nn_features, oci_nn_forward, oci_nn_param_count,
-               oci_nn_predict, oci_nn_static_features, oci_nn_targets, oci_nn_train_step, oci_nn_workspace_bytes)
+               oci_nn_predict, oci_nn_static_features, oci_nn_workspace_bytes)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "data", "cnn_weights.npy")
@@ -66,72 +67,22 @@ def init_params(seed=0):
     return p
 
 
-def _batch(data, idx, t):
-    """Gather phi_n, phi_{n-1}, phi_{n-2} (clamped at 0) of samples (traj, n)."""
-    import torch
-    tr = torch.as_tensor(idx[:, 0], device="cuda")
-    n = torch.as_tensor(idx[:, 1], device="cuda")
-    phi = data["phi"]
-    return (phi[tr, n].contiguous(), phi[tr, n - 1].contiguous(),
-            phi[tr, torch.clamp(n - 2, min=0)].contiguous(), data["stat"][tr].contiguous(),
-            data["qfeat"][tr].contiguous())
-
-
 def train(data, epochs=20, batch=32, lr=1e-3, seed=0, params=None, log=print, val_frac=0.05):
-    """Minibatch Adam on all (trajectory, step) samples; returns (params, history)."""
+    """The library's training procedure (oci_nn_train): minibatch Adam over all
+    (trajectory, step) samples with a held-out validation set and a cosine
+    learning-rate schedule.  Returns (params, statistics)."""
     import torch
-    T, S1, J, _ = data["phi"].shape
-    g = np.random.default_rng(seed)
-    samples = np.array([(t, n) for t in range(T) for n in range(1, S1)], dtype=np.int64)
-    g.shuffle(samples)
-    n_val = max(1, int(len(samples) * val_frac))
-    val, tr = samples[:n_val], samples[n_val:]
-    p = torch.tensor(init_params(seed) if params is None else params, device="cuda")
-    m = torch.zeros_like(p)
-    v = torch.zeros_like(p)
-    ws = torch.empty(oci_nn_workspace_bytes(batch, J), dtype=torch.uint8, device="cuda")
-    inp = torch.empty((batch, 13, J), dtype=torch.float32, device="cuda")
-    tgt = torch.empty((batch, 4, J), dtype=torch.float32, device="cuda")
-    scale = torch.empty(batch, dtype=torch.float32, device="cuda")
-    hist, step = [], 0
-    for ep in range(epochs):
-        g.shuffle(tr)
-        t0 = time.time()
-        losses = []
-        lr_ep = lr * 0.5 * (1 + math.cos(math.pi * ep / max(epochs, 1)))  # cosine decay
-        for b0 in range(0, len(tr) - batch + 1, batch):
-            phin, phi1, phi2, st, qf = _batch(data, tr[b0:b0 + batch], None)
-            oci_nn_features(phi1, phi2, st, qf, inp, scale)
-            oci_nn_targets(phin, phi1, scale, tgt)
-            step += 1
-            want = (b0 // batch) % 50 == 0
-            l = oci_nn_train_step(p, m, v, step, lr_ep, inp, tgt, ws, want_loss=want)
-            if want:
-                losses.append(l)
-        vl = evaluate_loss(p, data, val, batch)
-        hist.append({"epoch": ep, "train_loss": float(np.mean(losses)), "val_loss": vl, "seconds": time.time() - t0})
-        if log:
-            log(f"epoch {ep}: train {hist[-1]['train_loss']:.3e} val {vl:.3e} ({hist[-1]['seconds']:.1f} s)")
-    return p.cpu().numpy(), hist
-
-
-def evaluate_loss(p, data, idx, batch):
-    """Mean squared error of the network on samples idx (no update)."""
-    import torch
-    from . import oci_nn_loss_grad
-    J = data["phi"].shape[2]
-    ws = torch.empty(oci_nn_workspace_bytes(batch, J), dtype=torch.uint8, device="cuda")
-    inp = torch.empty((batch, 13, J), dtype=torch.float32, device="cuda")
-    tgt = torch.empty((batch, 4, J), dtype=torch.float32, device="cuda")
-    scale = torch.empty(batch, dtype=torch.float32, device="cuda")
-    tot, cnt = 0.0, 0
-    for b0 in range(0, len(idx) - batch + 1, batch):
-        phin, phi1, phi2, st, qf = _batch(data, idx[b0:b0 + batch], None)
-        oci_nn_features(phi1, phi2, st, qf, inp, scale)
-        oci_nn_targets(phin, phi1, scale, tgt)
-        tot += oci_nn_loss_grad(p, inp, tgt, None, ws)
-        cnt += 1
-    return tot / max(cnt, 1)
+    from . import oci_nn_train
+    p0 = torch.tensor(init_params(seed) if params is None else params, device="cuda")
+    out = torch.empty_like(p0)
+    t0 = time.time()
+    st = oci_nn_train(data["phi"], data["stat"], data["qfeat"], out, epochs=epochs, batch=batch, lr=lr,
+                      val_frac=val_frac, seed=seed, init_params=p0)
+    st["seconds"] = time.time() - t0
+    if log:
+        log(f"{st['epochs_done']} epochs, {st['steps_done']} steps: train {st['train_loss']:.3e} "
+            f"val {st['val_loss']:.3e} ({st['seconds']:.1f} s)")
+    return out.cpu().numpy(), st
 
 
 def predict(params, phi1, phi2, stat, qfeat):
@@ -184,7 +135,7 @@ def main():
     params, hist = train(data, epochs=a.epochs, batch=a.batch, lr=a.lr)
     os.makedirs(os.path.dirname(a.out), exist_ok=True)
     np.save(a.out, params)
-    print(f"saved {params.size} parameters to {a.out}; final val loss {hist[-1]['val_loss']:.3e}")
+    print(f"saved {params.size} parameters to {a.out}; final val loss {hist['val_loss']:.3e}")
 
 
 if __name__ == "__main__":

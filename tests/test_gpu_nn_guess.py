@@ -91,6 +91,8 @@ def test_trajectory_generation_and_short_training():
     data = learned.trajectories(range(7, 15), J=512, N=8, n_steps=6)
     assert data["phi"].shape == (8, 7, 512, 4)
     assert (data["iters"] > 0).all()
-    p, hist = learned.train(data, epochs=6, batch=4, lr=2e-3, log=None)
-    assert hist[-1]["train_loss"] < hist[0]["train_loss"]
+    p1, st1 = learned.train(data, epochs=1, batch=4, lr=2e-3, log=None, val_frac=0.2)
+    p, st = learned.train(data, epochs=6, batch=4, lr=2e-3, log=None, val_frac=0.2)
+    assert st["epochs_done"] == 6 and st["steps_done"] == 6 * (st["n_train"] // 4)
+    assert st["val_loss"] < st1["val_loss"]
     assert np.isfinite(p).all()

@@ -16,7 +16,6 @@ import paper_2305_13555_gb300 as pkg
 pytestmark = pytest.mark.gpu
 
 MAX_CELLS = 16384  # OCI_NN_NOALLOC_MAX_CELLS
-TOL = 2e-5         # same bound as the network's forward test (FP32 accumulation)
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +46,26 @@ def test_noalloc_forward_matches_workspace_forward_twice(lib):
             torch.cuda.synchronize()
             r, o = ref.cpu().numpy(), out.cpu().numpy()
             assert np.isfinite(o).all()
-            assert np.abs(o - r).max() <= TOL * max(1.0, np.abs(r).max())
+            # the same kernels with the same launch shapes as oci_nn_forward: bit for bit
+            assert np.array_equal(o, r), np.abs(o - r).max()
+
+
+def test_noalloc_call_allocates_no_device_memory(lib):
+    """After the first call on the device (its set-up: the array's address), a
+    call leaves the device's free memory unchanged."""
+    g = np.random.default_rng(12)
+    J = 4096
+    params = torch.tensor(g.normal(0, 0.15, pkg.oci_nn_param_count()).astype(np.float32), device="cuda")
+    x = torch.tensor(g.normal(0, 1, (1, 13, J)).astype(np.float32), device="cuda")
+    out = torch.empty((1, 4, J), dtype=torch.float32, device="cuda")
+    assert _noalloc(lib, params, x, J, out) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert _noalloc(lib, params, x, J, out) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(lib):
