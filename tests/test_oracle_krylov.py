@@ -6,12 +6,19 @@ applications of that map as plain OCI needs iterations on the deployment
 family's thin, highly scattering cells: one application moves information one
 cell, and no Krylov combination of k applications reaches further than k
 cells.  Each GMRES iteration also pays the orthogonalisation, so on the GPU it
-could only be slower.  CPU only (scipy's GMRES as a library step)."""
+could only be slower.  Where OCI itself is slow for another reason -- thick,
+highly scattering cells in steady state, S_64 -- GMRES does cut the
+applications 2-5x, but on a bandwidth-bound device the Krylov basis traffic
+(each basis vector a third of an OCI iteration's bytes, read twice per
+GMRES iteration) costs as much as it saves at every restart size; and the
+transient configurations converge in a handful of iterations.  CPU only
+(scipy's GMRES as a library step)."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
+import oracle
 import workloads
 from oracle import brute
 
@@ -50,3 +57,71 @@ def test_gmres_on_the_oci_map_does_not_save_applications(seed):
     assert np.linalg.norm(x - x_ref) < 1e-6 * scale and np.linalg.norm(xg - x_ref) < 1e-6 * scale
     assert n_oci >= 50  # a slowly converging step of the deployment family
     assert n_gm >= 0.9 * n_oci, (n_oci, n_gm)
+
+
+# ------------------------------------------------- S_64, thick and low-c cells
+# Matrix-free on the oracle's own OCI iteration (the whole-problem matrix of a
+# 256-cell S_64 slab would not fit): the map G(psi) of one iteration is affine,
+# so the step's solution solves (I - B) psi = G(0) with B psi = G(psi) - G(0),
+# and GMRES whose operator is I - B applies G once per iteration.
+
+def _map_counts(prob, restarts, tol=1e-8):
+    J, N = prob["n_cells"], prob["n_ord"]
+    P = oracle.Problem(prob)
+    pe = np.zeros((J, N, 2))
+    n = J * N * 4
+    _, w = np.polynomial.legendre.leggauss(N)
+    calls = [0]
+
+    def G(v):
+        calls[0] += 1
+        return oracle.oci_iteration(P, pe, v.reshape(J, N, 4))[0].ravel()
+
+    g0 = G(np.zeros(n))
+    x, phi, n_oci = np.zeros(n), np.zeros((J, 4)), 0
+    while n_oci < 20000:  # plain OCI to a relative change of phi below tol
+        xn = G(x)
+        n_oci += 1
+        phin = np.einsum("n,jnc->jc", w, xn.reshape(J, N, 4))
+        done = np.linalg.norm(phin - phi) < tol * np.linalg.norm(phin)
+        x, phi = xn, phin
+        if done:
+            break
+    A = spla.LinearOperator((n, n), matvec=lambda v: v - (G(v) - g0))
+    out = {}
+    for m in restarts:
+        calls[0] = 0
+        xg, info = spla.gmres(A, g0, rtol=0.1 * tol, restart=m, maxiter=20000)
+        assert info == 0
+        phig = np.einsum("n,jnc->jc", w, xg.reshape(J, N, 4))
+        assert np.abs(phig - phi).max() < 1e-5 * np.abs(phi).max()
+        out[m] = calls[0]
+    return n_oci, out
+
+
+def _gpu_cost(apps, m):
+    """Modelled device cost of GMRES(m) in OCI-iteration equivalents: one OCI
+    application moves 24 B per cell-ordinate (FP32), a Krylov vector of the
+    incident-flux halo 8 B (two FP32 words), and classical Gram-Schmidt reads
+    each of the (on average (m + 1) / 2) basis vectors twice per iteration."""
+    return apps * (1.0 + 2.0 * (m + 1) / 2.0 * 8.0 / 24.0)
+
+
+def test_gmres_on_the_oci_map_thick_high_c_s64_saves_applications_not_bandwidth():
+    """Steady state (v -> infinity), c = 0.99, 10 mfp cells, S_64: GMRES on the
+    OCI map needs 2-4x fewer applications than plain OCI, but its basis
+    traffic eats the saving on a bandwidth-bound device at every restart size."""
+    prob = dict(workloads.homogeneous(256, 64, 1.0, 0.99, 10.0, 1.0, 0.05, 1.0, "vacuum", "vacuum"), v=float("inf"))
+    n_oci, gm = _map_counts(prob, (5, 30))
+    assert n_oci >= 60
+    assert gm[30] < 0.5 * n_oci and gm[5] < 0.6 * n_oci, (n_oci, gm)
+    for m, apps in gm.items():
+        assert _gpu_cost(apps, m) > 0.9 * n_oci, (m, apps, n_oci)
+
+
+def test_gmres_on_the_oci_map_transient_s64_saves_nothing():
+    """The transient configurations (dt = 0.05, 1/(v dt) = 20 per mfp) converge
+    in a handful of OCI iterations; GMRES needs at least as many applications."""
+    prob = workloads.homogeneous(256, 64, 1.0, 0.99, 1.0, 1.0, 0.05, 1.0, "vacuum", "vacuum")
+    n_oci, gm = _map_counts(prob, (30,))
+    assert n_oci <= 10 and gm[30] >= n_oci, (n_oci, gm)
