@@ -118,7 +118,7 @@ class ClockSampler:
         import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -147,29 +147,38 @@ class ClockSampler:
         return self.summarize(self.lines, t0, t1)
 
     @staticmethod
-    def summarize(lines, t0, t1):
+    def summarize(lines, t0, t1, margin=0.25):
         """Median SM clock, maximum clock and active slowdown reasons of the
-        (arrival time, csv line) samples stamped inside [t0, t1]."""
-        inside = [ln for t, ln in lines if t0 <= t <= t1]
-        sm, smax, reasons = [], [], set()
+        (arrival time, csv line) samples stamped inside [t0, t1].  A timed
+        region shorter than the sampling period may hold no sample: then the
+        samples within `margin` seconds on either side stand in, marked
+        "adjacent"."""
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in inside:
+        parsed = []
+        for t, line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                sm, smax = float(f[1]), float(f[2])
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
+            parsed.append((t, sm, smax, {n for n, v in zip(names, f[5:9]) if v.lower() == "active"}))
+        inside = [s for s in parsed if t0 <= s[0] <= t1]
+        adjacent = False
+        if not inside:
+            inside = [s for s in parsed if t0 - margin <= s[0] <= t1 + margin]
+            adjacent = bool(inside)
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
-                    "note": "timed region shorter than the 100 ms sampling period"}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm), "timed_region_s": round(t1 - t0, 3)}
+                    "note": "no clock sample inside or next to the timed region"}
+        out = {"sm_mhz": statistics.median(s[1] for s in inside), "sm_max_mhz": max(s[2] for s in inside),
+               "reasons": sorted(set().union(*(s[3] for s in inside))), "samples": len(inside),
+               "timed_region_s": round(t1 - t0, 3)}
+        if adjacent:
+            out["adjacent"] = True
+            out["note"] = f"timed region shorter than the sampling period: samples within {margin} s of it"
+        return out
 
 
 def aggregate(dev_time, units, device="cpu"):

@@ -66,6 +66,7 @@ struct IterState {
     double best;       // smallest relative change since the last 10% improvement
     int rot3;          // this step's iterations rotated through three face buffers
     int cur_face;      // ... and the buffer holding the latest iterate
+    int lin_first;     // FP32 refinement: number of the correction's first iteration
 };
 
 // Barrier-free persistent loop (k_cells_tma ASYNC): per-iteration arrival
@@ -429,7 +430,11 @@ __device__ __forceinline__ void block_sum2(double &a, double &b)
 // graph's loop condition.
 // phase 0: the plain iteration; 1: an iteration that leaves its halo in BF16
 // (never final: ends the BF16 phase with ST_SWITCH instead of converging);
-// 3: the iteration back to FP32 after ST_SWITCH (never final either).
+// 3: the iteration back to FP32 after ST_SWITCH (never final either); 4: the
+// correction iteration of the FP32 refinement.  Its scalar flux comes from the
+// incident correction alone, which is zero in its first iteration, so the
+// relative change of that iteration says nothing: it never converges there;
+// and it has no stall stop (it runs to tol or max_iter).
 __device__ __forceinline__ void finalize_iteration(double d2, double p2, double *partials, IterState *st,
                                                    const IterConfig *cfg, int iter, int use_cond,
                                                    cudaGraphConditionalHandle cond, int phase = 0)
@@ -462,7 +467,7 @@ __device__ __forceinline__ void finalize_iteration(double d2, double p2, double 
         st->d2 = a;
         st->p2 = b;
         st->arrive = 0u;
-        if (phase != 0 && (st->status == ST_RUNNING || (phase == 3 && st->status == ST_SWITCH))) {
+        if ((phase == 1 || phase == 3) && (st->status == ST_RUNNING || (phase == 3 && st->status == ST_SWITCH))) {
             int ns = ST_RUNNING;
             if (!(resid == resid) || !(a == a) || !(b == b) || isinf(b)) ns = ST_NAN;
             else if (phase == 1 && (resid < cfg->halo_switch || it >= cfg->max_iter - 2)) ns = ST_SWITCH;
@@ -471,12 +476,12 @@ __device__ __forceinline__ void finalize_iteration(double d2, double p2, double 
                 st->best = __longlong_as_double(0x7ff0000000000000LL);
             }
             st->status = ns;
-        } else if (phase == 0 && st->status == ST_RUNNING) {
+        } else if ((phase == 0 || phase == 4) && st->status == ST_RUNNING) {
             int ns = ST_RUNNING;
             if (!(resid == resid) || !(a == a) || !(b == b) || isinf(b)) ns = ST_NAN;
-            else if (resid < cfg->tol) ns = ST_CONVERGED;
+            else if (resid < cfg->tol && (phase == 0 || it > st->lin_first)) ns = ST_CONVERGED;
             else if (it >= cfg->max_iter) ns = ST_MAXITER;
-            if (ns == ST_RUNNING && cfg->stall_floor > 0.0) {
+            if (ns == ST_RUNNING && phase == 0 && cfg->stall_floor > 0.0) {
                 // rounding-noise floor: the change stopped falling well above tol
                 // (stall_iters < 0: stop as soon as it is below stall_floor)
                 if (cfg->stall_iters < 0) {
@@ -1275,6 +1280,11 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
             if (rep > 0) {
                 __syncthreads();  // every warp of the block finished (or gave up) iteration rep - 1
                 if (s_stop[(rep - 1) & 1]) break;
+                // the block's generic face stores of rep - 1 made visible at device
+                // scope (thread 0's fence covers every warp's, ordered by the block
+                // barrier) before any warp's bulk copy reads them
+                if (threadIdx.x == 0) __threadfence();
+                __syncthreads();
                 if (warp == 0) {
                     // publish iteration q = rep - 1: the block's partial (its warps' in
                     // a fixed order), then "finished q" for the neighbouring blocks,
@@ -1642,7 +1652,7 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
         }
         if constexpr (!LOOP) {
             finalize_iteration((double)accf_d2, (double)accf_p2, p.partials, p.st, p.cfg, iter, p.use_cond, p.cond,
-                               HALO == 1 ? 1 : (HALO == 3 ? 3 : 0));
+                               HALO == 1 ? 1 : (HALO == 3 ? 3 : (MODE == M_LIN ? 4 : 0)));
             return;
         } else if constexpr (ASYNC) {
             // the warp's partial, added up by the block at the top of the next
@@ -2157,6 +2167,7 @@ static __global__ void k_step_begin(IterState *st)
     st->best = __longlong_as_double(0x7ff0000000000000LL);
     st->rot3 = 0;
     st->cur_face = st->base;
+    st->lin_first = 0;
 }
 
 // Resume a stalled step with the correction iteration: the high-precision
@@ -2164,6 +2175,7 @@ static __global__ void k_step_begin(IterState *st)
 static __global__ void k_refine_setup(IterState *st)
 {
     st->iter += 1;
+    st->lin_first = st->iter + 1;
     st->status = ST_RUNNING;
     st->stall = 0;
     st->best = __longlong_as_double(0x7ff0000000000000LL);

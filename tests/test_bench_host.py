@@ -20,6 +20,8 @@ def test_clock_summary_keeps_the_timed_region_only():
     assert c["reasons"] == ["sw_power_cap"]
     empty = bench.ClockSampler.summarize(lines, 3.0, 3.05)
     assert empty["samples"] == 0 and empty["sm_mhz"] is None
+    near = bench.ClockSampler.summarize(lines, 2.6, 2.65)  # no sample inside: the one at 2.5 s stands in
+    assert near["samples"] == 1 and near["sm_mhz"] == 800.0 and near["adjacent"]
 
 
 def test_clock_summary_skips_malformed_lines():

@@ -1,8 +1,12 @@
 """What the trained network (paper_2305_13555_gb300/data/cnn_weights.npy,
 trained by paper_2305_13555_gb300.learned on 2000 OCI trajectories of 4096-cell
-S_16 slabs) gains over plain OCI on a thin-cell deployment slab: fewer
-iterations per converged step, and an answer as close to a tightly converged
-FP64 solve as plain OCI's at the same tolerance."""
+S_16 slabs) changes against plain OCI on thin-cell deployment slabs, measured
+on eight slabs fixed before any of them was looked at (seeds 101-108, the
+benchmark's GAIN_SEEDS).  The network only moves the initial iterate, so the
+answer stays that of plain OCI at the same tolerance; iteration counts go up
+on some slabs and down on others.  The adaptive mode measures that per slab:
+after its plain/guessed/guessed/plain trial it keeps the guess only where it
+saved iterations, and elsewhere runs at plain OCI's counts."""
 import numpy as np
 import pytest
 
@@ -12,6 +16,8 @@ from paper_2305_13555_gb300 import learned
 
 pytestmark = pytest.mark.gpu
 
+SEEDS = (101, 102, 103, 104, 105, 106, 107, 108)
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _lib():
@@ -20,63 +26,66 @@ def _lib():
     pkg.load_library()
 
 
-def _steps(prob, W, n, precision="fp32", tol=1e-8):
-    its, phis = [], []
+def _steps(prob, W, n, mode=None, precision="fp32", tol=1e-8):
+    its, phis, accepts, secs = [], [], [], []
     with pkg.Solver(prob, precision=precision, tol=tol, max_iter=50000) as s:
         if W is not None:
-            pkg.oci_nn_attach(s.h, W, pkg.OCI_NN_GUESS, 50)
+            pkg.oci_nn_attach(s.h, W, mode, 50)
         for _ in range(n):
             rc, st = s.step()
             assert rc == pkg.OCI_OK, (rc, st)
             its.append(st["iters"])
+            accepts.append(st["nn_accepts"])
+            secs.append(st["seconds"])
             phis.append(s.fluxes())
-    return np.array(its), np.array(phis)
+    return np.array(its), np.array(phis), accepts, np.array(secs)
 
 
-def _rel_l2(a, ref):
-    return np.sqrt(((a - ref) ** 2).sum(axis=(1, 2)) / (ref ** 2).sum(axis=(1, 2)))
+def _maxrel(a, ref):
+    return np.array([np.abs(x - r).max() / np.abs(r).max() for x, r in zip(a, ref)])
 
 
-def test_trained_guess_saves_iterations_on_thin_cells():
+def test_guess_keeps_the_answer():
+    """With the guess the converged fluxes are as close to a tightly converged
+    FP64 solve as plain OCI's at the same tolerance (both stop on the relative
+    change 1e-8; the error left is that change over 1 - rho)."""
     W = learned.load_weights()
-    n = 6
-    prob = workloads.config5_deploy(8, J=131072, N=64, n_steps=n)
-    plain_it, plain_phi = _steps(prob, None, n)
-    nn_it, nn_phi = _steps(prob, W, n)
-    _, ref_phi = _steps(prob, None, n, precision="fp64", tol=1e-12)
-    e_plain, e_nn = _rel_l2(plain_phi, ref_phi), _rel_l2(nn_phi, ref_phi)
-    print("iterations plain", plain_it.tolist(), "with learned guess", nn_it.tolist())
-    print("relative L2 error vs FP64 at 1e-12: plain", e_plain.tolist(), "learned", e_nn.tolist())
-    assert nn_it.sum() < 0.85 * plain_it.sum()
-    # Both stop on the same residual ||dphi|| / ||phi|| < 1e-8.  The error left
-    # behind is that residual over (1 - rho); 175 iterations from O(1) to 1e-8
-    # put rho near 0.9, i.e. errors of order 1e-7.  The guess must not make it
-    # worse than plain OCI's by more than that order.
-    assert np.all(e_plain < 1e-5)
-    assert np.all(e_nn < np.maximum(3 * e_plain, 3e-7))
+    n = 4
+    prob = workloads.config5_deploy(SEEDS[0], J=131072, N=64, n_steps=n)
+    _, plain_phi, _, _ = _steps(prob, None, n)
+    _, nn_phi, acc, _ = _steps(prob, W, n, pkg.OCI_NN_GUESS)
+    _, ref_phi, _, _ = _steps(prob, None, n, precision="fp64", tol=1e-12)
+    e_plain, e_nn = _maxrel(plain_phi, ref_phi), _maxrel(nn_phi, ref_phi)
+    print("max-norm error vs FP64 at 1e-12: plain", e_plain.tolist(), "learned guess", e_nn.tolist())
+    assert acc == [1] * n
+    assert np.all(e_plain < 3e-5)
+    assert np.all(e_nn < np.maximum(3 * e_plain, 3e-6))
 
 
-def test_adaptive_guess_falls_back_where_the_guess_does_not_pay():
-    """OCI_NN_GUESS_ADAPTIVE: after two plain lead-in steps and its plain /
-    guessed / guessed / plain trial it keeps the guess on the slabs where the
-    guess saves iterations and drops it on those where it costs iterations
-    (seeds 8 and 7, 9, 10 of the deployment family); every step still converges."""
+def test_adaptive_mode_over_the_pre_fixed_seeds():
+    """On each of the eight slabs: every step converges; after the trial
+    (steps 3-6) the adaptive mode either keeps the guess -- and then runs at
+    no more iterations than plain OCI -- or drops it and runs at plain OCI's
+    counts.  The means over the eight slabs are printed (the benchmark
+    reports them too)."""
     W = learned.load_weights()
     n = 9
-    for seed, keep in ((8, True), (7, False), (9, False), (10, False)):
+    rows = []
+    for seed in SEEDS:
         prob = workloads.config5_deploy(seed, J=131072, N=64, n_steps=n)
-        plain_it, _ = _steps(prob, None, n)
-        its = []
-        with pkg.Solver(prob, precision="fp32", tol=1e-8, max_iter=50000) as s:
-            pkg.oci_nn_attach(s.h, W, pkg.OCI_NN_GUESS_ADAPTIVE, 50)
-            for k in range(n):
-                rc, st = s.step()
-                assert rc == pkg.OCI_OK, (rc, st)
-                its.append(st["iters"])
-                guessed = k in (3, 4) or (k >= 6 and keep)
-                assert st["nn_accepts"] == (1 if guessed else 0), (seed, k, st)
-        print("seed", seed, "plain", plain_it.tolist(), "adaptive", its)
+        p_it, _, _, p_s = _steps(prob, None, n)
+        g_it, _, _, g_s = _steps(prob, W, n, pkg.OCI_NN_GUESS)
+        a_it, _, acc, a_s = _steps(prob, W, n, pkg.OCI_NN_GUESS_ADAPTIVE)
+        assert acc[:2] == [0, 0] and acc[2:6] == [0, 1, 1, 0], (seed, acc)
+        keep = acc[6] == 1
+        assert acc[6:] == [1 if keep else 0] * (n - 6), (seed, acc)
         if keep:
-            assert sum(its[6:]) < 0.85 * sum(plain_it[6:].tolist())
-        else:  # back on the plain path (states equal to within the tolerance)
-            assert all(abs(a - b) <= 5 for a, b in zip(its[6:], plain_it[6:].tolist())), (its, plain_it)
+            assert a_it[6:].sum() <= 1.03 * p_it[6:].sum(), (seed, a_it, p_it)
+        else:
+            assert np.all(np.abs(a_it[6:] - p_it[6:]) <= 5), (seed, a_it, p_it)
+        rows.append((seed, keep, g_it[2:].sum() / p_it[2:].sum(), a_it[2:].sum() / p_it[2:].sum(),
+                     g_s[2:].sum() / p_s[2:].sum(), a_s[2:].sum() / p_s[2:].sum()))
+        print("seed %d keep %s  iterations guess/plain %.2f adaptive/plain %.2f  time guess/plain %.2f "
+              "adaptive/plain %.2f" % rows[-1])
+    r = np.array([x[2:] for x in rows])
+    print("means over the eight slabs (iterations guess, adaptive; time guess, adaptive):", r.mean(axis=0).tolist())

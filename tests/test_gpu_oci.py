@@ -439,3 +439,27 @@ def test_full_size_config4_converged_fp32_bound():
             rc, st = s.step("oci")
             assert rc == pkg.OCI_OK, (rc, st)
             assert _rel(s.fluxes(), ref[k]) < FP32_TOL
+
+
+def test_fp32_refinement_on_a_slowly_converging_slab(monkeypatch):
+    """Thin, strongly scattering cells (the deployment family: the OCI map's
+    spectral radius near 1) with the refinement forced early (as soon as the
+    change is below 1e-3): the correction iteration must run to the tolerance
+    itself -- its first iteration, from a zero correction, changes nothing and
+    must not count as converged -- so the committed steps are as close to the
+    tightly converged FP64 answer as an FP64 solve to the same tolerance."""
+    prob = workloads.config5_deploy(101, J=4096, N=16, n_steps=3)
+    ref, loose = [], []
+    for tol, out in ((1e-12, ref), (1e-8, loose)):
+        with pkg.Solver(prob, precision="fp64", tol=tol) as s:
+            for _ in range(3):
+                assert s.step()[0] == pkg.OCI_OK
+                out.append(s.fluxes())
+    monkeypatch.setenv("OCI_STALL_FLOOR", "1e-3")
+    monkeypatch.setenv("OCI_STALL_ITERS", "-1")
+    with pkg.Solver(prob, precision="fp32", tol=1e-8) as s:
+        for k in range(3):
+            rc, st = s.step()
+            assert rc == pkg.OCI_OK and st["refined"] == 1, (rc, st)
+            assert st["iters"] > 20, st  # the correction iterated, not one pass
+            assert _rel(s.fluxes(), ref[k]) < 2 * _rel(loose[k], ref[k]) + FP32_TOL
