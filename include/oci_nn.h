@@ -12,8 +12,13 @@
  * zero padding of 2 cells at the slab ends, channels 13 -> 32 -> 32 -> 32 ->
  * 32 -> 4, ReLU after layers 1-4.  Parameters: one flat FP32 array, per layer
  * W[co][ci][5] (row-major) then b[co]; oci_nn_param_count() elements.  The
- * kernels use the weights rounded to BF16 and accumulate in FP32;
- * activations are FP32.
+ * kernels use the weights rounded to BF16 and accumulate in FP32.  Inference
+ * (oci_nn_forward, oci_nn_forward_noalloc, the guess in oci_step) runs each
+ * layer as a GEMM on the BF16 tensor cores, its input rounded to BF16
+ * (oci_nn_forward and the guess: the five layers in one kernel, activations
+ * in shared memory; oci_nn_forward_noalloc: one kernel per layer, the same
+ * results bit for bit); training (oci_nn_loss_grad, oci_nn_train_step,
+ * oci_nn_train) keeps the activations in FP32.
  *
  * Input channels per cell j (array in[b][13][J], FP32), with the per-sample
  * scale S = max(rms over cells and moments of phi1, rms of qfeat):
@@ -52,7 +57,9 @@ int32_t oci_nn_param_count(void);
 size_t oci_nn_workspace_bytes(int32_t batch, int32_t n_cells);
 
 /* Build the input channels: phi1, phi2 [B][J][4] double; stat [B][J][4] and
- * qfeat [B][J] float; writes in [B][13][J] and the per-sample scale [B]. */
+ * qfeat [B][J] float; writes in [B][13][J] and the per-sample scale [B].  The
+ * scale's partial sums pass through `in` before the channels are written, so
+ * `in` must not overlap the inputs. */
 int oci_nn_features(const double *phi1, const double *phi2, const float *stat, const float *qfeat,
                     int32_t batch, int32_t n_cells, float *in, float *scale, void *stream);
 

@@ -100,6 +100,271 @@ __global__ void __launch_bounds__(TX) k_conv(const float *__restrict__ in, const
     }
 }
 
+// ------------------------------------------------- forward conv, tensor cores
+// Inference form of the layer: the same contraction as a GEMM per tile of TX
+// cells, out[x][co] = sum_{k, ci} in[x + k - 2][ci] W[co][ci][k], on the BF16
+// tensor-core MMA (m16n8k16, FP32 accumulate): the layer's input rounded to
+// BF16 (the weights already are), bias and ReLU in FP32.  Shared memory holds
+// the input tile transposed to [x][ci] and the weights as [k][co][ci], both
+// with the channel index contiguous so that every fragment register is one
+// 32-bit load of two adjacent channels; row strides padded by 8 elements keep
+// the eight rows of a fragment in distinct banks.  Each of the four warps owns
+// 32 cells (two 16-row tiles) and every output channel (CO / 8 8-column tiles).
+template <int CI, int CO, bool RELU>
+__global__ void __launch_bounds__(TX) k_conv_mma(const float *__restrict__ in, const __nv_bfloat16 *__restrict__ W,
+                                                 const float *__restrict__ bias, float *__restrict__ out, int J)
+{
+    constexpr int KC = (CI + 15) / 16, CIP = KC * 16;  // 16-channel K chunks, padded input channels
+    constexpr int NT = (CO + 7) / 8, COP = NT * 8;     // 8-channel N tiles, padded output channels
+    constexpr int RS = CIP + 8;                        // row stride of both tiles (bf16 elements)
+    constexpr int XR = TX + 2 * PAD;                   // input rows of a tile
+    static_assert(TX == 128, "four warps of 32 cells");
+    __shared__ __align__(16) __nv_bfloat16 s_in[XR * RS];
+    __shared__ __align__(16) __nv_bfloat16 s_w[KW * COP * RS];
+    const int b = blockIdx.y, x0 = blockIdx.x * TX, t = threadIdx.x;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    for (int e = t; e < KW * COP * CIP; e += TX) {
+        const int ci = e % CIP, co = (e / CIP) % COP, k = e / (CIP * COP);
+        s_w[(k * COP + co) * RS + ci] = (ci < CI && co < CO) ? W[(co * CI + ci) * KW + k] : zero;
+    }
+    for (int e = t; e < CIP * XR; e += TX) {
+        const int ci = e / XR, xx = e % XR;
+        const int x = x0 + xx - PAD;
+        const float v = (ci < CI && x >= 0 && x < J) ? in[((size_t)b * CI + ci) * J + x] : 0.f;
+        s_in[xx * RS + ci] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+    const int warp = t >> 5, lane = t & 31, g = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = warp * 32 + mt * 16 + g;  // this lane's two rows: r0 and r0 + 8
+        float acc[NT][4];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+#pragma unroll
+            for (int kc = 0; kc < KC; ++kc) {
+                const int c = kc * 16 + 2 * tq;
+                const unsigned a0 = *reinterpret_cast<const unsigned *>(&s_in[(r0 + k) * RS + c]);
+                const unsigned a1 = *reinterpret_cast<const unsigned *>(&s_in[(r0 + 8 + k) * RS + c]);
+                const unsigned a2 = *reinterpret_cast<const unsigned *>(&s_in[(r0 + k) * RS + c + 8]);
+                const unsigned a3 = *reinterpret_cast<const unsigned *>(&s_in[(r0 + 8 + k) * RS + c + 8]);
+#pragma unroll
+                for (int n = 0; n < NT; ++n) {
+                    const __nv_bfloat16 *wr = &s_w[(k * COP + n * 8 + g) * RS + c];
+                    const unsigned b0 = *reinterpret_cast<const unsigned *>(wr);
+                    const unsigned b1 = *reinterpret_cast<const unsigned *>(wr + 8);
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                        "{%8, %9}, {%0, %1, %2, %3};\n"
+                        : "+f"(acc[n][0]), "+f"(acc[n][1]), "+f"(acc[n][2]), "+f"(acc[n][3])
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+                }
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < NT; ++n)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int co = n * 8 + 2 * tq + (h & 1);
+                const int x = x0 + r0 + (h >> 1) * 8;
+                if (co < CO && x < J) {
+                    float r = acc[n][h] + bias[co];
+                    if (RELU) r = fmaxf(r, 0.f);
+                    out[((size_t)b * CO + co) * J + x] = r;
+                }
+            }
+    }
+}
+
+// ------------------------------------------------------------- fused inference
+// All five layers of one tile of cells in one CTA, the activations kept in
+// shared memory.  Output cell x of the network depends on input cells x - 10 ..
+// x + 10 (five layers of half-width 2), so a tile of FOUT = 240 output cells
+// reads FB = 260 input rows; every layer computes FR = 256 rows (16 m-tiles of
+// the m16n8k16 MMA, two per warp) of which the valid region shrinks by two
+// rows per side and layer, ending on the tile's 240 cells.  Rows whose cell is
+// outside the slab are stored as zero after every layer (the zero padding of
+// each layer's input).  Arithmetic per output element is that of k_conv_mma
+// (same MMA sequence, FP32 bias and ReLU, the next layer's input rounded to
+// BF16), so the result is bit-identical to the per-layer kernels.
+// Shared image of the parameters (packed once per call by k_pack_fused): per
+// layer [k][co][ci] BF16 with row stride ci_padded + 8, then the FP32 biases.
+constexpr int FWARPS = 8, FTHREADS = FWARPS * 32;
+constexpr int FR = 16 * 2 * FWARPS;          // rows computed per layer
+constexpr int FB = FR + 2 * PAD;             // rows of each activation buffer
+constexpr int FOUT = FB - 2 * PAD * NL;      // valid output cells per tile
+constexpr int fcip(int l) { return ((CH[l] + 15) / 16) * 16; }
+constexpr int fcop(int l) { return ((CH[l + 1] + 7) / 8) * 8; }
+constexpr int frs(int l) { return fcip(l) + 8; }
+constexpr int fw_off(int l)
+{
+    int o = 0;
+    for (int i = 0; i < l; ++i) o += KW * fcop(i) * frs(i);
+    return o;
+}
+constexpr int FW_ELEMS = fw_off(NL);                      // BF16 weight elements
+constexpr int FBIAS = 4 * 32 + 8;                         // FP32 biases, layer by layer (last padded to 8)
+constexpr int fb_off(int l) { return l * 32; }
+constexpr int FPACK_BYTES = FW_ELEMS * 2 + FBIAS * 4;     // the packed image
+constexpr int FCI = CH[0], FCO = CH[NL];                  // network input and output channels
+constexpr int FRS_ACT = 32 + 8;                           // row stride of the 32-channel buffers
+constexpr int FSMEM = FPACK_BYTES + FB * frs(0) * 2 + 2 * FB * FRS_ACT * 2;
+static_assert(FPACK_BYTES % 16 == 0 && (FB * frs(0) * 2) % 16 == 0, "16-byte aligned regions");
+static_assert(4 * FOUT * 4 <= FB * frs(0) * 2, "output staging fits in the input buffer");
+
+template <int L>
+__device__ __forceinline__ void pack_layer(const float *__restrict__ params, __nv_bfloat16 *__restrict__ w,
+                                           float *__restrict__ bias, int r)
+{
+    constexpr int CI = CH[L], CO = CH[L + 1], RS = frs(L), COP = fcop(L), WOFF = layer_off(L);
+    constexpr int N = KW * COP * RS;
+    if (r < N) {
+        const int ci = r % RS, co = (r / RS) % COP, k = r / (RS * COP);
+        const float v = (ci < CI && co < CO) ? params[WOFF + (co * CI + ci) * KW + k] : 0.f;
+        w[fw_off(L) + r] = __float2bfloat16_rn(v);
+    } else if (r < N + 32) {
+        const int co = r - N;
+        if (L < NL - 1 || co < 8) bias[fb_off(L) + co] = co < CO ? params[WOFF + CI * CO * KW + co] : 0.f;
+    }
+}
+
+// one thread per element of a layer's weight image (and its biases): grid (blocks, NL)
+__global__ void k_pack_fused(const float *__restrict__ params, unsigned char *__restrict__ pack)
+{
+    __nv_bfloat16 *w = reinterpret_cast<__nv_bfloat16 *>(pack);
+    float *bias = reinterpret_cast<float *>(pack + FW_ELEMS * 2);
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    switch (blockIdx.y) {
+    case 0: pack_layer<0>(params, w, bias, r); break;
+    case 1: pack_layer<1>(params, w, bias, r); break;
+    case 2: pack_layer<2>(params, w, bias, r); break;
+    case 3: pack_layer<3>(params, w, bias, r); break;
+    default: pack_layer<4>(params, w, bias, r); break;
+    }
+}
+constexpr int FPACK_MAX_LAYER = KW * 32 * (32 + 8) + 32;  // elements of the largest layer image + biases
+
+// One layer over the tile: src rows [0, FB) (stride frs(L)) -> rows [2, FB - 2)
+// of dst (stride FRS_ACT, BF16, zero outside the slab), or, for the last layer,
+// the FP32 outputs of the tile's valid rows into dout[co][row - 2 PAD NL].
+template <int L>
+__device__ __forceinline__ void fused_layer(const __nv_bfloat16 *src, const __nv_bfloat16 *w, const float *bias,
+                                            __nv_bfloat16 *dst, float *dout, int xrow0, int J, int warp, int lane)
+{
+    constexpr int CO = CH[L + 1];
+    constexpr int KC = fcip(L) / 16, RS = frs(L);
+    constexpr int NT = fcop(L) / 8, COP = NT * 8;
+    const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi) {
+        const int i0 = 16 * (warp + FWARPS * mi) + g;  // input row of tap 0 for this lane's first output row
+        float acc[NT][4];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+#pragma unroll
+            for (int kc = 0; kc < KC; ++kc) {
+                const int c = kc * 16 + 2 * tq;
+                const unsigned a0 = *reinterpret_cast<const unsigned *>(&src[(i0 + k) * RS + c]);
+                const unsigned a1 = *reinterpret_cast<const unsigned *>(&src[(i0 + 8 + k) * RS + c]);
+                const unsigned a2 = *reinterpret_cast<const unsigned *>(&src[(i0 + k) * RS + c + 8]);
+                const unsigned a3 = *reinterpret_cast<const unsigned *>(&src[(i0 + 8 + k) * RS + c + 8]);
+#pragma unroll
+                for (int n = 0; n < NT; ++n) {
+                    const __nv_bfloat16 *wr = &w[(k * COP + n * 8 + g) * RS + c];
+                    const unsigned b0 = *reinterpret_cast<const unsigned *>(wr);
+                    const unsigned b1 = *reinterpret_cast<const unsigned *>(wr + 8);
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                        "{%8, %9}, {%0, %1, %2, %3};\n"
+                        : "+f"(acc[n][0]), "+f"(acc[n][1]), "+f"(acc[n][2]), "+f"(acc[n][3])
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+                }
+            }
+        }
+#pragma unroll
+        for (int hr = 0; hr < 2; ++hr) {  // this lane's output rows i0 + 2 and i0 + 10
+            const int o = i0 + PAD + 8 * hr;
+            const int x = xrow0 + o;
+            const bool inside = x >= 0 && x < J;
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                const int co = n * 8 + 2 * tq;
+                float v0 = acc[n][2 * hr] + bias[co], v1 = acc[n][2 * hr + 1] + bias[co + 1];
+                if (L < NL - 1) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                    if (!inside) v0 = v1 = 0.f;
+                    *reinterpret_cast<__nv_bfloat162 *>(&dst[o * FRS_ACT + co]) = __floats2bfloat162_rn(v0, v1);
+                } else {
+                    const int r = o - PAD * NL;
+                    if (r >= 0 && r < FOUT && co < CO) {
+                        dout[co * FOUT + r] = v0;
+                        dout[(co + 1) * FOUT + r] = v1;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Persistent over tiles (b, tile), two CTAs per SM; tile t of sample b covers
+// output cells [t FOUT, (t + 1) FOUT).
+__global__ void __launch_bounds__(FTHREADS, 2) k_forward_fused(const unsigned char *__restrict__ pack,
+                                                                const float *__restrict__ in, float *__restrict__ out,
+                                                                int B, int J)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const __nv_bfloat16 *s_w = reinterpret_cast<const __nv_bfloat16 *>(fsm);
+    const float *s_bias = reinterpret_cast<const float *>(fsm + FW_ELEMS * 2);
+    __nv_bfloat16 *s_x = reinterpret_cast<__nv_bfloat16 *>(fsm + FPACK_BYTES);
+    __nv_bfloat16 *s_a = s_x + FB * frs(0);
+    __nv_bfloat16 *s_b = s_a + FB * FRS_ACT;
+    float *s_out = reinterpret_cast<float *>(s_x);  // free once layer 0 has read it
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(pack);
+        uint4 *dst = reinterpret_cast<uint4 *>(fsm);
+        for (int e = t; e < FPACK_BYTES / 16; e += FTHREADS) dst[e] = src[e];
+        const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+        for (int e = t; e < 2 * PAD * FRS_ACT; e += FTHREADS) {  // edge rows no layer writes
+            const int r = e / FRS_ACT, c = e % FRS_ACT, row = r < PAD ? r : FB - 2 * PAD + r;
+            s_a[row * FRS_ACT + c] = zero;
+            s_b[row * FRS_ACT + c] = zero;
+        }
+    }
+    const int per = (J + FOUT - 1) / FOUT;
+    for (int tile = blockIdx.x; tile < B * per; tile += gridDim.x) {
+        const int b = tile / per, x0 = (tile % per) * FOUT;
+        const int xrow0 = x0 - PAD * NL;  // cell of buffer row 0
+        for (int e = t; e < fcip(0) * FB; e += FTHREADS) {
+            const int ci = e / FB, r = e % FB, x = xrow0 + r;
+            const float v = (ci < FCI && x >= 0 && x < J) ? in[((size_t)b * FCI + ci) * J + x] : 0.f;
+            s_x[r * frs(0) + ci] = __float2bfloat16_rn(v);
+        }
+        __syncthreads();
+        fused_layer<0>(s_x, s_w + fw_off(0), s_bias + fb_off(0), s_a, nullptr, xrow0, J, warp, lane);
+        __syncthreads();
+        fused_layer<1>(s_a, s_w + fw_off(1), s_bias + fb_off(1), s_b, nullptr, xrow0, J, warp, lane);
+        __syncthreads();
+        fused_layer<2>(s_b, s_w + fw_off(2), s_bias + fb_off(2), s_a, nullptr, xrow0, J, warp, lane);
+        __syncthreads();
+        fused_layer<3>(s_a, s_w + fw_off(3), s_bias + fb_off(3), s_b, nullptr, xrow0, J, warp, lane);
+        __syncthreads();
+        fused_layer<4>(s_b, s_w + fw_off(4), s_bias + fb_off(4), nullptr, s_out, xrow0, J, warp, lane);
+        __syncthreads();
+        const int nx = J - x0 < FOUT ? J - x0 : FOUT;
+        for (int e = t; e < FCO * FOUT; e += FTHREADS) {
+            const int co = e / FOUT, r = e % FOUT;
+            if (r < nx) out[((size_t)b * FCO + co) * J + x0 + r] = s_out[e];
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------- weight grad
 // Per tile of TX cells of one sample: partial dW[co][ci][k] = sum_x g[co][x]
 // in[ci][x+k-2] and db[co] = sum_x g[co][x], where g is the output gradient
@@ -219,31 +484,82 @@ __global__ void k_to_bf16(const float *__restrict__ p, int n, __nv_bfloat16 *__r
 // ------------------------------------------------------------- features
 // Per-sample scale S = sqrt(mean over cells and moments of phi1^2), floored by
 // the source scale, so that the network sees O(1) inputs at every flux level.
-__global__ void __launch_bounds__(256) k_scale(const double *__restrict__ phi1, const float *__restrict__ qfeat,
-                                               int J, float *__restrict__ scale)
+// Two kernels, no workspace: k_scale_part spreads each sample over many blocks
+// (block i sums the squares of a fixed contiguous slice of phi1 and of qfeat in
+// FP64) and parks the two partial sums as 32-bit word pairs at the head of the
+// sample's block of `in`, which k_features overwrites afterwards; k_scale_final
+// adds the partials of each sample in a fixed order.  Deterministic.
+constexpr int SC_T = 256;          // threads of the scale kernels
+constexpr int SC_PER_BLOCK = 2048; // phi1 elements per partial-sum block
+
+inline int scale_blocks(int J)
 {
-    __shared__ double sh[2][8];
-    const int b = blockIdx.x;
-    double a = 0.0, q = 0.0;
-    for (int i = threadIdx.x; i < 4 * J; i += blockDim.x) {
-        const double v = phi1[(size_t)b * 4 * J + i];
+    const long long n = (4LL * J + SC_PER_BLOCK - 1) / SC_PER_BLOCK;
+    return (int)(n < 1 ? 1 : (n > 1024 ? 1024 : n));  // 4 words per block fit in 13 J floats
+}
+
+// fixed-order sum of one double per thread over a block of SC_T threads (thread 0 gets it)
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < SC_T / 32; ++w) r += sh[w];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SC_T) k_scale_part(const double *__restrict__ phi1, const float *__restrict__ qfeat,
+                                                     int J, int nblk, float *__restrict__ in)
+{
+    __shared__ double sh[SC_T / 32];
+    const int b = blockIdx.y, i = blockIdx.x;
+    const long long n1 = 4LL * J;
+    const long long lo1 = n1 * i / nblk, hi1 = n1 * (i + 1) / nblk;
+    const long long lo2 = (long long)J * i / nblk, hi2 = (long long)J * (i + 1) / nblk;
+    const double *p = phi1 + (size_t)b * n1;
+    const float *q = qfeat + (size_t)b * J;
+    double a = 0.0, c = 0.0;
+#pragma unroll 4
+    for (long long e = lo1 + threadIdx.x; e < hi1; e += SC_T) {
+        const double v = p[e];
         a += v * v;
     }
-    for (int j = threadIdx.x; j < J; j += blockDim.x) {
-        const double v = qfeat[(size_t)b * J + j];
-        q += v * v;
+    for (long long e = lo2 + threadIdx.x; e < hi2; e += SC_T) {
+        const double v = q[e];
+        c += v * v;
     }
-    for (int o = 16; o; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        q += __shfl_xor_sync(0xffffffffu, q, o);
-    }
-    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = a; sh[1][threadIdx.x >> 5] = q; }
-    __syncthreads();
+    a = block_sum(a, sh);
+    c = block_sum(c, sh);
     if (threadIdx.x == 0) {
-        double sa = 0.0, sq = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sa += sh[0][w]; sq += sh[1][w]; }
-        double s = sqrt(sa / (4.0 * J));
-        const double sqv = sqrt(sq / J);
+        unsigned *wd = reinterpret_cast<unsigned *>(in + (size_t)b * 13 * J) + 4 * i;
+        const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+        const unsigned long long uc = (unsigned long long)__double_as_longlong(c);
+        wd[0] = (unsigned)ua;
+        wd[1] = (unsigned)(ua >> 32);
+        wd[2] = (unsigned)uc;
+        wd[3] = (unsigned)(uc >> 32);
+    }
+}
+
+__global__ void __launch_bounds__(SC_T) k_scale_final(const float *__restrict__ in, int J, int nblk,
+                                                      float *__restrict__ scale)
+{
+    __shared__ double sh[SC_T / 32];
+    const int b = blockIdx.x;
+    const unsigned *wd = reinterpret_cast<const unsigned *>(in + (size_t)b * 13 * J);
+    double a = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += SC_T) {
+        a += __longlong_as_double((long long)(((unsigned long long)wd[4 * i + 1] << 32) | wd[4 * i]));
+        c += __longlong_as_double((long long)(((unsigned long long)wd[4 * i + 3] << 32) | wd[4 * i + 2]));
+    }
+    a = block_sum(a, sh);
+    c = block_sum(c, sh);
+    if (threadIdx.x == 0) {
+        double s = sqrt(a / (4.0 * J));
+        const double sqv = sqrt(c / J);
         if (s < sqv) s = sqv;
         if (!(s > 1e-30)) s = 1.0;
         scale[b] = (float)s;
@@ -296,6 +612,7 @@ __global__ void k_predict(const double *__restrict__ phi1, const float *__restri
 // ------------------------------------------------------------- workspace
 struct Work {
     __nv_bfloat16 *wb;     // BF16 weights [NPARAM]
+    unsigned char *pack;   // the fused inference kernel's parameter image [FPACK_BYTES]
     float *act[NL + 1];    // act[0] = input (caller's), act[l] = output of layer l
     float *g[2];           // gradient ping-pong [B][32][J]
     float *grad;           // [NPARAM]
@@ -319,6 +636,7 @@ size_t workspace_layout(int B, int J, Work *w, char *base)
     Work tmp{};
     Work &o = w ? *w : tmp;
     o.wb = (__nv_bfloat16 *)take(sizeof(__nv_bfloat16) * NPARAM);
+    o.pack = (unsigned char *)take(FPACK_BYTES);
     o.act[0] = nullptr;
     for (int l = 1; l <= NL; ++l) o.act[l] = (float *)take(sizeof(float) * cells * CH[l]);
     o.g[0] = (float *)take(sizeof(float) * cells * MAXC);
@@ -345,6 +663,34 @@ void forward_all(const Work &w, const float *params, int B, int J, cudaStream_t 
     launch_fwd<2>(w, params + layer_off(2) + layer_w(2), B, J, s);
     launch_fwd<3>(w, params + layer_off(3) + layer_w(3), B, J, s);
     launch_fwd<4>(w, params + layer_off(4) + layer_w(4), B, J, s);
+}
+
+// Inference: the five layers on the tensor cores, activations ping-ponging
+// between two buffers a and b (layer 0 reads in, the last layer writes out).
+void forward_mma(const __nv_bfloat16 *wb, const float *params, const float *in, float *a, float *b, float *out, int B,
+                 int J, cudaStream_t s)
+{
+    const dim3 grid((J + TX - 1) / TX, B);
+    k_conv_mma<13, 32, true><<<grid, TX, 0, s>>>(in, wb + layer_off(0), params + layer_off(0) + layer_w(0), a, J);
+    k_conv_mma<32, 32, true><<<grid, TX, 0, s>>>(a, wb + layer_off(1), params + layer_off(1) + layer_w(1), b, J);
+    k_conv_mma<32, 32, true><<<grid, TX, 0, s>>>(b, wb + layer_off(2), params + layer_off(2) + layer_w(2), a, J);
+    k_conv_mma<32, 32, true><<<grid, TX, 0, s>>>(a, wb + layer_off(3), params + layer_off(3) + layer_w(3), b, J);
+    k_conv_mma<32, 4, false><<<grid, TX, 0, s>>>(b, wb + layer_off(4), params + layer_off(4) + layer_w(4), out, J);
+}
+
+// Inference in one kernel: the parameter image, then the fused layers on a
+// persistent grid of two CTAs per SM.
+int forward_fused(unsigned char *pack, const float *params, const float *in, float *out, int B, int J, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(k_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, FSMEM) != cudaSuccess)
+        return 3;
+    k_pack_fused<<<dim3((FPACK_MAX_LAYER + 255) / 256, NL), 256, 0, s>>>(params, pack);
+    const long long tiles = (long long)B * ((J + FOUT - 1) / FOUT);
+    const int grid = (int)(tiles < 2LL * sms ? tiles : 2LL * sms);
+    k_forward_fused<<<grid, FTHREADS, FSMEM, s>>>(pack, in, out, B, J);
+    return 0;
 }
 
 // Backward of layer L: gin = gradient w.r.t. the layer's output (before the
@@ -513,7 +859,9 @@ int oci_nn_features(const double *phi1, const double *phi2, const float *stat, c
 {
     if (!phi1 || !phi2 || !stat || !qfeat || !in || !scale || batch < 1 || n_cells < 1) return 1;
     cudaStream_t s = (cudaStream_t)stream;
-    k_scale<<<batch, 256, 0, s>>>(phi1, qfeat, n_cells, scale);
+    const int nblk = scale_blocks(n_cells);
+    k_scale_part<<<dim3(nblk, batch), SC_T, 0, s>>>(phi1, qfeat, n_cells, nblk, in);
+    k_scale_final<<<batch, SC_T, 0, s>>>(in, n_cells, nblk, scale);
     k_features<<<dim3((n_cells + 255) / 256, batch), 256, 0, s>>>(phi1, phi2, stat, qfeat, scale, n_cells, in);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
@@ -533,11 +881,7 @@ int oci_nn_forward(const float *params, const float *in, int32_t batch, int32_t 
     Work w{};
     if (workspace_layout(batch, n_cells, nullptr, nullptr) > ws_bytes) return 1;
     workspace_layout(batch, n_cells, &w, (char *)ws);
-    w.act[0] = const_cast<float *>(in);
-    cudaStream_t s = (cudaStream_t)stream;
-    k_to_bf16<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, NPARAM, w.wb);
-    forward_all(w, params, batch, n_cells, s);
-    cudaMemcpyAsync(out, w.act[NL], sizeof(float) * (size_t)batch * 4 * n_cells, cudaMemcpyDeviceToDevice, s);
+    if (forward_fused(w.pack, params, in, out, batch, n_cells, (cudaStream_t)stream)) return 3;
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
@@ -700,14 +1044,8 @@ int oci_nn_forward_noalloc(const float *params, const float *in, int32_t n_cells
     float *a = (float *)((char *)scratch + kStaticWeightBytes);
     float *b = a + kStaticActFloats;
     cudaStream_t s = (cudaStream_t)stream;
-    const int J = n_cells;
-    const dim3 grid((J + TX - 1) / TX, 1);
     k_to_bf16<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, NPARAM, wb);
-    k_conv<13, 32, true, false><<<grid, TX, 0, s>>>(in, nullptr, wb + layer_off(0), params + layer_off(0) + layer_w(0), a, J);
-    k_conv<32, 32, true, false><<<grid, TX, 0, s>>>(a, nullptr, wb + layer_off(1), params + layer_off(1) + layer_w(1), b, J);
-    k_conv<32, 32, true, false><<<grid, TX, 0, s>>>(b, nullptr, wb + layer_off(2), params + layer_off(2) + layer_w(2), a, J);
-    k_conv<32, 32, true, false><<<grid, TX, 0, s>>>(a, nullptr, wb + layer_off(3), params + layer_off(3) + layer_w(3), b, J);
-    k_conv<32, 4, false, false><<<grid, TX, 0, s>>>(b, nullptr, wb + layer_off(4), params + layer_off(4) + layer_w(4), out, J);
+    forward_mma(wb, params, in, a, b, out, 1, n_cells, s);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

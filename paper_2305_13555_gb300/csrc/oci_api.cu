@@ -1372,7 +1372,7 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
     else if (si) launches += 3 + main_iters * (h->sweep == OCI_SWEEP_SCAN ? 4 : 2);  // begin, prep, sweep + cells, commit
     else if (halo_graph) launches += 6;  // begin, entry, BF16 loop, exit, loop, commit
     else if (async_run) launches += 2;   // begin, the barrier-free loop (which ends the step)
-    else if (h->use_loop) launches += 1 + 2 * graph_runs + corrections;  // begin, (loop, commit) per graph run, lifts
+    else if (h->use_loop) launches += 1 + graph_runs + corrections;  // begin, one loop (which commits) per graph run, lifts
     else launches += 2 + body_launches(main_iters) + corrections * (unroll + 1);  // begin, bodies, commit, lifts
     int refined = 0;
     if (s.status == ocik::ST_STALL && !si && h->scheme == OCI_TIME_MB && h->cells_lin && h->ks.refine) {
@@ -1893,7 +1893,7 @@ int oci_step_wait(oci_handle *h, oci_stats *st)
     int launches = h->pend_launches;
     if (h->pend_halo) launches += 6;
     else if (h->pend_async) launches += 2;
-    else if (h->use_loop) launches += 3;
+    else if (h->use_loop) launches += 2;  // begin, the loop (which commits)
     else launches += 2 + unroll * ((s.iter + unroll - 1) / unroll);
     int refined = 0;
     if (s.status == ocik::ST_STALL && h->cells_lin && h->ks.refine) {

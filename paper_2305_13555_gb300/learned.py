@@ -67,6 +67,39 @@ def init_params(seed=0):
     return p
 
 
+def extrapolation_params(seed=0):
+    """Parameters whose network is exactly linear extrapolation in time,
+    out = (phi_{n-1} - phi_{n-2}) / S (so phi_hat = 2 phi_{n-1} - phi_{n-2}),
+    with room to learn a correction on top: in layers 1-4, channels 0-7
+    carry the positive and negative parts of input channels 4-7 (the
+    normalised change of the last step) on the centre tap, channels 8-31
+    start He-uniform, and the last layer reads only channels 0-7, so training
+    starts from the extrapolation's loss and moves away from it only where
+    that lowers the loss."""
+    g = np.random.default_rng(seed)
+    ch = (13, 32, 32, 32, 32, 4)
+    out = []
+    for l, (ci, co) in enumerate(zip(ch[:-1], ch[1:])):
+        bound = math.sqrt(6.0 / (ci * 5))
+        W = g.uniform(-bound, bound, (co, ci, 5))
+        if l == 0:
+            W[:8] = 0.0
+            for c in range(4):
+                W[2 * c, 4 + c, 2], W[2 * c + 1, 4 + c, 2] = 1.0, -1.0
+        elif l < len(ch) - 2:
+            W[:8] = 0.0
+            for c in range(8):
+                W[c, c, 2] = 1.0
+        else:
+            W[:] = 0.0
+            for c in range(4):
+                W[c, 2 * c, 2], W[c, 2 * c + 1, 2] = 1.0, -1.0
+        out += [W.ravel(), np.zeros(co)]
+    p = np.concatenate(out).astype(np.float32)
+    assert p.size == oci_nn_param_count()
+    return p
+
+
 def train(data, epochs=20, batch=32, lr=1e-3, seed=0, params=None, log=print, val_frac=0.05):
     """The library's training procedure (oci_nn_train): minibatch Adam over all
     (trajectory, step) samples with a held-out validation set and a cosine
@@ -118,6 +151,9 @@ def main():
     ap.add_argument("--family", default="config4", choices=["config4", "thin"],
                     help="training slabs: the config-4 family (default) or thin, strongly scattering "
                          "cells like the deployment slabs")
+    ap.add_argument("--init", default="extrapolation", choices=["extrapolation", "random"],
+                    help="starting parameters: linear extrapolation in time plus free channels "
+                         "(extrapolation_params), or He-uniform (init_params)")
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     a = ap.parse_args()
     import torch
@@ -132,7 +168,8 @@ def main():
                         problem=problem)
     print(f"generated {a.trajectories} trajectories x {a.steps} steps in {time.time() - t0:.1f} s; "
           f"mean OCI iterations per step {data['iters'].mean():.1f}", flush=True)
-    params, hist = train(data, epochs=a.epochs, batch=a.batch, lr=a.lr)
+    p0 = extrapolation_params() if a.init == "extrapolation" else init_params()
+    params, hist = train(data, epochs=a.epochs, batch=a.batch, lr=a.lr, params=p0)
     os.makedirs(os.path.dirname(a.out), exist_ok=True)
     np.save(a.out, params)
     print(f"saved {params.size} parameters to {a.out}; final val loss {hist['val_loss']:.3e}")

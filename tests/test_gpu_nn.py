@@ -1,10 +1,11 @@
 """GPU kernels of the learned guess against the FP64 CNN oracle (oracle.nn).
 
-The kernels use BF16-rounded weights with FP32 accumulation; the oracle is fed
-the same rounded weights in FP64, so the remaining difference is FP32
-accumulation over at most 32 channels x 5 taps per layer: bound 2e-5 of the
-output scale for the forward pass, 1e-4 relative (to the largest component)
-for gradients summed over hundreds of cells.
+Training kernels use BF16-rounded weights with FP32 activations and FP32
+accumulation; the oracle is fed the same rounded weights in FP64, so the
+remaining difference is FP32 accumulation over at most 32 channels x 5 taps
+per layer: 1e-4 relative (to the largest component) for gradients summed over
+hundreds of cells.  Inference runs on the tensor cores with every layer's
+input rounded to BF16 too (see test_forward_matches_oracle for its bound).
 """
 import numpy as np
 import pytest
@@ -47,15 +48,47 @@ def test_param_count():
     assert pkg.oci_nn_param_count() == onn.n_params()
 
 
-@pytest.mark.parametrize("B,J", [(1, 7), (2, 300), (3, 129)])
+def _bf16(a):
+    return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _forward_bf16_inputs(theta, x):
+    """The oracle's layers with every layer's input rounded to BF16, as the
+    tensor-core inference kernels take it (FP64 otherwise)."""
+    layers = onn.unflatten(_bf16_round(theta))
+    out = []
+    for s in range(x.shape[0]):
+        h = np.asarray(x[s], dtype=np.float64)
+        for li, (W, b) in enumerate(layers):
+            z = onn.conv_forward(_bf16(h), W, b)
+            h = np.maximum(z, 0.0) if li < len(layers) - 1 else z
+        out.append(h)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("B,J", [(1, 7), (2, 300), (3, 129), (1, 240), (1, 241), (2, 479), (1, 4099), (4, 20000)])
 def test_forward_matches_oracle(B, J):
+    """Inference on the tensor cores (BF16 operands, FP32 accumulation), all
+    five layers in one kernel over tiles of 240 cells (sizes below, at and
+    across a tile, and more tiles than the persistent grid's CTAs), against
+    the oracle fed the same BF16 rounding of weights and layer inputs.  The
+    GPU rounds its FP32 sums to BF16 where the oracle rounds FP64 ones, so a
+    value within FP32 rounding of a BF16 rounding boundary can land one BF16 ulp
+    (2^-8 relative) apart and move the outputs downstream: the bound is a few
+    such ulps of the output scale, and the mean error stays at FP32 level."""
     theta, x, _ = _data(1, B, J)
     ws = torch.empty(pkg.oci_nn_workspace_bytes(B, J), dtype=torch.uint8, device="cuda")
     out = torch.empty((B, 4, J), dtype=torch.float32, device="cuda")
     pkg.oci_nn_forward(torch.tensor(theta, device="cuda"), torch.tensor(x, device="cuda"), out, ws)
     torch.cuda.synchronize()
-    ref, _ = onn.forward(_bf16_round(theta), x.astype(np.float64))
-    assert np.abs(out.cpu().numpy() - ref).max() < 2e-5 * max(1.0, np.abs(ref).max())
+    ref = _forward_bf16_inputs(theta, x)
+    err = np.abs(out.cpu().numpy() - ref)
+    scale = max(1.0, np.abs(ref).max())
+    assert err.max() < 1e-2 * scale
+    assert err.mean() < 1e-4 * scale
+    # and it is the same network as the FP32-activation form up to that rounding
+    ref32, _ = onn.forward(_bf16_round(theta), x.astype(np.float64))
+    assert np.abs(out.cpu().numpy() - ref32).max() < 5e-2 * max(1.0, np.abs(ref32).max())
 
 
 @pytest.mark.parametrize("B,J", [(1, 9), (2, 260)])
@@ -90,8 +123,10 @@ def test_train_step_adam_matches_oracle():
     assert np.abs(p.cpu().double().numpy() - ref).max() < 1e-6
 
 
-def test_features_targets_predict_follow_their_definition():
-    B, J = 2, 50
+@pytest.mark.parametrize("B,J", [(1, 1), (2, 50), (3, 5000)])
+def test_features_targets_predict_follow_their_definition(B, J):
+    """The scale's sums of squares are split over blocks of 2048 elements of
+    phi1 (one block below 512 cells, ten at 5000)."""
     g = np.random.default_rng(4)
     phi1 = g.uniform(0, 2, (B, J, 4)); phi2 = g.uniform(0, 2, (B, J, 4)); phin = g.uniform(0, 2, (B, J, 4))
     stat = g.normal(0, 1, (B, J, 4)).astype(np.float32); q = g.uniform(0, 1, (B, J)).astype(np.float32)

@@ -46,7 +46,8 @@ def test_noalloc_forward_matches_workspace_forward_twice(lib):
             torch.cuda.synchronize()
             r, o = ref.cpu().numpy(), out.cpu().numpy()
             assert np.isfinite(o).all()
-            # the same kernels with the same launch shapes as oci_nn_forward: bit for bit
+            # one kernel per layer against oci_nn_forward's fused kernel, with the same
+            # arithmetic per output element: bit for bit
             assert np.array_equal(o, r), np.abs(o - r).max()
 
 
