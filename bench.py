@@ -326,9 +326,9 @@ def run_ours(args, rank, world):
 
 
 def run_compare(args, pkg, torch, stream):
-    """SI (the paper's sequential sweep, and the parallel-prefix sweep), FP64 OCI
-    and the backward-Euler time scheme on the same problem (fewer steps), for
-    context."""
+    """SI (the paper's sequential sweep, and the parallel-prefix sweep), FP64 OCI,
+    the backward-Euler time scheme, FP32 OCI started from the extrapolation in
+    time and the BF16 halo on the same problem (fewer steps), for context."""
     out = {}
     prob, _ = make_problem(args)
     J, N = prob["n_cells"], prob["n_ord"]
@@ -341,11 +341,12 @@ def run_compare(args, pkg, torch, stream):
             ("oci_backward_euler_fp32", "oci", "fp32", "march", "be", "fp32"),
             ("oci_backward_euler_fp64", "oci", "fp64", "march", "be", "fp32"),
             ("oci_fp32_same_window", "oci", "fp32", "march", "mb", "fp32"),
+            ("oci_fp32_extrapolated", "oci", "fp32", "march", "mb", "fp32"),
             ("oci_fp32_bf16_halo", "oci", "fp32", "march", "mb", "bf16")):
-        if (halo == "bf16" or name == "oci_fp32_same_window") and args.precision != "fp32":
+        if (halo == "bf16" or name.startswith("oci_fp32_")) and args.precision != "fp32":
             continue
         s = pkg.Solver(prob, precision=prec, tol=prob["tol"], stream=stream.cuda_stream, sweep=sweep, scheme=scheme,
-                       halo=halo)
+                       halo=halo, guess="extrapolate" if name == "oci_fp32_extrapolated" else "previous")
         n_w, n_t = 2, min(args.steps, 5)
         its, secs = [], []
         ok = True
@@ -368,7 +369,7 @@ def run_compare(args, pkg, torch, stream):
 
 
 def _run_steps(pkg, stream, prob, n_steps, precision="fp32", method="oci", sweep="march", halo="fp32", tol=None,
-               nn=0, W=None, k_corr=50, max_iter=100000, keep_phi=False, skip=0, cap=None):
+               nn=0, W=None, k_corr=50, max_iter=100000, keep_phi=False, skip=0, cap=None, guess="previous"):
     """Steps 1..n_steps of a trajectory from psi0 on one handle: per-step device
     seconds and iterations (steps after the first ``skip`` are summarised), the
     published fluxes of every step if asked, or the failing status.  With
@@ -377,7 +378,7 @@ def _run_steps(pkg, stream, prob, n_steps, precision="fp32", method="oci", sweep
     above the tolerance)."""
     tol = prob["tol"] if tol is None else tol
     s = pkg.Solver(prob, precision=precision, tol=tol, stream=stream.cuda_stream, max_iter=max_iter, sweep=sweep,
-                   halo=halo)
+                   halo=halo, guess=guess)
     capped, worst = 0, 0.0
     try:
         if nn:
@@ -524,14 +525,16 @@ def run_learned(args, pkg, torch, stream):
     for seed in GAIN_SEEDS:
         prob = workloads.config5_deploy(seed, J=131072, N=64, n_steps=8)
         rec = {}
-        for key, nn in (("fp32_plain", 0), ("fp32_nn_guess", pkg.OCI_NN_GUESS),
-                        ("fp32_nn_adaptive", pkg.OCI_NN_GUESS_ADAPTIVE)):
-            r = _run_steps(pkg, stream, prob, 8, "fp32", nn=nn, W=W, max_iter=50000, skip=2)
+        for key, nn, guess in (("fp32_plain", 0, "previous"), ("fp32_nn_guess", pkg.OCI_NN_GUESS, "previous"),
+                               ("fp32_nn_adaptive", pkg.OCI_NN_GUESS_ADAPTIVE, "previous"),
+                               ("fp32_extrapolated", 0, "extrapolate"),
+                               ("fp32_extrapolated_nn_adaptive", pkg.OCI_NN_GUESS_ADAPTIVE, "extrapolate")):
+            r = _run_steps(pkg, stream, prob, 8, "fp32", nn=nn, W=W, max_iter=50000, skip=2, guess=guess)
             rec[key] = r
         per_seed[str(seed)] = rec
     out["per_seed"] = per_seed
     out["inference_breakdown_us"] = nn_breakdown(pkg, torch, W, stream)
-    for key in ("fp32_nn_guess", "fp32_nn_adaptive"):
+    for key in ("fp32_nn_guess", "fp32_nn_adaptive", "fp32_extrapolated", "fp32_extrapolated_nn_adaptive"):
         ok = [r for r in per_seed.values() if "s_per_step" in r["fp32_plain"] and "s_per_step" in r[key]]
         if ok:
             out[f"{key}_over_plain_time_ratio_mean"] = sum(r[key]["s_per_step"] / r["fp32_plain"]["s_per_step"]
@@ -583,22 +586,26 @@ def nn_breakdown(pkg, torch, W, stream, J=131072, reps=50):
 def run_deploy200(args, pkg, torch, stream):
     """One whole 200-step deployment trajectory (131072 cells, S_64, thin cells,
     c 0.9-0.999, dt 0.02, tol 1e-8, seed --nn-seed): device seconds and
-    iterations per converged step of plain FP32 OCI, FP32 OCI with the learned
-    guess (adaptive), plain FP64 OCI, and SI (FP32, the paper's march and the
-    parallel prefix)."""
+    iterations per converged step of plain FP32 OCI (from the previous step's
+    flux, and from its extrapolation in time), FP32 OCI with the learned guess
+    (adaptive, always, adaptive on the extrapolated start), plain FP64 OCI, and
+    SI (FP32, the paper's march and the parallel prefix)."""
     from paper_2305_13555_gb300 import learned
     W = learned.load_weights() if os.path.exists(learned.DEFAULT_WEIGHTS) else None
     n = args.deploy_steps
     prob = workloads.config5_deploy(args.nn_seed, J=131072, N=64, n_steps=n)
     out = {"workload": f"deployment slab 131072 cells, S_64, seed {args.nn_seed}, steps 1-{n}, tol 1e-8"}
-    runs = [("oci_fp32_plain", "fp32", "oci", "march", 0), ("oci_fp64_plain", "fp64", "oci", "march", 0),
-            ("si_march_fp32", "fp32", "si", "march", 0), ("si_scan_fp32", "fp32", "si", "scan", 0),
-            ("si_scan_fp64", "fp64", "si", "scan", 0)]
+    P, E = "previous", "extrapolate"
+    runs = [("oci_fp32_plain", "fp32", "oci", "march", 0, P), ("oci_fp32_extrapolated", "fp32", "oci", "march", 0, E),
+            ("oci_fp64_plain", "fp64", "oci", "march", 0, P),
+            ("si_march_fp32", "fp32", "si", "march", 0, P), ("si_scan_fp32", "fp32", "si", "scan", 0, P),
+            ("si_scan_fp64", "fp64", "si", "scan", 0, P)]
     if W is not None:
-        runs.insert(1, ("oci_fp32_nn_adaptive", "fp32", "oci", "march", pkg.OCI_NN_GUESS_ADAPTIVE))
-        runs.insert(2, ("oci_fp32_nn_guess", "fp32", "oci", "march", pkg.OCI_NN_GUESS))
-    for key, prec, method, sweep, nn in runs:
-        out[key] = _run_steps(pkg, stream, prob, n, prec, method, sweep, nn=nn, W=W, max_iter=50000)
+        runs.insert(2, ("oci_fp32_nn_adaptive", "fp32", "oci", "march", pkg.OCI_NN_GUESS_ADAPTIVE, P))
+        runs.insert(3, ("oci_fp32_nn_guess", "fp32", "oci", "march", pkg.OCI_NN_GUESS, P))
+        runs.insert(4, ("oci_fp32_extrapolated_nn_adaptive", "fp32", "oci", "march", pkg.OCI_NN_GUESS_ADAPTIVE, E))
+    for key, prec, method, sweep, nn, guess in runs:
+        out[key] = _run_steps(pkg, stream, prob, n, prec, method, sweep, nn=nn, W=W, max_iter=50000, guess=guess)
     return out
 
 

@@ -196,6 +196,27 @@ int oci_set_time_scheme(oci_handle *h, int32_t scheme);
 enum { OCI_HALO_FP32 = 0, OCI_HALO_BF16 = 1 };
 int oci_set_halo(oci_handle *h, int32_t halo);
 
+/* Initial iterate of the next time step, formed when a multiple-balance OCI
+ * step commits (the paper does not state one; a step's iteration starts from
+ * some Psi^(0) and converges to the same discrete solution from any).
+ * OCI_GUESS_PREVIOUS (default): both time moments of every corner take the
+ * committed end-of-step flux psi_{k+1/2}.  OCI_GUESS_EXTRAPOLATE: the linear
+ * extrapolation in time through the last two end-of-step fluxes, with
+ * d = psi_{k+1/2} - psi_{k-1/2} (the flux the step started from): step-average
+ * moment psi_{k+1/2} + d/2, end moment psi_{k+1/2} + d (not the paper's;
+ * exact for a flux linear in time; only iteration counts change).  The
+ * iterate's scalar-flux moments, which only enter the first iteration's
+ * relative change, stay the end-of-step moments, so that change is measured
+ * from the previous step's flux.  A learned guess lifts this iterate, taking
+ * its scalar flux as the same extrapolation of the last two committed steps'
+ * moments.  Applies to the commits of OCI steps of the multiple-balance scheme
+ * after the call; SI and backward-Euler steps, and a step after
+ * oci_set_state or an uncommitted step, start from the end-of-step flux.
+ * OCI_EINVAL for an unknown mode, OCI_ESTATE while a step is pending or a
+ * decomposed step is open. */
+enum { OCI_GUESS_PREVIOUS = 0, OCI_GUESS_EXTRAPOLATE = 1 };
+int oci_set_guess(oci_handle *h, int32_t guess);
+
 /* Diagnostics of the bounded waits (the paper has no counterpart).  The
  * persistent FP32 iteration meets the other blocks at a grid barrier once per
  * iteration; every wait there gives up after poll_limit polls (0: the default,

@@ -20,6 +20,7 @@ OCI_OK, OCI_EINVAL, OCI_ENOMEM, OCI_ECUDA, OCI_ENOTCONV, OCI_ENAN, OCI_ETIMEOUT,
 OCI_BC_VACUUM, OCI_BC_REFLECT, OCI_BC_INCIDENT = 0, 1, 2
 OCI_FP64, OCI_FP32, OCI_FP32_BF16HALO = 0, 1, 2
 OCI_HALO_FP32, OCI_HALO_BF16 = 0, 1
+OCI_GUESS_PREVIOUS, OCI_GUESS_EXTRAPOLATE = 0, 1
 OCI_SOLVER_WOODBURY, OCI_SOLVER_DENSE = 0, 1
 OCI_SWEEP_MARCH, OCI_SWEEP_SCAN = 0, 1
 OCI_TIME_MB, OCI_TIME_BE = 0, 1
@@ -31,6 +32,7 @@ _BC = {"vacuum": OCI_BC_VACUUM, "reflect": OCI_BC_REFLECT, "reflecting": OCI_BC_
 _PREC = {"fp64": OCI_FP64, "f64": OCI_FP64, "double": OCI_FP64, "fp32": OCI_FP32, "f32": OCI_FP32,
          "float": OCI_FP32, "fp32_bf16halo": OCI_FP32_BF16HALO}
 _HALO = {"fp32": OCI_HALO_FP32, "bf16": OCI_HALO_BF16}
+_GUESS = {"previous": OCI_GUESS_PREVIOUS, "extrapolate": OCI_GUESS_EXTRAPOLATE}
 
 
 class OciProblem(ctypes.Structure):
@@ -68,6 +70,7 @@ SIGNATURES = {
     "oci_set_sweep": (ctypes.c_int, [_VP, _I32]),
     "oci_set_time_scheme": (ctypes.c_int, [_VP, _I32]),
     "oci_set_halo": (ctypes.c_int, [_VP, _I32]),
+    "oci_set_guess": (ctypes.c_int, [_VP, _I32]),
     "oci_step_async": (ctypes.c_int, [_VP]),
     "oci_step_wait": (ctypes.c_int, [_VP, _VP]),
     "oci_fluxes_async": (ctypes.c_int, [_VP, _VP]),
@@ -237,6 +240,13 @@ def oci_set_halo(h, halo):
     _check(load_library().oci_set_halo(h, int(halo)), "oci_set_halo", h)
 
 
+def oci_set_guess(h, guess):
+    """OCI_GUESS_PREVIOUS (default) or OCI_GUESS_EXTRAPOLATE: the next step's
+    initial iterate (see oci.h); also "previous" / "extrapolate"."""
+    guess = _GUESS.get(guess, guess)
+    _check(load_library().oci_set_guess(h, int(guess)), "oci_set_guess", h)
+
+
 def oci_step(h):
     """One OCI time step; returns (status, stats dict).  Raises only on
     OCI_EINVAL / OCI_ECUDA; convergence failures come back as the status."""
@@ -356,7 +366,7 @@ class Solver:
     """Owns one handle.  ``step()`` / ``si_step()`` advance one time step."""
 
     def __init__(self, prob, precision="fp64", tol=None, max_iter=100000, stream=None, solver="woodbury",
-                 sweep="march", scheme="mb", halo="fp32"):
+                 sweep="march", scheme="mb", halo="fp32", guess="previous"):
         self.prob = prob
         self.h = oci_create(prob, precision, tol, max_iter, stream)
         try:
@@ -368,6 +378,8 @@ class Solver:
                 oci_set_sweep(self.h, sweep)
             if scheme != "mb":
                 oci_set_time_scheme(self.h, scheme)
+            if guess != "previous":
+                oci_set_guess(self.h, guess)
         except Exception:
             self.close()
             raise

@@ -903,11 +903,11 @@ int launch_lift(oci_handle *h, const void *fn)
 {
     if (h->prec == OCI_FP64) {
         KParams<double> p = make_params<double>(h, 0, 0);
-        void *a[] = {&p, &h->nn_phat};
+        void *a[] = {&p, &h->nn_phat, &h->nn_hist[0], &h->nn_hist[1]};
         CK(h, cudaLaunchKernel(fn, dim3(h->grid_pc), dim3(kBlock), a, 0, h->stream));
     } else {
         KParams<float> p = make_params<float>(h, 0, 0);
-        void *a[] = {&p, &h->nn_phat};
+        void *a[] = {&p, &h->nn_phat, &h->nn_hist[0], &h->nn_hist[1]};
         CK(h, cudaLaunchKernel(fn, dim3(h->grid_pc), dim3(kBlock), a, 0, h->stream));
     }
     return OCI_OK;
@@ -1459,6 +1459,7 @@ int oci_create(const oci_problem *p, oci_handle **out)
     h->cfg.stall_floor = 0.0;  // enabled below for the FP32 path with refinement
     h->cfg.bar_poll_limit = 0;
     h->cfg.bar_shortfall = 0;
+    h->cfg.extrap = 0;
     gauss_legendre(N, h->mu, h->w);
     h->dx.assign(p->dx, p->dx + J);
     // materials: distinct (dx, sigma_t, sigma_s)
@@ -1784,6 +1785,15 @@ int oci_set_halo(oci_handle *h, int32_t halo)
     }
     h->halo = halo;
     return OCI_OK;
+}
+
+int oci_set_guess(oci_handle *h, int32_t guess)
+{
+    if (!h || (guess != OCI_GUESS_PREVIOUS && guess != OCI_GUESS_EXTRAPOLATE)) return OCI_EINVAL;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
+    CK(h, cudaSetDevice(h->device));
+    h->cfg.extrap = guess == OCI_GUESS_EXTRAPOLATE ? 1 : 0;
+    return set_device_cfg(h, h->cfg);
 }
 
 int oci_set_time_scheme(oci_handle *h, int32_t scheme)

@@ -95,6 +95,7 @@ struct IterConfig {
     int bar_shortfall;        // arrivals the grid barrier waits for beyond the grid (diagnostic; 0)
     double halo_switch;       // BF16-halo phase: leave it once the relative change is below this ...
     int halo_stall;           // ... or after this many iterations without a 10% improvement
+    int extrap;               // next step's initial iterate: 0 the end-of-step flux, 1 its extrapolation in time
 };
 
 
@@ -280,6 +281,15 @@ __device__ __forceinline__ void load_phi4(const phi_t<R> *ph, int cell, R &a, R 
 }
 
 template <typename R>
+__device__ __forceinline__ phi_t<R> phi_from_double(double x);
+template <> __device__ __forceinline__ double phi_from_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ float2 phi_from_double<float>(double x)
+{
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+
+template <typename R>
 struct KParams {
     int J, P;
     int bc_left, bc_right;
@@ -328,6 +338,41 @@ struct KParams {
     unsigned *as_done;
     double *as_part;
 };
+
+// Arithmetic of the end of a step with every rounding spelled out (no compiler
+// contraction), so that every kernel that commits a step -- the per-cell
+// commit, and the persistent loops that end the step in the same launch --
+// produces the same bits from the same inputs.
+__device__ __forceinline__ float mul_x(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_x(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_x(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_x(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float fma_x(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_x(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// End-of-step (k+1/2) corner fluxes of ordinate pair (+mu, -mu) of one cell:
+// the right-hand side from the source qd, the previous end-of-step flux pe
+// (times e), the scattering terms F (already times s) and the incident faces
+// inP / inM, then the second rows of the complex 2x2 inverse a.  Outputs:
+// +mu (L, R) = (phr, phi), -mu (L, R) = (mhr, -mhi).
+template <typename R>
+__device__ __forceinline__ void commit_corners(const Coef<R> &a, const r4<R> &qd, R e, const r4<R> &pe, R Fkl,
+                                               R Fkr, R Fhl, R Fhr, R mu, const r2<R> &inP, const r2<R> &inM,
+                                               R &phr, R &phi, R &mhr, R &mhi)
+{
+    const R ukr = fma_x(mu, inP.x, add_x(fma_x(e, pe.x, qd.x), Fkl));
+    const R uki = add_x(fma_x(e, pe.y, qd.y), Fkr);
+    const R uhr = fma_x(mu, inP.y, add_x(qd.z, Fhl));
+    const R uhi = add_x(qd.w, Fhr);
+    const R vkr = add_x(fma_x(e, pe.z, qd.x), Fkl);
+    const R vki = fma_x(-mu, inM.x, -add_x(fma_x(e, pe.w, qd.y), Fkr));
+    const R vhr = add_x(qd.z, Fhl);
+    const R vhi = fma_x(-mu, inM.y, -add_x(qd.w, Fhr));
+    phr = fma_x(-a.vi, uhi, fma_x(a.vr, uhr, fma_x(-a.ui, uki, mul_x(a.ur, ukr))));
+    phi = fma_x(a.vi, uhr, fma_x(a.vr, uhi, fma_x(a.ui, ukr, mul_x(a.ur, uki))));
+    mhr = fma_x(-a.vi, vhi, fma_x(a.vr, vhr, fma_x(-a.ui, vki, mul_x(a.ur, vkr))));
+    mhi = fma_x(a.vi, vhr, fma_x(a.vr, vhi, fma_x(a.ui, vkr, mul_x(a.ur, vki))));
+}
 
 // Reduce V values per lane (s with compensation e) over the LPC lanes of a
 // segment.  Afterwards lane holds NV = max(V/LPC, 1) sums in s[0..NV-1] for
@@ -1107,6 +1152,7 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
     // iteration's memory-level parallelism.  It starts at ring position rp with
     // no copy in flight; it writes psi_edge of its own cells and buffer fgs.
     auto ring_commit = [&](int frd_l, int fgs, const phi_t<R> *phf) {
+        const bool ext = p.cfg->extrap != 0;
         auto issue_commit = [&](int i) {  // lane 0: every copy of local chunk i
             if (i >= nmine) return;
             const int c0 = chunk_of(i) * CPC;
@@ -1170,19 +1216,18 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
                     const r2<R> inP = (refl_l && cell == 0) ? ldcg2(p.faceM[frd_l] + pp) : sP[cl * P + pp];
                     const r2<R> inM = (refl_r && cell == J - 1) ? ldcg2(p.faceP[frd_l] + (size_t)J * P + pp)
                                                                 : sM[cl * P + pp];
-                    R ukr = qd.x + ce * pe.x + Fkl, uki = qd.y + ce * pe.y + Fkr, uhr = qd.z + Fhl, uhi = qd.w + Fhr;
-                    R vkr = qd.x + ce * pe.z + Fkl, vki = -(qd.y + ce * pe.w) - Fkr, vhr = qd.z + Fhl,
-                      vhi = -qd.w - Fhr;
-                    ukr += mw[t].x * inP.x; uhr += mw[t].x * inP.y;
-                    vki -= mw[t].x * inM.x; vhi -= mw[t].x * inM.y;
                     // end-of-step components (k+1/2): second rows of A^{-1}
-                    const R phr_ = a.ur * ukr - a.ui * uki + a.vr * uhr - a.vi * uhi;
-                    const R phi_ = a.ur * uki + a.ui * ukr + a.vr * uhi + a.vi * uhr;
-                    const R mhr = a.ur * vkr - a.ui * vki + a.vr * vhr - a.vi * vhi;
-                    const R mhi = a.ur * vki + a.ui * vkr + a.vr * vhi + a.vi * vhr;
+                    R phr_, phi_, mhr, mhi;
+                    commit_corners<R>(a, qd, ce, pe, Fkl, Fkr, Fhl, Fhr, mw[t].x, inP, inM, phr_, phi_, mhr, mhi);
                     st4(p.psi_edge + (size_t)cell * P + pp, phr_, phi_, mhr, -mhi);
-                    st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, phi_, phi_);
-                    st2(p.faceM[fgs] + (size_t)cell * P + pp, mhr, mhr);
+                    if (ext) {  // linear in time through the previous end-of-step flux pe
+                        const R dP = phi_ - pe.y, dM = mhr - pe.z;
+                        st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, phi_ + R(0.5) * dP, phi_ + dP);
+                        st2(p.faceM[fgs] + (size_t)cell * P + pp, mhr + R(0.5) * dM, mhr + dM);
+                    } else {
+                        st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, phi_, phi_);
+                        st2(p.faceM[fgs] + (size_t)cell * P + pp, mhr, mhr);
+                    }
                 }
                 for (int c = ls; c < 4; c += LPC) {
                     const float2 v = c == 0 ? fph[r][0] : c == 1 ? fph[r][1] : c == 2 ? fph[r][2] : fph[r][3];
@@ -1890,6 +1935,7 @@ __device__ __forceinline__ void percell_body(const KParams<R> &p, int gw, int nw
     const int J = p.J, P = p.P;
     const bool refl_l = (MODE == C_COMMIT_OCI || MODE == C_COMMIT_LIN) && p.bc_left == BC_REFLECT;
     const bool refl_r = (MODE == C_COMMIT_OCI || MODE == C_COMMIT_LIN) && p.bc_right == BC_REFLECT;
+    const bool ext = (MODE == C_COMMIT_OCI || MODE == C_COMMIT_LIN) && p.cfg->extrap != 0;
     R mu[PPL];
 #pragma unroll
     for (int i = 0; i < PPL; ++i) mu[i] = (ls + LPC * i < P) ? ldg2(p.muw + ls + LPC * i).x : R(0);
@@ -1969,17 +2015,20 @@ __device__ __forceinline__ void percell_body(const KParams<R> &p, int gw, int nw
                     }
                     continue;
                 }
-                ukr += mu[i] * inPr[r][i].x; uhr += mu[i] * inPr[r][i].y;
-                vki -= mu[i] * inMr[r][i].x; vhi -= mu[i] * inMr[r][i].y;
                 // end-of-step components only (k+1/2): second rows of A^{-1}
-                const R phr_ = a.ur * ukr - a.ui * uki + a.vr * uhr - a.vi * uhi;
-                const R phi_ = a.ur * uki + a.ui * ukr + a.vr * uhi + a.vi * uhr;
-                const R mhr = a.ur * vkr - a.ui * vki + a.vr * vhr - a.vi * vhi;
-                const R mhi = a.ur * vki + a.ui * vkr + a.vr * vhi + a.vi * vhr;
+                R phr_, phi_, mhr, mhi;
+                commit_corners<R>(a, qd, es.x, pe, Fkl, Fkr, Fhl, Fhr, mu[i], inPr[r][i], inMr[r][i], phr_, phi_, mhr,
+                                  mhi);
                 // psi+ = (L, R) = (Re, Im); psi- = conj(z): (Re z, -Im z)
                 st4(p.psi_edge + (size_t)cell * P + pp, phr_, phi_, mhr, -mhi);
-                st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, phi_, phi_);
-                st2(p.faceM[fgs] + (size_t)cell * P + pp, mhr, mhr);
+                if (ext) {  // linear in time through the previous end-of-step flux pe
+                    const R dP = phi_ - pe.y, dM = mhr - pe.z;
+                    st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, phi_ + R(0.5) * dP, phi_ + dP);
+                    st2(p.faceM[fgs] + (size_t)cell * P + pp, mhr + R(0.5) * dM, mhr + dM);
+                } else {
+                    st2(p.faceP[fgs] + (size_t)(cell + 1) * P + pp, phi_, phi_);
+                    st2(p.faceM[fgs] + (size_t)cell * P + pp, mhr, mhr);
+                }
             }
             if (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI) {
                 for (int c = ls; c < 4; c += LPC) {
@@ -2012,17 +2061,9 @@ __device__ __forceinline__ void percell_body(const KParams<R> &p, int gw, int nw
 // ---------------------------------------------------------------------------
 enum : int { LIFT_GUESS = 0, LIFT_CORR = 1 };
 
-template <typename R>
-__device__ __forceinline__ phi_t<R> phi_from_double(double x);
-template <> __device__ __forceinline__ double phi_from_double<double>(double x) { return x; }
-template <> __device__ __forceinline__ float2 phi_from_double<float>(double x)
-{
-    const float h = (float)x;
-    return make_float2(h, (float)(x - (double)h));
-}
-
 template <typename R, int LPC, int PPL, int MODE>
-__global__ void __launch_bounds__(256) k_lift(const KParams<R> p, const double *__restrict__ phat)
+__global__ void __launch_bounds__(256) k_lift(const KParams<R> p, const double *__restrict__ phat,
+                                              const double *__restrict__ hist0, const double *__restrict__ hist1)
 {
     constexpr int SPW = 32 / LPC;
     const int lane = threadIdx.x & 31;
@@ -2044,9 +2085,20 @@ __global__ void __launch_bounds__(256) k_lift(const KParams<R> p, const double *
         const bool valid = cell < J;  // all lanes stay in the loop body (warp barriers below)
         double d[4] = {0.0, 0.0, 0.0, 0.0};
         if (valid) {
+            // the iterate's moments: phi0, or with the initial iterate extrapolated in
+            // time, the same extrapolation of the last two committed end-of-step moments
+            const bool ext = MODE == LIFT_GUESS && p.cfg->extrap != 0;
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                d[c] = phat[4 * (size_t)cell + c] - PhiStore<R>::wide(ph[4 * (size_t)cell + c]);
+            for (int c = 0; c < 4; ++c) {
+                double it;
+                if (ext) {
+                    const double e1 = hist0[4 * (size_t)cell + 2 + (c & 1)], e2 = hist1[4 * (size_t)cell + 2 + (c & 1)];
+                    it = e1 + (c < 2 ? 0.5 : 1.0) * (e1 - e2);
+                } else {
+                    it = PhiStore<R>::wide(ph[4 * (size_t)cell + c]);
+                }
+                d[c] = phat[4 * (size_t)cell + c] - it;
+            }
         }
         __syncwarp();
         if (!valid) continue;
