@@ -273,41 +273,37 @@ def run_ours(args, rank, world):
                                      if rs == 4 else "48 B per cell-ordinate + 100 B per cell",
                 "working_set_vs_l2": f"{abytes / 1e6:.0f} MB per iteration against a 129 MB L2"}
 
-    # end to end through the C ABI with host buffers: source in, fluxes out, both in
-    # pinned host memory (page-locked, so the copies are direct DMA), pipelined
-    # the way a user streams steps: each step's source is staged on the library's
-    # copy stream while the previous step runs, and each step's fluxes are copied
-    # out while the next one runs (oci_step_async / oci_step_wait / oci_fluxes_async)
-    q_pin = torch.empty((J, 4), dtype=torch.float64).pin_memory()
-    phi_pins = [torch.empty((J, 4), dtype=torch.float64).pin_memory() for _ in range(2)]
-    q_host, phi_hosts = q_pin.numpy(), [t.numpy() for t in phi_pins]
-    q_host[:] = np.asarray(prob["q"], dtype=np.float64).reshape(J, 4)
+    # end to end through the C ABI with host buffers: each step's source in and
+    # its fluxes out, in pinned host memory (page-locked, so the copies are
+    # direct DMA), through oci_run_steps: the next step is queued on the device
+    # before the host waits for the current one, the copies run on the library's
+    # copy streams; calls of at most 32 steps, the trajectory restarts between them
+    CH = 32
+    q_pin = torch.empty((CH, J, 4), dtype=torch.float64).pin_memory()
+    phi_pin = torch.empty((CH, J, 4), dtype=torch.float64).pin_memory()
+    q_host, phi_host = q_pin.numpy(), phi_pin.numpy()
+    q_host[:] = np.asarray(prob["q"], dtype=np.float64).reshape(1, J, 4)
     e2e_iters = 0
     r0 = counter["restarts"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    restart_if_due()
-    pkg.oci_set_source(s.h, q_host)
-    pkg.oci_step_async(s.h)
-    for k in range(args.steps):
-        last = k + 1 == args.steps
-        if not last:
-            pkg.oci_set_source(s.h, q_host)  # the next step's source, staged while this step runs
-        rc, st = pkg.oci_step_wait(s.h)
-        assert rc == pkg.OCI_OK, (rc, st)
-        e2e_iters += st["iters"]
-        pkg.oci_fluxes_async(s.h, phi_hosts[k % 2])  # copied out while the next step runs
-        if not last:
-            restart_if_due()
-            pkg.oci_step_async(s.h)
-    pkg.oci_sync(s.h)
+    k = 0
+    while k < args.steps:
+        pos = counter["k"] % n_traj  # steps of the current trajectory already run (0: it restarts)
+        restart_if_due()
+        m = min(CH, args.steps - k, n_traj - pos)
+        counter["k"] += m - 1
+        rc, done, stats = pkg.oci_run_steps(s.h, m, q_host[:m], phi_host[:m])
+        assert rc == pkg.OCI_OK and done == m, (rc, done, stats)
+        e2e_iters += sum(st["iters"] for st in stats)
+        k += m
     e2e_t = time.perf_counter() - t0
     state_bytes = (counter["restarts"] - r0) * psi_init.nbytes  # initial conditions of the replayed trajectories
     e2e = {"value": float(J) * N * e2e_iters / e2e_t, "unit": UNIT,
-           "h2d_bytes_per_step": int(q_host.nbytes + state_bytes / args.steps),
-           "d2h_bytes_per_step": int(phi_hosts[0].nbytes),
+           "h2d_bytes_per_step": int(q_host[0].nbytes + state_bytes / args.steps),
+           "d2h_bytes_per_step": int(phi_host[0].nbytes),
            "h2d": "source Q each step, initial angular flux psi0 at each trajectory restart (pinned host memory)",
-           "api": "oci_step_async / oci_step_wait with oci_set_source and oci_fluxes_async on the copy stream"}
+           "api": "oci_run_steps: two steps in flight, sources up and moments down on the library's copy stream"}
     s.close()
 
     compare = {}

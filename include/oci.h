@@ -53,7 +53,8 @@ enum {
     OCI_ENOTCONV = 4,  /* max_iter reached before the tolerance */
     OCI_ENAN = 5,      /* non-finite scalar flux detected in the residual */
     OCI_ETIMEOUT = 6,  /* device-side iteration guard tripped (launch cap) */
-    OCI_ESTATE = 7     /* call not valid in the handle's current state */
+    OCI_ESTATE = 7,    /* call not valid in the handle's current state */
+    OCI_ESKIPPED = 8   /* oci_run_steps: not run, an earlier step of the call did not commit */
 };
 
 enum { OCI_BC_VACUUM = 0, OCI_BC_REFLECT = 1, OCI_BC_INCIDENT = 2 };
@@ -89,7 +90,7 @@ typedef struct oci_problem {
 /* Per-step statistics. */
 typedef struct oci_stats {
     int32_t iters;       /* iterations taken (the one meeting tol included) */
-    int32_t status;      /* OCI_OK, OCI_ENOTCONV, OCI_ENAN, OCI_ETIMEOUT */
+    int32_t status;      /* OCI_OK, OCI_ENOTCONV, OCI_ENAN, OCI_ETIMEOUT (OCI_ESKIPPED: oci_run_steps) */
     double residual;     /* last relative change of phi */
     double seconds;      /* device time of the step (CUDA events on the handle's stream) */
     int32_t committed;   /* 1 if the step advanced the state */
@@ -266,6 +267,27 @@ int si_step(oci_handle *h, oci_stats *st);
  * guess attached, the dense solver, backward Euler); use oci_step there. */
 int oci_step_async(oci_handle *h);
 int oci_step_wait(oci_handle *h, oci_stats *st);
+
+/* Several time steps in one call (no counterpart in the paper; it keeps the
+ * device busy across steps): steps k = 0 .. n-1, each with source moments
+ * q + k J 4 (host [n][J][4]; NULL: keep the current source), its published
+ * moments copied to phi + k J 4 (host [n][J][4], may be NULL) and its
+ * statistics to stats[k] (may be NULL).  The results are those of n rounds of
+ * oci_set_source / oci_step / oci_fluxes.  For an OCI_FP32 handle whose step
+ * runs start to end on the device (the persistent loop; no learned guess,
+ * Woodbury solver, multiple balance, FP32 halo or a BF16 phase not in use),
+ * the next step is enqueued before the host waits for the current one, the
+ * sources go up and the moments come down on two copy streams, and the queued
+ * step's prologue holds it (it does nothing) unless the one before it
+ * committed; a step that stalls in FP32 is refined on the host and the step
+ * behind it is enqueued again.  Other handles run the steps one at a time.
+ * Pass page-locked (pinned) q and phi for the copies to overlap.  The call
+ * returns when every copy is done.  The first step that does not commit ends
+ * the call: its status is returned, later steps are not run (stats status
+ * OCI_ESKIPPED) and the handle keeps that step's source.  *done (may be NULL)
+ * = steps committed.  OCI_OK when all n committed; OCI_EINVAL for n < 0,
+ * OCI_ESTATE while a step is pending or a decomposed step is open. */
+int oci_run_steps(oci_handle *h, int32_t n, const double *q, double *phi, oci_stats *stats, int32_t *done);
 
 /* Copy the moments published by the last step enqueued before this call (as
  * oci_fluxes, [J][4]) to host memory without waiting: a device snapshot on the

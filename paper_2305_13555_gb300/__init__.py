@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-OCI_OK, OCI_EINVAL, OCI_ENOMEM, OCI_ECUDA, OCI_ENOTCONV, OCI_ENAN, OCI_ETIMEOUT, OCI_ESTATE = range(8)
+OCI_OK, OCI_EINVAL, OCI_ENOMEM, OCI_ECUDA, OCI_ENOTCONV, OCI_ENAN, OCI_ETIMEOUT, OCI_ESTATE, OCI_ESKIPPED = range(9)
 OCI_BC_VACUUM, OCI_BC_REFLECT, OCI_BC_INCIDENT = 0, 1, 2
 OCI_FP64, OCI_FP32, OCI_FP32_BF16HALO = 0, 1, 2
 OCI_HALO_FP32, OCI_HALO_BF16 = 0, 1
@@ -73,6 +73,7 @@ SIGNATURES = {
     "oci_set_guess": (ctypes.c_int, [_VP, _I32]),
     "oci_step_async": (ctypes.c_int, [_VP]),
     "oci_step_wait": (ctypes.c_int, [_VP, _VP]),
+    "oci_run_steps": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP]),
     "oci_fluxes_async": (ctypes.c_int, [_VP, _VP]),
     "oci_sync": (ctypes.c_int, [_VP]),
     "oci_set_wait_limits": (ctypes.c_int, [_VP, ctypes.c_uint32, _I32]),
@@ -270,6 +271,23 @@ def oci_step_wait(h):
     if rc in (OCI_EINVAL, OCI_ECUDA, OCI_ENOMEM, OCI_ESTATE):
         _check(rc, "oci_step_wait", h)
     return rc, st.as_dict()
+
+
+def oci_run_steps(h, n, q=None, phi=None):
+    """n steps in one call (see oci.h): q [n][J][4] float64 sources or None (keep
+    the current one), phi [n][J][4] float64 to receive each step's moments or
+    None; both ideally page-locked.  Returns (status, steps committed, list of
+    per-step stats dicts)."""
+    for a in (q, phi):
+        if a is not None and not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+            raise ValueError("q and phi must be C-contiguous float64 arrays")
+    stats = (OciStats * max(n, 1))()
+    done = ctypes.c_int32()
+    rc = load_library().oci_run_steps(h, int(n), None if q is None else _ptr(q), None if phi is None else _ptr(phi),
+                                      stats, ctypes.byref(done))
+    if rc in (OCI_EINVAL, OCI_ECUDA, OCI_ENOMEM, OCI_ESTATE):
+        _check(rc, "oci_run_steps", h)
+    return rc, done.value, [stats[k].as_dict() for k in range(n)]
 
 
 def oci_fluxes_async(h, out):

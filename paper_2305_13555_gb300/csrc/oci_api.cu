@@ -205,6 +205,16 @@ struct oci_handle {
     bool step_pending = false, q_pending = false;
     bool pend_halo = false, pend_async = false;
     int pend_launches = 0;
+    // several steps in one call (oci_run_steps): the sources staged on an upload
+    // stream into two device buffers (each kept until the step two after its own
+    // is enqueued, so a step's cell sources can be scaled again); per-slot state
+    // copies (pinned) and events
+    void *rs_mem = nullptr;
+    double *rs_stage[2] = {nullptr, nullptr};
+    IterState *rs_st = nullptr;
+    cudaStream_t rs_up = nullptr;  // uploads, apart from the copy stream's downloads (which wait for their steps)
+    cudaEvent_t rs_ev0[2] = {nullptr, nullptr}, rs_ev1[2] = {nullptr, nullptr}, rs_done[2] = {nullptr, nullptr},
+                rs_ready[2] = {nullptr, nullptr}, rs_free[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -1184,6 +1194,7 @@ int map_status(int s)
     case ocik::ST_MAXITER: return OCI_ENOTCONV;
     case ocik::ST_NAN: return OCI_ENAN;
     case ocik::ST_STALL: return OCI_ENOTCONV;
+    case ocik::ST_HELD: return OCI_ESKIPPED;
     default: return OCI_ETIMEOUT;
     }
 }
@@ -1414,6 +1425,70 @@ int run_step(oci_handle *h, bool si, oci_stats *st)
         st->launches = launches;
     }
     return status;
+}
+
+
+// ------------------------------------------------------------ oci_run_steps
+// Steps that run start to end on the device (the FP32 persistent loop that
+// ends the step itself) can be queued two deep: the next step is enqueued
+// before the host waits for the previous one.
+bool queue_capable(const oci_handle *h)
+{
+    return h->prec == OCI_FP32 && h->use_loop && !h->use_async && h->solver == OCI_SOLVER_WOODBURY &&
+           h->scheme == OCI_TIME_MB && h->nn_mode == OCI_NN_OFF &&
+           !(h->halo == OCI_HALO_BF16 && h->exec_oci_h && h->cfg.max_iter >= 4);
+}
+
+int rs_setup(oci_handle *h)
+{
+    if (h->rs_mem) return OCI_OK;
+    if (!h->rs_st && cudaMallocHost(&h->rs_st, 2 * sizeof(IterState)) != cudaSuccess) {
+        h->rs_st = nullptr;
+        return OCI_ENOMEM;
+    }
+    if (!h->rs_up) CK(h, cudaStreamCreateWithFlags(&h->rs_up, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        if (!h->rs_ev0[k]) CK(h, cudaEventCreate(&h->rs_ev0[k]));
+        if (!h->rs_ev1[k]) CK(h, cudaEventCreate(&h->rs_ev1[k]));
+        for (cudaEvent_t *e : {&h->rs_done[k], &h->rs_ready[k], &h->rs_free[k]})
+            if (!*e) CK(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    const size_t qb = ((size_t)h->J * 32 + 255) & ~(size_t)255;
+    void *m = nullptr;
+    if (cudaMalloc(&m, 2 * qb) != cudaSuccess) return OCI_ENOMEM;
+    h->rs_stage[0] = (double *)m;
+    h->rs_stage[1] = (double *)((char *)m + qb);
+    h->rs_mem = m;
+    return OCI_OK;
+}
+
+// One queued step on the handle's stream: [the chain flag: hold it unless the
+// step before it commits], the step graph (prologue, the loop that ends the
+// step), its state to the slot's pinned copy.
+int rs_launch(oci_handle *h, int slot, bool chain)
+{
+    if (chain) CK(h, cudaMemsetAsync(&h->d_st->chain, 1, sizeof(int), h->stream));
+    CK(h, cudaEventRecord(h->rs_ev0[slot], h->stream));
+    CK(h, cudaGraphLaunch(h->exec_oci, h->stream));
+    CK(h, cudaEventRecord(h->rs_ev1[slot], h->stream));
+    CK(h, cudaMemcpyAsync(h->rs_st + slot, h->d_st, sizeof(IterState), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaEventRecord(h->rs_done[slot], h->stream));
+    return OCI_OK;
+}
+
+// The published moments at this point of the stream to host dst: a device
+// snapshot on the handle's stream, the host copy on the copy stream (the
+// slot's snapshot is reused once its previous host copy is done).
+int rs_snapshot(oci_handle *h, int slot, double *dst)
+{
+    const size_t bytes = (size_t)h->J * 32;
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_d2h[slot], 0));
+    CK(h, cudaMemcpyAsync(h->phi_snap[slot], h->phi_out, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaEventRecord(h->ev_snap[slot], h->stream));
+    CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_snap[slot], 0));
+    CK(h, cudaMemcpyAsync(dst, h->phi_snap[slot], bytes, cudaMemcpyDeviceToHost, h->copy_stream));
+    CK(h, cudaEventRecord(h->ev_d2h[slot], h->copy_stream));
+    return OCI_OK;
 }
 
 }  // namespace
@@ -1726,6 +1801,12 @@ void oci_destroy(oci_handle *h)
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->h_st) cudaFreeHost(h->h_st);
+    if (h->rs_st) cudaFreeHost(h->rs_st);
+    if (h->rs_mem) cudaFree(h->rs_mem);
+    if (h->rs_up) cudaStreamDestroy(h->rs_up);
+    for (int k = 0; k < 2; ++k)
+        for (cudaEvent_t e : {h->rs_ev0[k], h->rs_ev1[k], h->rs_done[k], h->rs_ready[k], h->rs_free[k]})
+            if (e) cudaEventDestroy(e);
     if (h->d_base) cudaFree(h->d_base);
     delete h;
 }
@@ -1959,6 +2040,146 @@ int oci_sync(oci_handle *h)
     CK(h, cudaStreamSynchronize(h->stream));
     if (h->copy_stream) CK(h, cudaStreamSynchronize(h->copy_stream));
     return OCI_OK;
+}
+
+int oci_run_steps(oci_handle *h, int32_t n, const double *q, double *phi, oci_stats *stats, int32_t *done)
+{
+    if (!h || n < 0) return OCI_EINVAL;
+    if (h->step_pending || h->dd_active) return OCI_ESTATE;
+    CK(h, cudaSetDevice(h->device));
+    if (done) *done = 0;
+    const size_t Jq = (size_t)h->J * 4;
+    auto skip_from = [&](int k0) {
+        for (int k = k0; stats && k < n; ++k) {
+            stats[k] = oci_stats{};
+            stats[k].status = OCI_ESKIPPED;
+        }
+    };
+    if (!queue_capable(h)) {  // one step at a time, as oci_set_source / oci_step / oci_fluxes
+        for (int k = 0; k < n; ++k) {
+            int rc = q ? upload_source(h, q + (size_t)k * Jq) : OCI_OK;
+            if (rc) return rc;
+            oci_stats st{};
+            const int status = run_step(h, false, &st);
+            if (stats) stats[k] = st;
+            if (!st.committed) {
+                skip_from(k + 1);
+                return status == OCI_OK ? OCI_ENOTCONV : status;
+            }
+            if (phi && (rc = oci_fluxes(h, phi + (size_t)k * Jq))) return rc;
+            if (done) *done = k + 1;
+        }
+        return OCI_OK;
+    }
+    int rc = pipe_setup(h);
+    if (!rc) rc = ensure_graphs(h);
+    if (!rc) rc = rs_setup(h);
+    if (!rc) rc = apply_pending_source(h);
+    if (!rc) rc = set_device_cfg(h, h->cfg);
+    if (rc) return rc;
+    if (n == 0) return OCI_OK;
+    StepRange range("oci_run_steps");
+    const int grid = std::min((h->J + 255) / 256, 152 * 8);
+    int launches[2] = {0, 0};
+    // the cell sources from the source moments staged in a slot (a slot's staging
+    // buffer keeps its step's moments until the step two after it is enqueued)
+    auto rescale = [&](int slot) -> int {
+        k_scale_source<float><<<grid, 256, 0, h->stream>>>(h->rs_stage[slot], h->dx_dev, h->J, (r4<float> *)h->cellq);
+        CK(h, cudaGetLastError());
+        CK(h, cudaEventRecord(h->rs_free[slot], h->stream));  // the next upload into the slot waits for this read
+        return OCI_OK;
+    };
+    // step k in slot k & 1: its source staged and scaled, [the initial iterate],
+    // the step, its moments copied out; `behind`: queued behind step k - 1
+    auto enqueue = [&](int k, bool behind) -> int {
+        const int slot = k & 1;
+        int r = OCI_OK;
+        launches[slot] = 2;  // prologue, the loop (which commits)
+        if (q) {
+            CK(h, cudaStreamWaitEvent(h->rs_up, h->rs_free[slot], 0));
+            CK(h, cudaMemcpyAsync(h->rs_stage[slot], q + (size_t)k * Jq, Jq * 8, cudaMemcpyHostToDevice, h->rs_up));
+            CK(h, cudaEventRecord(h->rs_ready[slot], h->rs_up));
+            CK(h, cudaStreamWaitEvent(h->stream, h->rs_ready[slot], 0));
+            if ((r = rescale(slot))) return r;
+            ++launches[slot];
+        }
+        if (!behind && !h->guess_valid) {
+            if ((r = launch_guess(h))) return r;
+            ++launches[slot];
+        }
+        r = rs_launch(h, slot, behind);
+        if (!r && phi) r = rs_snapshot(h, slot, phi + (size_t)k * Jq);
+        return r;
+    };
+    int status = OCI_OK, src_slot = (n - 1) & 1;  // slot whose staged source the cell sources hold at the end
+    if ((rc = enqueue(0, false))) return rc;
+    int queued_to = 1;  // steps enqueued
+    for (int k = 0; k < n; ++k) {
+        const int slot = k & 1, nslot = slot ^ 1;
+        if (queued_to < n && queued_to == k + 1) {
+            if ((rc = enqueue(queued_to, true))) return rc;
+            ++queued_to;
+        }
+        const bool queued = queued_to == k + 2;  // step k + 1 is on the stream behind this one
+        CK(h, cudaEventSynchronize(h->rs_done[slot]));
+        IterState s = h->rs_st[slot];
+        int refined = 0, lc = launches[slot];
+        if (s.status == ocik::ST_STALL && h->cells_lin && h->ks.refine) {
+            if (queued) {
+                CK(h, cudaEventSynchronize(h->rs_done[nslot]));  // held behind this step: it did nothing
+                if (q && (rc = rescale(slot))) return rc;         // this step's cell sources for its refinement
+            }
+            const int main_iters = s.iter;
+            if ((rc = refine_step(h, &s))) return rc;
+            refined = 1;
+            lc += 2 + (s.iter - main_iters);
+            CK(h, cudaEventRecord(h->rs_ev1[slot], h->stream));
+            if ((rc = read_state(h, &s))) return rc;
+            if (phi && s.committed && (rc = rs_snapshot(h, slot, phi + (size_t)k * Jq))) return rc;
+            if (queued) {
+                if (q && (rc = rescale(nslot))) return rc;
+                if (s.committed) {  // the held step again, now behind a committed one
+                    if ((rc = rs_launch(h, nslot, false))) return rc;
+                    launches[nslot] += 2;
+                    if (phi && (rc = rs_snapshot(h, nslot, phi + (size_t)(k + 1) * Jq))) return rc;
+                }
+            }
+        }
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, h->rs_ev0[slot], h->rs_ev1[slot]));
+        h->guess_valid = s.committed != 0;
+        const int code = map_status(s.status);
+        if (stats) {
+            oci_stats &o = stats[k];
+            o = oci_stats{};
+            o.iters = s.iter;
+            o.status = code;
+            o.residual = s.resid;
+            o.seconds = ms * 1e-3;
+            o.committed = s.committed;
+            o.refined = refined;
+            o.launches = lc;
+        }
+        if (!s.committed) {
+            status = code == OCI_OK ? OCI_ENOTCONV : code;
+            if (queued) {
+                CK(h, cudaEventSynchronize(h->rs_done[nslot]));  // held: it did nothing
+                if (q && (rc = rescale(slot))) return rc;         // the handle keeps this step's sources
+            }
+            src_slot = slot;
+            skip_from(k + 1);
+            break;
+        }
+        if (done) *done = k + 1;
+    }
+    if (q) {  // the source moments of the cell sources now in place (as oci_set_source leaves them)
+        CK(h, cudaMemcpyAsync(h->q_dev, h->rs_stage[src_slot], Jq * 8, cudaMemcpyDeviceToDevice, h->stream));
+        h->q_host_valid = false;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaStreamSynchronize(h->copy_stream));
+    CK(h, cudaStreamSynchronize(h->rs_up));
+    return status;
 }
 
 int oci_fluxes(const oci_handle *hc, double *phi)
@@ -2333,6 +2554,7 @@ const char *oci_strerror(int code)
     case OCI_ENAN: return "non-finite scalar flux";
     case OCI_ETIMEOUT: return "device iteration guard tripped";
     case OCI_ESTATE: return "call not valid in this state";
+    case OCI_ESKIPPED: return "step not run: an earlier step of the call did not commit";
     default: return "unknown status";
     }
 }

@@ -45,7 +45,7 @@ struct __align__(16) kmat { double k00, k01, k10, k11; };
 
 enum : int { BC_VACUUM = 0, BC_REFLECT = 1, BC_INCIDENT = 2 };
 enum : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXITER = 2, ST_NAN = 3, ST_GUARD = 4, ST_TIMEOUT = 5, ST_STALL = 6,
-             ST_SWITCH = 7 };  // ST_SWITCH: the BF16-halo phase of a step ended, FP32 iterations follow
+             ST_SWITCH = 7, ST_HELD = 8 };  // ST_SWITCH: the BF16-halo phase of a step ended, FP32 iterations follow
 // k_cells modes (M_LIN: correction equation of the FP32 refinement, staged kernel only)
 enum : int { M_OCI = 0, M_SI = 1, M_LIN = 2 };
 // k_percell modes
@@ -67,6 +67,7 @@ struct IterState {
     int rot3;          // this step's iterations rotated through three face buffers
     int cur_face;      // ... and the buffer holding the latest iterate
     int lin_first;     // FP32 refinement: number of the correction's first iteration
+    int chain;         // set before a step queued behind another: hold it unless that one committed
 };
 
 // Barrier-free persistent loop (k_cells_tma ASYNC): per-iteration arrival
@@ -995,6 +996,9 @@ __global__ void __launch_bounds__(tma_max_threads(CHUNK, PPL), 1) k_cells_tma(co
     constexpr bool IN_BF = HALO == 2 || HALO == 3, OUT_BF = HALO == 1 || HALO == 2;
     constexpr unsigned FB = IN_BF ? 4u : 8u;  // bytes per face pair read
     extern __shared__ __align__(128) unsigned char smem[];
+    // a step held by its prologue (queued behind a step that did not commit):
+    // every block leaves before touching anything
+    if (LOOP && __ldcg(&p.st->status) == ST_HELD) return;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
@@ -2209,6 +2213,13 @@ __global__ void __launch_bounds__(256) k_refine_residual(const KParams<float> p,
 // Step prologue: reset the iteration state for a new time step.
 static __global__ void k_step_begin(IterState *st)
 {
+    if (st->chain) {  // queued behind the previous step: run only if that one committed cleanly
+        st->chain = 0;
+        if (!st->committed || st->status == ST_STALL) {
+            st->status = ST_HELD;
+            return;
+        }
+    }
     st->iter = 0;
     st->status = ST_RUNNING;
     st->arrive = 0u;
