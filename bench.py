@@ -541,42 +541,17 @@ def run_learned(args, pkg, torch, stream):
 
 
 def nn_breakdown(pkg, torch, W, stream, J=131072, reps=50):
-    """Device time of the network's parts for one 131072-cell sample (CUDA
-    events on the launching stream, mean of reps after warm-up): the input
-    features, the forward pass (the BF16 parameter image and the fused
-    five-layer tensor-core kernel) and the prediction of the moments (the lift into the iterate is one
-    pass over the faces, inside the step)."""
+    """Device time of the network's parts for one 131072-cell sample of the
+    first deployment slab (learned.time_inference: CUDA events on the launching
+    stream, mean of reps after warm-up)."""
+    from paper_2305_13555_gb300 import learned
     prob = workloads.config5_deploy(GAIN_SEEDS[0], J=J, N=64, n_steps=2)
     s = pkg.Solver(prob, precision="fp32", tol=1e-8, stream=stream.cuda_stream)
-    dev = "cuda"
-    stat = torch.empty((1, J, 4), dtype=torch.float32, device=dev)
-    qf = torch.empty((1, J), dtype=torch.float32, device=dev)
+    stat = torch.empty((1, J, 4), dtype=torch.float32, device="cuda")
+    qf = torch.empty((1, J), dtype=torch.float32, device="cuda")
     pkg.oci_nn_static_features(s.h, stat, qf)
     s.close()
-    g = torch.Generator(device=dev).manual_seed(0)
-    phi1 = torch.rand((1, J, 4), dtype=torch.float64, device=dev, generator=g)
-    phi2 = torch.rand((1, J, 4), dtype=torch.float64, device=dev, generator=g)
-    inp = torch.empty((1, 13, J), dtype=torch.float32, device=dev)
-    out = torch.empty((1, 4, J), dtype=torch.float32, device=dev)
-    sc = torch.empty(1, dtype=torch.float32, device=dev)
-    phat = torch.empty((1, J, 4), dtype=torch.float64, device=dev)
-    ws = torch.empty(pkg.oci_nn_workspace_bytes(1, J), dtype=torch.uint8, device=dev)
-    Wd = torch.tensor(W, device=dev)
-    res = {}
-    for name, fn in (("features", lambda: pkg.oci_nn_features(phi1, phi2, stat, qf, inp, sc, stream.cuda_stream)),
-                     ("forward", lambda: pkg.oci_nn_forward(Wd, inp, out, ws, stream.cuda_stream)),
-                     ("predict", lambda: pkg.oci_nn_predict(phi1, out, sc, phat, stream.cuda_stream))):
-        for _ in range(5):
-            fn()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        res[name] = round(e0.elapsed_time(e1) * 1e3 / reps, 2)
-    return res
+    return learned.time_inference(W, J, reps=reps, stat=stat, qfeat=qf, stream=stream)
 
 
 def run_deploy200(args, pkg, torch, stream):

@@ -13,6 +13,7 @@ Usage (on a GPU):
         --out paper_2305_13555_gb300/data/cnn_weights.npy
 """
 import argparse
+import json
 import math
 import os
 import time
@@ -134,6 +135,45 @@ def predict(params, phi1, phi2, stat, qfeat):
     return phat
 
 
+def time_inference(params, J, reps=50, warmup=5, stat=None, qfeat=None, stream=None):
+    """Device microseconds of the network's parts for one J-cell sample (CUDA
+    events on the launching stream, mean of reps after warmup): the input
+    features, the forward pass (the BF16 parameter image and the fused
+    five-layer tensor-core kernel) and the prediction of the moments.  Random
+    moments; static inputs random unless given."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    if stat is None:
+        stat = torch.rand((1, J, 4), dtype=torch.float32, device="cuda", generator=g)
+    if qfeat is None:
+        qfeat = torch.rand((1, J), dtype=torch.float32, device="cuda", generator=g)
+    phi1 = torch.rand((1, J, 4), dtype=torch.float64, device="cuda", generator=g)
+    phi2 = torch.rand((1, J, 4), dtype=torch.float64, device="cuda", generator=g)
+    inp = torch.empty((1, 13, J), dtype=torch.float32, device="cuda")
+    out = torch.empty((1, 4, J), dtype=torch.float32, device="cuda")
+    sc = torch.empty(1, dtype=torch.float32, device="cuda")
+    phat = torch.empty((1, J, 4), dtype=torch.float64, device="cuda")
+    ws = torch.empty(oci_nn_workspace_bytes(1, J), dtype=torch.uint8, device="cuda")
+    p = torch.as_tensor(params, device="cuda")
+    cs = stream.cuda_stream
+    res = {}
+    for name, fn in (("features", lambda: oci_nn_features(phi1, phi2, stat, qfeat, inp, sc, cs)),
+                     ("forward", lambda: oci_nn_forward(p, inp, out, ws, cs)),
+                     ("predict", lambda: oci_nn_predict(phi1, out, sc, phat, cs))):
+        for _ in range(warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = round(e0.elapsed_time(e1) * 1e3 / reps, 2)
+    return res
+
+
 def load_weights(path=DEFAULT_WEIGHTS):
     return np.load(path).astype(np.float32)
 
@@ -155,9 +195,16 @@ def main():
                     help="starting parameters: linear extrapolation in time plus free channels "
                          "(extrapolation_params), or He-uniform (init_params)")
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--time-inference", type=int, metavar="J", default=0,
+                    help="only time the inference of the weights at --out on a J-cell sample and print it")
     a = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
+    if a.time_inference:
+        from . import load_library
+        load_library()
+        print(json.dumps(time_inference(load_weights(a.out), a.time_inference)))
+        return
     t0 = time.time()
     problem = None
     if a.family == "thin":
