@@ -325,10 +325,45 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_forward_fused(const unsigned ch
     __nv_bfloat16 *s_b = s_a + FB * FRS_ACT;
     float *s_out = reinterpret_cast<float *>(s_x);  // free once layer 0 has read it
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int per = (J + FOUT - 1) / FOUT;
+    // the tile's input rows, FP32 in registers: loaded for the next tile while the
+    // current one's layers run, rounded and transposed into s_x afterwards
+    constexpr int NST = (fcip(0) * FB + FTHREADS - 1) / FTHREADS;
+    float stage[NST];
+    auto load_tile = [&](int tile) {
+        const int b = tile / per, xrow0 = (tile % per) * FOUT - PAD * NL;
+#pragma unroll
+        for (int u = 0; u < NST; ++u) {
+            const int e = t + u * FTHREADS;
+            const int ci = e / FB, r = e % FB, x = xrow0 + r;
+            stage[u] = (e < fcip(0) * FB && ci < FCI && x >= 0 && x < J) ? __ldg(in + ((size_t)b * FCI + ci) * J + x)
+                                                                        : 0.f;
+        }
+    };
+    auto store_tile = [&]() {
+#pragma unroll
+        for (int u = 0; u < NST; ++u) {
+            const int e = t + u * FTHREADS;
+            if (e < fcip(0) * FB) s_x[(e % FB) * frs(0) + e / FB] = __float2bfloat16_rn(stage[u]);
+        }
+    };
+    if (blockIdx.x < B * per) load_tile(blockIdx.x);
     {
+        // the parameter image: every thread's 16-byte loads issued before any is stored
+        constexpr int NW = (FPACK_BYTES / 16 + FTHREADS - 1) / FTHREADS;
         const uint4 *src = reinterpret_cast<const uint4 *>(pack);
         uint4 *dst = reinterpret_cast<uint4 *>(fsm);
-        for (int e = t; e < FPACK_BYTES / 16; e += FTHREADS) dst[e] = src[e];
+        uint4 wv[NW];
+#pragma unroll
+        for (int u = 0; u < NW; ++u) {
+            const int e = t + u * FTHREADS;
+            if (e < FPACK_BYTES / 16) wv[u] = __ldg(src + e);
+        }
+#pragma unroll
+        for (int u = 0; u < NW; ++u) {
+            const int e = t + u * FTHREADS;
+            if (e < FPACK_BYTES / 16) dst[e] = wv[u];
+        }
         const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
         for (int e = t; e < 2 * PAD * FRS_ACT; e += FTHREADS) {  // edge rows no layer writes
             const int r = e / FRS_ACT, c = e % FRS_ACT, row = r < PAD ? r : FB - 2 * PAD + r;
@@ -336,16 +371,12 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_forward_fused(const unsigned ch
             s_b[row * FRS_ACT + c] = zero;
         }
     }
-    const int per = (J + FOUT - 1) / FOUT;
     for (int tile = blockIdx.x; tile < B * per; tile += gridDim.x) {
         const int b = tile / per, x0 = (tile % per) * FOUT;
         const int xrow0 = x0 - PAD * NL;  // cell of buffer row 0
-        for (int e = t; e < fcip(0) * FB; e += FTHREADS) {
-            const int ci = e / FB, r = e % FB, x = xrow0 + r;
-            const float v = (ci < FCI && x >= 0 && x < J) ? in[((size_t)b * FCI + ci) * J + x] : 0.f;
-            s_x[r * frs(0) + ci] = __float2bfloat16_rn(v);
-        }
+        store_tile();
         __syncthreads();
+        if (tile + (int)gridDim.x < B * per) load_tile(tile + gridDim.x);  // lands while the layers run
         fused_layer<0>(s_x, s_w + fw_off(0), s_bias + fb_off(0), s_a, nullptr, xrow0, J, warp, lane);
         __syncthreads();
         fused_layer<1>(s_a, s_w + fw_off(1), s_bias + fb_off(1), s_b, nullptr, xrow0, J, warp, lane);

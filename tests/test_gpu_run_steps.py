@@ -49,13 +49,13 @@ def _batched(prob, q, precision, n, **kw):
         return rc, done, stats, phi, s.get_state()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_run_steps_equals_one_step_at_a_time(precision):
+@pytest.mark.parametrize("precision,guess", [("fp32", "previous"), ("fp64", "previous"), ("fp32", "extrapolate")])
+def test_run_steps_equals_one_step_at_a_time(precision, guess):
     n = 6
     prob = workloads.hetero(seed=21, J=20000, N=64, n_steps=n)
     q = _sources(prob, n, 1)
-    ref_phi, ref_its, _, ref_state = _sequential(prob, q, precision, n)
-    rc, done, stats, phi, state = _batched(prob, q, precision, n)
+    ref_phi, ref_its, _, ref_state = _sequential(prob, q, precision, n, guess=guess)
+    rc, done, stats, phi, state = _batched(prob, q, precision, n, guess=guess)
     assert rc == pkg.OCI_OK and done == n
     assert [st["iters"] for st in stats] == ref_its
     assert np.array_equal(phi, ref_phi)
