@@ -303,7 +303,7 @@ def run_ours(args, rank, world):
            "h2d_bytes_per_step": int(q_host[0].nbytes + state_bytes / args.steps),
            "d2h_bytes_per_step": int(phi_host[0].nbytes),
            "h2d": "source Q each step, initial angular flux psi0 at each trajectory restart (pinned host memory)",
-           "api": "oci_run_steps: two steps in flight, sources up and moments down on the library's copy stream"}
+           "api": "oci_run_steps: two steps in flight, sources up and moments down on the library's upload and copy streams"}
     s.close()
 
     compare = {}
