@@ -128,3 +128,23 @@ def test_learned_guess_on_the_extrapolated_iterate_keeps_the_answer():
                 out.append(s.fluxes())
             phis[guess] = np.array(out)
     assert _rel(phis["extrapolate"], phis["previous"]) < 1e-7
+
+
+@pytest.mark.parametrize("bcl,bcr", [("reflect", "vacuum"), ("vacuum", "reflect")])
+def test_si_steps_after_extrapolated_commits_keep_the_answer(bcl, bcr):
+    """OCI and SI steps alternating on a handle with the extrapolated start (an
+    SI step starts from the committed moments and, at a reflecting right face,
+    the extrapolated face it lags; its own commit leaves the end-of-step flux):
+    every step converges to the answer of the same sequence without it."""
+    n = 6
+    prob = workloads.random_small(seed=41, J=300, N=16, bc_left=bcl, bc_right=bcr)
+    out = {}
+    for guess in ("previous", "extrapolate"):
+        phis = []
+        with pkg.Solver(prob, precision="fp64", tol=1e-11, guess=guess) as s:
+            for k in range(n):
+                rc, st = s.step("si" if k % 2 else "oci")
+                assert rc == pkg.OCI_OK, (guess, k, rc, st)
+                phis.append(s.fluxes())
+        out[guess] = np.array(phis)
+    assert _rel(out["extrapolate"], out["previous"]) < 1e-8
