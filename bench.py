@@ -466,8 +466,9 @@ def run_sweep(args, pkg, torch, stream, n_steps=None):
     ratio, the cell width and the quadrature order (c in {0.5, 0.9, 0.99}, dx in
     {0.01, 0.1, 1, 10} mfp, S_32 and S_64; Sigma = 1, dt = 0.05, reflecting left /
     vacuum right, tol 1e-8): iterations and device seconds per converged step
-    over the trajectory's first steps, for OCI in FP32 and FP64, SI with the
-    paper's march and SI with the parallel prefix (FP32)."""
+    over the trajectory's first steps, for OCI in FP32 and FP64, FP32 OCI started
+    from the extrapolation in time, SI with the paper's march and SI with the
+    parallel prefix (FP32)."""
     n_steps = n_steps or args.sweep_steps
     rows = []
     for N in (32, 64):
@@ -475,10 +476,12 @@ def run_sweep(args, pkg, torch, stream, n_steps=None):
             for dx in (0.01, 0.1, 1.0, 10.0):
                 prob = workloads.config2(N=N, c=c, dx=dx, J=65536, n_steps=n_steps)
                 row = {"N": N, "c": c, "dx": dx}
-                for key, prec, method, sweep in (("oci_fp32", "fp32", "oci", "march"), ("oci_fp64", "fp64", "oci", "march"),
-                                                 ("si_march_fp32", "fp32", "si", "march"),
-                                                 ("si_scan_fp32", "fp32", "si", "scan")):
-                    r = _run_steps(pkg, stream, prob, n_steps, prec, method, sweep, cap=500)
+                for key, prec, method, sweep, guess in (
+                        ("oci_fp32", "fp32", "oci", "march", "previous"), ("oci_fp64", "fp64", "oci", "march", "previous"),
+                        ("oci_fp32_extrapolated", "fp32", "oci", "march", "extrapolate"),
+                        ("si_march_fp32", "fp32", "si", "march", "previous"),
+                        ("si_scan_fp32", "fp32", "si", "scan", "previous")):
+                    r = _run_steps(pkg, stream, prob, n_steps, prec, method, sweep, cap=500, guess=guess)
                     row[key] = ({"iters": round(r["iters_per_step"], 2), "ms": round(r["s_per_step"] * 1e3, 4)}
                                 if "s_per_step" in r else r)
                     if r.get("steps_at_cap"):
@@ -490,6 +493,8 @@ def run_sweep(args, pkg, torch, stream, n_steps=None):
                     row["si_march_over_oci_fp32_time"] = round(row["si_march_fp32"]["ms"] / row["oci_fp32"]["ms"], 3)
                 if "ms" in row["oci_fp32"] and best_si is not None:
                     row["best_si_over_oci_fp32_time"] = round(best_si / row["oci_fp32"]["ms"], 3)
+                if "ms" in row["oci_fp32_extrapolated"] and best_si is not None:
+                    row["best_si_over_oci_fp32_extrapolated_time"] = round(best_si / row["oci_fp32_extrapolated"]["ms"], 3)
                 rows.append(row)
     return {"workload": f"homogeneous slab 65536 cells, Sigma=1, dt=0.05, v=1, Q=1, reflect/vacuum, tol 1e-8; "
                         f"steps 1-{n_steps} of each trajectory from psi0 = 0",
