@@ -284,7 +284,8 @@ int oci_step_wait(oci_handle *h, oci_stats *st);
  * Pass page-locked (pinned) q and phi for the copies to overlap.  The call
  * returns when every copy is done.  The first step that does not commit ends
  * the call: its status is returned, later steps are not run (stats status
- * OCI_ESKIPPED) and the handle keeps that step's source.  *done (may be NULL)
+ * OCI_ESKIPPED; their phi entries are unspecified) and the handle keeps that
+ * step's source.  *done (may be NULL)
  * = steps committed.  OCI_OK when all n committed; OCI_EINVAL for n < 0,
  * OCI_ESTATE while a step is pending or a decomposed step is open. */
 int oci_run_steps(oci_handle *h, int32_t n, const double *q, double *phi, oci_stats *stats, int32_t *done);
