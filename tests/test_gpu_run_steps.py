@@ -49,18 +49,20 @@ def _batched(prob, q, precision, n, **kw):
         return rc, done, stats, phi, s.get_state()
 
 
-@pytest.mark.parametrize("precision,guess", [("fp32", "previous"), ("fp64", "previous"), ("fp32", "extrapolate")])
-def test_run_steps_equals_one_step_at_a_time(precision, guess):
+@pytest.mark.parametrize("precision,guess,halo", [("fp32", "previous", "fp32"), ("fp64", "previous", "fp32"),
+                                                  ("fp32", "extrapolate", "fp32"), ("fp32", "previous", "bf16")])
+def test_run_steps_equals_one_step_at_a_time(precision, guess, halo):
+    """Queued (FP32 loop), and one at a time (FP64; the BF16-halo phase)."""
     n = 6
     prob = workloads.hetero(seed=21, J=20000, N=64, n_steps=n)
     q = _sources(prob, n, 1)
-    ref_phi, ref_its, _, ref_state = _sequential(prob, q, precision, n, guess=guess)
-    rc, done, stats, phi, state = _batched(prob, q, precision, n, guess=guess)
+    ref_phi, ref_its, _, ref_state = _sequential(prob, q, precision, n, guess=guess, halo=halo)
+    rc, done, stats, phi, state = _batched(prob, q, precision, n, guess=guess, halo=halo)
     assert rc == pkg.OCI_OK and done == n
     assert [st["iters"] for st in stats] == ref_its
     assert np.array_equal(phi, ref_phi)
     assert np.array_equal(state, ref_state)
-    if precision == "fp32":  # queued: prologue, the loop that commits, the source scaling (+ the first guess)
+    if precision == "fp32" and halo == "fp32":  # queued: prologue, the loop that commits, the source scaling (+ the first guess)
         assert [st["launches"] for st in stats] == [4] + [3] * (n - 1), stats
 
 
