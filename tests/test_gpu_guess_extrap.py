@@ -148,3 +148,18 @@ def test_si_steps_after_extrapolated_commits_keep_the_answer(bcl, bcr):
                 phis.append(s.fluxes())
         out[guess] = np.array(phis)
     assert _rel(out["extrapolate"], out["previous"]) < 1e-8
+
+
+def test_extrapolated_iterate_full_size_fp64_and_fp32():
+    """65536 cells, S_64 (the benchmark's launch configuration; FP32: the
+    persistent loop that ends the step, extrapolating in its ring-streamed
+    commit): two steps of two fixed iterations against the oracle's iteration
+    from the host-built extrapolated iterate, on every output."""
+    prob = workloads.config2(N=64, c=0.9, dx=0.1, J=65536, n_steps=2)
+    ref_phi, ref_pe = _oracle_extrapolated(prob, 2, 2)
+    phis, state = _gpu_fixed(prob, 2, 2, "fp64")
+    assert _rel(phis, ref_phi) < FP64_TOL
+    assert _rel(state, ref_pe) < FP64_TOL
+    phis, state = _gpu_fixed(prob, 2, 2, "fp32")
+    assert _rel(phis, ref_phi) < FP32_TOL
+    assert _rel(state, ref_pe) < FP32_TOL
