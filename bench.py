@@ -468,7 +468,7 @@ def run_sweep(args, pkg, torch, stream, n_steps=None):
     vacuum right, tol 1e-8): iterations and device seconds per converged step
     over the trajectory's first steps, for OCI in FP32 and FP64, FP32 OCI started
     from the extrapolation in time, SI with the paper's march and SI with the
-    parallel prefix (FP32)."""
+    parallel prefix (FP32), the latter also from the extrapolated start."""
     n_steps = n_steps or args.sweep_steps
     rows = []
     for N in (32, 64):
@@ -480,7 +480,8 @@ def run_sweep(args, pkg, torch, stream, n_steps=None):
                         ("oci_fp32", "fp32", "oci", "march", "previous"), ("oci_fp64", "fp64", "oci", "march", "previous"),
                         ("oci_fp32_extrapolated", "fp32", "oci", "march", "extrapolate"),
                         ("si_march_fp32", "fp32", "si", "march", "previous"),
-                        ("si_scan_fp32", "fp32", "si", "scan", "previous")):
+                        ("si_scan_fp32", "fp32", "si", "scan", "previous"),
+                        ("si_scan_fp32_extrapolated", "fp32", "si", "scan", "extrapolate")):
                     r = _run_steps(pkg, stream, prob, n_steps, prec, method, sweep, cap=500, guess=guess)
                     row[key] = ({"iters": round(r["iters_per_step"], 2), "ms": round(r["s_per_step"] * 1e3, 4)}
                                 if "s_per_step" in r else r)
@@ -495,6 +496,9 @@ def run_sweep(args, pkg, torch, stream, n_steps=None):
                     row["best_si_over_oci_fp32_time"] = round(best_si / row["oci_fp32"]["ms"], 3)
                 if "ms" in row["oci_fp32_extrapolated"] and best_si is not None:
                     row["best_si_over_oci_fp32_extrapolated_time"] = round(best_si / row["oci_fp32_extrapolated"]["ms"], 3)
+                se, oe = row["si_scan_fp32_extrapolated"], row["oci_fp32_extrapolated"]
+                if "ms" in se and "ms" in oe and not se.get("steps_at_cap"):  # like for like: both extrapolated
+                    row["si_scan_over_oci_fp32_both_extrapolated_time"] = round(se["ms"] / oe["ms"], 3)
                 rows.append(row)
     return {"workload": f"homogeneous slab 65536 cells, Sigma=1, dt=0.05, v=1, Q=1, reflect/vacuum, tol 1e-8; "
                         f"steps 1-{n_steps} of each trajectory from psi0 = 0",
@@ -565,7 +569,8 @@ def run_deploy200(args, pkg, torch, stream):
     iterations per converged step of plain FP32 OCI (from the previous step's
     flux, and from its extrapolation in time), FP32 OCI with the learned guess
     (adaptive, always, adaptive on the extrapolated start), plain FP64 OCI, and
-    SI (FP32, the paper's march and the parallel prefix)."""
+    SI (FP32, the paper's march and the parallel prefix, the latter also from
+    the extrapolated start)."""
     from paper_2305_13555_gb300 import learned
     W = learned.load_weights() if os.path.exists(learned.DEFAULT_WEIGHTS) else None
     n = args.deploy_steps
@@ -575,7 +580,7 @@ def run_deploy200(args, pkg, torch, stream):
     runs = [("oci_fp32_plain", "fp32", "oci", "march", 0, P), ("oci_fp32_extrapolated", "fp32", "oci", "march", 0, E),
             ("oci_fp64_plain", "fp64", "oci", "march", 0, P),
             ("si_march_fp32", "fp32", "si", "march", 0, P), ("si_scan_fp32", "fp32", "si", "scan", 0, P),
-            ("si_scan_fp64", "fp64", "si", "scan", 0, P)]
+            ("si_scan_fp32_extrapolated", "fp32", "si", "scan", 0, E), ("si_scan_fp64", "fp64", "si", "scan", 0, P)]
     if W is not None:
         runs.insert(2, ("oci_fp32_nn_adaptive", "fp32", "oci", "march", pkg.OCI_NN_GUESS_ADAPTIVE, P))
         runs.insert(3, ("oci_fp32_nn_guess", "fp32", "oci", "march", pkg.OCI_NN_GUESS, P))

@@ -205,14 +205,17 @@ int oci_set_halo(oci_handle *h, int32_t halo);
  * extrapolation in time through the last two end-of-step fluxes, with
  * d = psi_{k+1/2} - psi_{k-1/2} (the flux the step started from): step-average
  * moment psi_{k+1/2} + d/2, end moment psi_{k+1/2} + d (not the paper's;
- * exact for a flux linear in time; only iteration counts change).  The
- * iterate's scalar-flux moments, which only enter the first iteration's
- * relative change, stay the end-of-step moments, so that change is measured
- * from the previous step's flux.  A learned guess lifts this iterate, taking
- * its scalar flux as the same extrapolation of the last two committed steps'
- * moments.  Applies to the commits of OCI steps of the multiple-balance scheme
- * after the call; SI and backward-Euler steps, and a step after
- * oci_set_state or an uncommitted step, start from the end-of-step flux.
+ * exact for a flux linear in time; only iteration counts change).  After an
+ * OCI step the iterate's scalar-flux moments, which only enter the first
+ * iteration's relative change, stay the end-of-step moments, so that change is
+ * measured from the previous step's flux; after an SI step, whose iteration
+ * starts from them, they are extrapolated the same way (step average
+ * phi_{k+1/2} + (phi_{k+1/2} - phi_{k-1/2})/2, end phi_{k+1/2} + (phi_{k+1/2} -
+ * phi_{k-1/2})).  A learned guess lifts the iterate, taking its scalar flux as
+ * the same extrapolation of the last two committed steps' moments.  Applies
+ * to the commits of multiple-balance steps after the call; backward-Euler
+ * steps, and a step after oci_set_state or an uncommitted step, start from the
+ * end-of-step flux.
  * OCI_EINVAL for an unknown mode, OCI_ESTATE while a step is pending or a
  * decomposed step is open. */
 enum { OCI_GUESS_PREVIOUS = 0, OCI_GUESS_EXTRAPOLATE = 1 };

@@ -375,6 +375,21 @@ __device__ __forceinline__ void commit_corners(const Coef<R> &a, const r4<R> &qd
     mhi = fma_x(a.vi, vhr, fma_x(a.vr, vhi, fma_x(a.ui, vkr, mul_x(a.ur, vki))));
 }
 
+// The previous end-of-step moments (entries 2, 3 of a cell's published phi)
+// for every lane of the cell's segment (mask, its first lane base, lane ls in
+// it): each is read by the lane that later overwrites it (lane c % LPC stores
+// moment c), so the read precedes that store in the lane's own order, and
+// shuffled to the others.
+__device__ __forceinline__ void prev_end_moments(const double *phi_cell, unsigned mask, int base, int ls,
+                                                 double &old2, double &old3)
+{
+    const int lpc = __popc(mask);
+    const double v2 = ls == 2 % lpc ? __ldcg(phi_cell + 2) : 0.0;
+    const double v3 = ls == 3 % lpc ? __ldcg(phi_cell + 3) : 0.0;
+    old2 = __shfl_sync(mask, v2, base + 2 % lpc);
+    old3 = __shfl_sync(mask, v3, base + 3 % lpc);
+}
+
 // Reduce V values per lane (s with compensation e) over the LPC lanes of a
 // segment.  Afterwards lane holds NV = max(V/LPC, 1) sums in s[0..NV-1] for
 // value indices [base, base + NV) with base = NV * (lane % LPC) when V >= LPC,
@@ -1939,7 +1954,7 @@ __device__ __forceinline__ void percell_body(const KParams<R> &p, int gw, int nw
     const int J = p.J, P = p.P;
     const bool refl_l = (MODE == C_COMMIT_OCI || MODE == C_COMMIT_LIN) && p.bc_left == BC_REFLECT;
     const bool refl_r = (MODE == C_COMMIT_OCI || MODE == C_COMMIT_LIN) && p.bc_right == BC_REFLECT;
-    const bool ext = (MODE == C_COMMIT_OCI || MODE == C_COMMIT_LIN) && p.cfg->extrap != 0;
+    const bool ext = (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI || MODE == C_COMMIT_LIN) && p.cfg->extrap != 0;
     R mu[PPL];
 #pragma unroll
     for (int i = 0; i < PPL; ++i) mu[i] = (ls + LPC * i < P) ? ldg2(p.muw + ls + LPC * i).x : R(0);
@@ -2034,7 +2049,18 @@ __device__ __forceinline__ void percell_body(const KParams<R> &p, int gw, int nw
                     st2(p.faceM[fgs] + (size_t)cell * P + pp, mhr, mhr);
                 }
             }
-            if (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI) {
+            if (MODE == C_COMMIT_SI && ext) {
+                // an SI step starts from its scalar flux: extrapolate it in time as the faces
+                double old2, old3;
+                prev_end_moments(p.phi_out + 4 * (size_t)cell,
+                                 LPC == 32 ? 0xffffffffu : (((1u << LPC) - 1u) << (seg * LPC)), seg * LPC, ls, old2, old3);
+                for (int c = ls; c < 4; c += LPC) {
+                    p.phi_out[4 * (size_t)cell + c] = PhiStore<R>::wide(__ldcg(phi_pub + 4 * (size_t)cell + c));
+                    const double nh = PhiStore<R>::wide(__ldcg(phi_pub + 4 * (size_t)cell + 2 + (c & 1)));
+                    const double old = (c & 1) ? old3 : old2;
+                    p.phi0[4 * (size_t)cell + c] = phi_from_double<R>(nh + (c < 2 ? 0.5 : 1.0) * (nh - old));
+                }
+            } else if (MODE == C_COMMIT_OCI || MODE == C_COMMIT_SI) {
                 for (int c = ls; c < 4; c += LPC) {
                     p.phi_out[4 * (size_t)cell + c] = PhiStore<R>::wide(__ldcg(phi_pub + 4 * (size_t)cell + c));
                     p.phi0[4 * (size_t)cell + c] = __ldcg(phi_pub + 4 * (size_t)cell + 2 + (c & 1));

@@ -163,3 +163,46 @@ def test_extrapolated_iterate_full_size_fp64_and_fp32():
     phis, state = _gpu_fixed(prob, 2, 2, "fp32")
     assert _rel(phis, ref_phi) < FP32_TOL
     assert _rel(state, ref_pe) < FP32_TOL
+
+
+def _oracle_si_extrapolated(prob, n_iter, n_steps):
+    """n_iter SI iterations per step; from step 2 on the iterate is extrapolated
+    in time: the faces as in _oracle_extrapolated and the scalar flux the SI
+    iteration starts from, e + (e - e_old)/2 (step average) and e + (e - e_old)
+    (end), e / e_old the last two published end-of-step moments."""
+    J, N = prob["n_cells"], prob["n_ord"]
+    _, w = np.polynomial.legendre.leggauss(N)
+    pe = np.asarray(oracle.run(prob, "si", 0)["psi_edge"]).reshape(J, N, 2).copy()
+    e_prev = np.einsum("n,jnc->jc", w, pe)  # published end moments of the initial state
+    pe_prev, e_old, phis = None, None, []
+    for _ in range(n_steps):
+        if pe_prev is None:
+            psi = np.concatenate([pe, pe], axis=2)
+            phi = np.einsum("n,jnc->jc", w, psi)
+        else:
+            d = pe - pe_prev
+            psi = np.concatenate([pe + 0.5 * d, pe + d], axis=2)
+            de = e_prev - e_old
+            phi = np.concatenate([e_prev + 0.5 * de, e_prev + de], axis=1)
+        for _ in range(n_iter):
+            psi, phi = oracle.si_iteration(prob, pe, phi, psi)
+        pe_prev, pe = pe, psi[:, :, 2:4].copy()
+        e_old, e_prev = e_prev, phi[:, 2:4].copy()
+        phis.append(phi)
+    return np.array(phis), pe
+
+
+@pytest.mark.parametrize("bcl,bcr", [("reflect", "vacuum"), ("vacuum", "reflect"), ("incident", "reflect")])
+def test_extrapolated_si_iterate_fp64_matches_oracle(bcl, bcr):
+    prob = workloads.random_small(seed=55, J=150, N=16, bc_left=bcl, bc_right=bcr)
+    ref_phi, ref_pe = _oracle_si_extrapolated(prob, 3, 4)
+    phis = []
+    with pkg.Solver(prob, precision="fp64", guess="extrapolate") as s:
+        s.set_iteration(0.0, 3, commit_unconverged=True)
+        for _ in range(4):
+            rc, st = s.step("si")
+            assert rc == pkg.OCI_ENOTCONV and st["iters"] == 3 and st["committed"] == 1, (rc, st)
+            phis.append(s.fluxes())
+        state = s.get_state()
+    assert _rel(np.array(phis), ref_phi) < FP64_TOL
+    assert _rel(state, ref_pe) < FP64_TOL
