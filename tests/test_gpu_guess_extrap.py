@@ -192,9 +192,12 @@ def _oracle_si_extrapolated(prob, n_iter, n_steps):
     return np.array(phis), pe
 
 
-@pytest.mark.parametrize("bcl,bcr", [("reflect", "vacuum"), ("vacuum", "reflect"), ("incident", "reflect")])
-def test_extrapolated_si_iterate_fp64_matches_oracle(bcl, bcr):
-    prob = workloads.random_small(seed=55, J=150, N=16, bc_left=bcl, bc_right=bcr)
+@pytest.mark.parametrize("N,bcl,bcr", [(16, "reflect", "vacuum"), (16, "vacuum", "reflect"), (16, "incident", "reflect"),
+                                       (2, "reflect", "reflect"), (4, "vacuum", "reflect"), (64, "reflect", "incident")])
+def test_extrapolated_si_iterate_fp64_matches_oracle(N, bcl, bcr):
+    """Also one and two lanes per cell (S_2, S_4), where a lane publishes
+    several moments of its cell, and 32 (S_64)."""
+    prob = workloads.random_small(seed=55 + N, J=150, N=N, bc_left=bcl, bc_right=bcr)
     ref_phi, ref_pe = _oracle_si_extrapolated(prob, 3, 4)
     phis = []
     with pkg.Solver(prob, precision="fp64", guess="extrapolate") as s:
