@@ -191,6 +191,20 @@ def aggregate(dev_time, units, device="cpu"):
     return float(tmax[0]), float(t[1])
 
 
+def trajectory_chunks(k0, steps, n_traj, ch):
+    """Calls of the end-to-end leg: (restart from psi0 before the call, steps in
+    the call) for `steps` more steps of a trajectory of n_traj steps replayed
+    from psi0, k0 steps already run; a call never runs across a restart and has
+    at most ch steps."""
+    out, k, done = [], k0, 0
+    while done < steps:
+        m = min(ch, steps - done, n_traj - k % n_traj)
+        out.append((k > 0 and k % n_traj == 0, m))
+        k += m
+        done += m
+    return out
+
+
 def algorithmic_bytes(J, N, rs):
     """Bytes one OCI iteration must move: per cell-ordinate 2 incident values,
     2 time-edge values, 2 outgoing values (6 words); per cell phi^l in and
@@ -287,16 +301,14 @@ def run_ours(args, rank, world):
     r0 = counter["restarts"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    k = 0
-    while k < args.steps:
-        pos = counter["k"] % n_traj  # steps of the current trajectory already run (0: it restarts)
-        restart_if_due()
-        m = min(CH, args.steps - k, n_traj - pos)
-        counter["k"] += m - 1
+    for restart, m in trajectory_chunks(counter["k"], args.steps, n_traj, CH):
+        if restart:
+            s.set_state(psi_init)
+            counter["restarts"] += 1
+        counter["k"] += m
         rc, done, stats = pkg.oci_run_steps(s.h, m, q_host[:m], phi_host[:m])
         assert rc == pkg.OCI_OK and done == m, (rc, done, stats)
         e2e_iters += sum(st["iters"] for st in stats)
-        k += m
     e2e_t = time.perf_counter() - t0
     state_bytes = (counter["restarts"] - r0) * psi_init.nbytes  # initial conditions of the replayed trajectories
     e2e = {"value": float(J) * N * e2e_iters / e2e_t, "unit": UNIT,

@@ -1,7 +1,10 @@
 """Host logic of bench.py (CPU only): the clock record keeps only samples
-taken inside the timed region, and the reference arm sizes each step's
-sample so warm-up plus timed steps stay within its time budget."""
+taken inside the timed region, the reference arm sizes each step's sample so
+warm-up plus timed steps stay within its time budget, and the end-to-end leg's
+batched calls cover the steps without running across a trajectory restart."""
 import argparse
+
+import pytest
 
 import bench
 
@@ -88,3 +91,20 @@ def test_reference_arm_on_the_default_layered_slab(monkeypatch):
     assert set(fake.cells) == {131072}
     assert "131072-cell S_64" in r["cpu_baseline"]["sample"] and "layered slab" in r["config"]["workload"]
     assert total < 150.0
+
+
+@pytest.mark.parametrize("k0,steps,n_traj,ch", [(1005, 1000, 100, 32), (25, 20, 100, 32), (0, 7, 3, 2),
+                                               (100, 100, 100, 32), (99, 3, 100, 32)])
+def test_end_to_end_calls_cover_the_steps_without_crossing_a_restart(k0, steps, n_traj, ch):
+    """The end-to-end leg's calls of oci_run_steps: exactly `steps` steps, at
+    most ch per call, a restart from psi0 before a call exactly when the
+    trajectory is at a multiple of its length (and not at its very start), and
+    no call running across a trajectory's end."""
+    calls = bench.trajectory_chunks(k0, steps, n_traj, ch)
+    assert sum(m for _, m in calls) == steps
+    k = k0
+    for restart, m in calls:
+        assert 1 <= m <= ch
+        assert restart == (k > 0 and k % n_traj == 0)
+        assert k // n_traj == (k + m - 1) // n_traj  # inside one pass over the trajectory
+        k += m
